@@ -1,0 +1,196 @@
+/*
+ * sem_schwarz.h - C ABI of the GB300 library for the hybrid Schwarz/multigrid
+ * spectral-element Poisson solver of J. Stiller, "Nonuniformly weighted Schwarz
+ * smoothers for spectral element multigrid" (J. Sci. Comput.).
+ *
+ * The library solves the 2D spectral-element system A u = f of Sec. 2
+ * (Eq. (discrete), Eq. (system matrix): A = M_y (x) L_x + L_y (x) M_x on a
+ * Cartesian mesh of n_x x n_y elements of order p) with
+ *   - the weighted additive Schwarz smoother of Sec. 3.1 (Alg. 2),
+ *   - the p-multigrid V-cycle of Sec. 3.2 (Alg. 3),
+ *   - the inexact multigrid-preconditioned CG (MGCG) of Sec. 3.3 (Alg. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Vectors.  A field is the full node grid of the finest level, row-major with
+ *    x fastest: ny_nodes rows of nx_nodes doubles (sem_sizes).  With Dirichlet
+ *    walls the grid includes the wall nodes; their input values are ignored and
+ *    the library writes 0 there.  Periodic grids have n_x p x n_y p nodes.
+ *    Unless a call says otherwise, vector pointers are DEVICE pointers owned by
+ *    the caller, valid on the handle's device, 8-byte aligned, non-overlapping.
+ *  Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls marked "async" only enqueue work on that stream; calls
+ *    marked "sync" return after the work has finished.
+ *  Ownership.  The handle owns every workspace; no call allocates device memory
+ *    after sem_create returns.  Handles are not thread-safe: one host thread and
+ *    one stream at a time per handle.
+ *  Errors.  Every call returns a sem_status.  Nothing aborts and no exception
+ *    crosses the ABI.  sem_last_error() gives a message for the calling thread.
+ *    There is no CPU fallback: without a usable CUDA device sem_create fails.
+ */
+#ifndef SEM_SCHWARZ_H
+#define SEM_SCHWARZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sem_status {
+  SEM_OK = 0,
+  SEM_NOT_CONVERGED = 1, /* i_max reached before the residual test passed     */
+  SEM_BREAKDOWN = 2,     /* p^T q <= 0, or a NaN/Inf in a reduction           */
+  SEM_TIMEOUT = 3,       /* a bounded device wait gave up                     */
+  SEM_BAD_ARG = 4,       /* invalid configuration or argument                 */
+  SEM_CUDA_ERROR = 5,    /* a CUDA runtime call failed                         */
+  SEM_OOM = 6            /* device allocation failed in sem_create           */
+} sem_status;
+
+/* Weight functions of Table (weighting), Sec. 3.1.  SEM_W_ARITH is the
+ * arithmetic mean W = R_s C^+ R_s^T; SEM_W_IDENTITY is W = I (classical
+ * additive Schwarz). */
+typedef enum sem_weight {
+  SEM_W_LINEAR = 1,
+  SEM_W_CUBIC = 3,
+  SEM_W_QUINTIC = 5,
+  SEM_W_SEPTIC = 7,
+  SEM_W_TOPHAT = 100,
+  SEM_W_ARITH = 101,
+  SEM_W_IDENTITY = 102
+} sem_weight;
+
+/* Overlap n_{o,l} per level (Sec. 4): a fixed count, floor(p_l/8),
+ * ceil(p_l/8) or ceil(p_l/2); always capped at p_l - 1. */
+typedef enum sem_overlap_rule {
+  SEM_OVERLAP_FIXED = 0,
+  SEM_OVERLAP_FLOOR8 = 1,
+  SEM_OVERLAP_CEIL8 = 2,
+  SEM_OVERLAP_CEIL2 = 3
+} sem_overlap_rule;
+
+/* Arithmetic of the multigrid preconditioner.  The outer MGCG iteration, the
+ * operator application q = A p, the coarse solve and all dot products are
+ * FP64 in every mode.
+ *   SEM_PREC_FP64   the plain method, FP64 throughout.
+ *   SEM_PREC_FP32   V-cycle (residuals, transfers, FDM) in FP32.
+ *   SEM_PREC_TF32   as FP32, FDM contractions on tensor cores with TF32
+ *                   operands and FP32 accumulation.
+ *   SEM_PREC_BF16   as FP32, FDM contractions on tensor cores with BF16
+ *                   operands and FP32 accumulation. */
+typedef enum sem_precision {
+  SEM_PREC_FP64 = 0,
+  SEM_PREC_FP32 = 1,
+  SEM_PREC_TF32 = 2,
+  SEM_PREC_BF16 = 3
+} sem_precision;
+
+typedef struct sem_config {
+  int32_t nx, ny;          /* elements per direction (>= 2)                      */
+  int32_t p;               /* polynomial order, a power of two in [2, 32]        */
+  int32_t periodic;        /* 1: periodic in x and y; 0: homogeneous Dirichlet   */
+  double lx, ly;           /* domain [0, lx] x [0, ly] (uniform meshes)          */
+  const double* x_edges;   /* optional host array of nx+1 increasing x edges     */
+  const double* y_edges;   /* optional host array of ny+1 increasing y edges     */
+  int32_t overlap_rule;    /* sem_overlap_rule                                   */
+  int32_t overlap;         /* n_o for SEM_OVERLAP_FIXED                          */
+  int32_t weight;          /* sem_weight                                         */
+  int32_t ns1, ns2;        /* pre-/post-smoothing steps per level (Alg. 3)       */
+  int32_t variable_cycle;  /* 1: n_{s,l} doubles per coarser level (Sec. 4.2)    */
+  int32_t precision;       /* sem_precision                                      */
+  double tol;              /* MGCG stops when ||r_i|| <= tol * ||r_0||           */
+  int32_t i_max;           /* MGCG iteration limit                               */
+} sem_config;
+
+typedef struct sem_result {
+  int32_t iterations;      /* i at exit of Alg. 4 (or V-cycles of sem_mg_solve)   */
+  int32_t status;          /* sem_status of the solve                            */
+  double res0;             /* ||r_0||_2                                          */
+  double res;              /* ||r_i||_2 at exit (recursively updated residual)   */
+  double rbar;             /* log10(res0 / res) / iterations (Sec. 4)            */
+} sem_result;
+
+typedef struct sem_handle sem_handle;
+
+/* Fill *cfg with defaults: 4x4 Dirichlet unit square, p = 4, n_o = 1, w_5,
+ * MG(1,0) steps, FP64, tol 1e-10, i_max 200. */
+void sem_default_config(sem_config* cfg);
+
+/* Set up a solver (sync).  Host FP64 set-up of Sec. 2 and Sec. 3: GLL nodes,
+ * element matrices, generalised eigenpairs of the restricted 1D pairs for the
+ * fast-diagonalisation inverse (Eq. (FDM)), weights (Eq. (weight function)),
+ * interpolation I_l, coarse factors; then allocates all device workspace on
+ * the current CUDA device and uploads the tables.
+ * Errors: SEM_BAD_ARG (invalid cfg, *out untouched), SEM_OOM, SEM_CUDA_ERROR. */
+int sem_create(const sem_config* cfg, sem_handle** out);
+
+/* Free everything the handle owns (sync).  NULL is ignored. */
+void sem_destroy(sem_handle* h);
+
+/* Node-grid layout of the finest level (host, no device work).  Any output
+ * pointer may be NULL.  n_unknowns excludes Dirichlet wall nodes. */
+int sem_sizes(const sem_handle* h, int64_t* n_unknowns, int64_t* nx_nodes, int64_t* ny_nodes);
+
+/* Node coordinates of the finest level (host): x[nx_nodes], y[ny_nodes],
+ * caller-owned HOST arrays. */
+int sem_coords(const sem_handle* h, double* x, double* y);
+
+/* b = M_2D f with M_2D = M_y (x) M_x, the GLL-quadrature mass (Sec. 2); the
+ * discrete right side of Eq. (discrete) for nodal source values f (async).
+ * Periodic grids: b is projected to zero mean (the range of A, Sec. 3.2). */
+int sem_mass(sem_handle* h, const double* f_nodal, double* b, void* stream);
+
+/* Au = A u, Eq. (system matrix), FP64, sum-factorised (async). */
+int sem_apply(sem_handle* h, const double* u, double* Au, void* stream);
+
+/* n_it sweeps of the weighted additive Schwarz method on the finest level,
+ * Alg. 2: r = f - A u; u += sum_s R_s^T W A_ss^{-1} R_s r (async).  u is
+ * updated in place.  Runs in the handle's precision (FP64 storage of u). */
+int sem_smooth(sem_handle* h, double* u, const double* f, int32_t n_it, void* stream);
+
+/* One multigrid V-cycle, Alg. 3 MultigridCycle(u, f, n_s), u in place (async). */
+int sem_vcycle(sem_handle* h, double* u, const double* f, void* stream);
+
+/* Stand-alone multigrid iteration MG(ns1, ns2) (sync): V-cycles until
+ * ||f - A u|| <= tol ||f - A u_0|| or i_max cycles.  If history != NULL it
+ * receives the residual norms of cycles 0..iterations (HOST array of
+ * history_len doubles). */
+int sem_mg_solve(sem_handle* h, double* u, const double* f, sem_result* res,
+                 double* history, int32_t history_len, void* stream);
+
+/* Inexact MG-preconditioned CG, Alg. 4 (sync): from the caller's u (in place)
+ * until ||r_i|| <= tol ||r_0|| or i_max iterations; beta by the Polak-Ribiere
+ * form z^T (r - r_old) / delta.  history as in sem_mg_solve (norms ||r_i||,
+ * i = 0..iterations).  Returns res->status. */
+int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res,
+                  double* history, int32_t history_len, void* stream);
+
+/* Host-only inspection of the set-up tables of one level (no device work;
+ * works without a GPU).  Fills *info; every array pointer may be NULL, else it
+ * is a caller-owned HOST array of the size given by info (call once with NULL
+ * arrays to get the sizes):
+ *   tab_x[nx]                  subdomain table id of each element column
+ *   S_x[n_tables_x * m * m]    padded eigenvectors (row = window slot a, the
+ *                              element-local node a - n_o; column = eigen-slot)
+ *   lam_x[n_tables_x * m]      eigenvalues (padding slots hold 1)
+ *   w_x[n_tables_x * m]        1D weights (padding slots hold 0)
+ *   coords_x[nx_nodes]         node coordinates
+ * The x direction is reported; y is built by the same code.
+ * Errors: SEM_BAD_ARG for an invalid cfg or level. */
+typedef struct sem_level_info {
+  int32_t p, n_o, m, n_tables_x, nx_nodes;
+} sem_level_info;
+int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info, int32_t* tab_x,
+                      double* S_x, double* lam_x, double* w_x, double* coords_x);
+
+/* Name of a status code. */
+const char* sem_status_string(int32_t status);
+
+/* Last error message of the calling thread ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_SCHWARZ_H */

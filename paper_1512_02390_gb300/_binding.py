@@ -1,0 +1,228 @@
+"""ctypes binding of include/sem_schwarz.h: argument marshalling only.
+
+Every function here has the name of the C entry point it forwards to.  Vector
+arguments are CUDA float64 torch tensors (or raw device addresses as int);
+``stream`` is a torch.cuda.Stream, a raw cudaStream_t as int, or None for the
+current torch stream.  There is no CPU fallback: if the compiled library is
+missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsemschwarz.so")
+
+# sem_status
+SEM_OK, SEM_NOT_CONVERGED, SEM_BREAKDOWN, SEM_TIMEOUT, SEM_BAD_ARG, SEM_CUDA_ERROR, SEM_OOM = range(7)
+# sem_weight
+SEM_W_LINEAR, SEM_W_CUBIC, SEM_W_QUINTIC, SEM_W_SEPTIC = 1, 3, 5, 7
+SEM_W_TOPHAT, SEM_W_ARITH, SEM_W_IDENTITY = 100, 101, 102
+# sem_overlap_rule
+SEM_OVERLAP_FIXED, SEM_OVERLAP_FLOOR8, SEM_OVERLAP_CEIL8, SEM_OVERLAP_CEIL2 = range(4)
+# sem_precision
+SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_TF32, SEM_PREC_BF16 = range(4)
+
+EXPORTS = [
+    "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
+    "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
+    "sem_inspect_level", "sem_status_string", "sem_last_error",
+]
+
+
+class sem_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("p", ctypes.c_int32), ("periodic", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("x_edges", ctypes.POINTER(ctypes.c_double)), ("y_edges", ctypes.POINTER(ctypes.c_double)),
+        ("overlap_rule", ctypes.c_int32), ("overlap", ctypes.c_int32), ("weight", ctypes.c_int32),
+        ("ns1", ctypes.c_int32), ("ns2", ctypes.c_int32), ("variable_cycle", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("i_max", ctypes.c_int32),
+    ]
+
+
+class sem_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("rbar", ctypes.c_double)]
+
+
+class sem_level_info(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("n_o", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("n_tables_x", ctypes.c_int32), ("nx_nodes", ctypes.c_int32)]
+
+
+class SemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status_name(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: build it with `python -m paper_1512_02390_gb300.build` "
+                           "(or __graft_entry__.build()); there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "sem_default_config": (None, [ctypes.POINTER(sem_config)]),
+        "sem_create": (i32, [ctypes.POINTER(sem_config), ctypes.POINTER(vp)]),
+        "sem_destroy": (None, [vp]),
+        "sem_sizes": (i32, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64)]),
+        "sem_coords": (i32, [vp, dp, dp]),
+        "sem_mass": (i32, [vp, vp, vp, vp]),
+        "sem_apply": (i32, [vp, vp, vp, vp]),
+        "sem_smooth": (i32, [vp, vp, vp, i32, vp]),
+        "sem_vcycle": (i32, [vp, vp, vp, vp]),
+        "sem_mg_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), dp, i32, vp]),
+        "sem_pcg_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), dp, i32, vp]),
+        "sem_inspect_level": (i32, [ctypes.POINTER(sem_config), i32, ctypes.POINTER(sem_level_info),
+                                    ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]),
+        "sem_status_string": (ctypes.c_char_p, [i32]),
+        "sem_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_name(status: int) -> str:
+    return load_library().sem_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    return load_library().sem_last_error().decode()
+
+
+def _check(rc: int, allow=(SEM_OK,)):
+    if rc not in allow:
+        raise SemError(rc, last_error())
+    return rc
+
+
+def _ptr(t, n=None):
+    """Device address of a CUDA float64 tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("tensor has %d elements, the node grid has %d" % (t.numel(), n))
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def sem_default_config() -> sem_config:
+    cfg = sem_config()
+    load_library().sem_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def sem_create(cfg: sem_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().sem_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def sem_destroy(h) -> None:
+    load_library().sem_destroy(h)
+
+
+def sem_sizes(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().sem_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sem_coords(h):
+    _, nx, ny = sem_sizes(h)
+    x = np.zeros(nx)
+    y = np.zeros(ny)
+    _check(load_library().sem_coords(h, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return x, y
+
+
+def _n(h):
+    _, nx, ny = sem_sizes(h)
+    return nx * ny
+
+
+def sem_mass(h, f_nodal, b, stream=None):
+    n = _n(h)
+    _check(load_library().sem_mass(h, _ptr(f_nodal, n), _ptr(b, n), _stream(stream)))
+
+
+def sem_apply(h, u, Au, stream=None):
+    n = _n(h)
+    _check(load_library().sem_apply(h, _ptr(u, n), _ptr(Au, n), _stream(stream)))
+
+
+def sem_smooth(h, u, f, n_it, stream=None):
+    n = _n(h)
+    _check(load_library().sem_smooth(h, _ptr(u, n), _ptr(f, n), int(n_it), _stream(stream)))
+
+
+def sem_vcycle(h, u, f, stream=None):
+    n = _n(h)
+    _check(load_library().sem_vcycle(h, _ptr(u, n), _ptr(f, n), _stream(stream)))
+
+
+def _solve(fn, h, u, f, history_len, stream):
+    n = _n(h)
+    res = sem_result()
+    hist = np.zeros(max(0, int(history_len)))
+    hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history_len else None
+    rc = fn(h, _ptr(u, n), _ptr(f, n), ctypes.byref(res), hp, int(history_len), _stream(stream))
+    _check(rc, allow=(SEM_OK, SEM_NOT_CONVERGED, SEM_BREAKDOWN))
+    return res, hist[: min(len(hist), res.iterations + 1)]
+
+
+def sem_mg_solve(h, u, f, history_len=0, stream=None):
+    return _solve(load_library().sem_mg_solve, h, u, f, history_len, stream)
+
+
+def sem_pcg_solve(h, u, f, history_len=0, stream=None):
+    return _solve(load_library().sem_pcg_solve, h, u, f, history_len, stream)
+
+
+def sem_inspect_level(cfg: sem_config, level: int):
+    """Host-side set-up tables of one level (x direction); needs no GPU."""
+    lib = load_library()
+    info = sem_level_info()
+    _check(lib.sem_inspect_level(ctypes.byref(cfg), int(level), ctypes.byref(info), None, None, None, None, None))
+    nt, m = info.n_tables_x, info.m
+    tab = np.zeros(cfg.nx, dtype=np.int32)
+    S = np.zeros(nt * m * m)
+    lam = np.zeros(nt * m)
+    w = np.zeros(nt * m)
+    xc = np.zeros(info.nx_nodes)
+    d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib.sem_inspect_level(ctypes.byref(cfg), int(level), ctypes.byref(info),
+                                 tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), d(S), d(lam), d(w), d(xc)))
+    return dict(p=info.p, n_o=info.n_o, m=m, tab=tab, S=S.reshape(nt, m, m), lam=lam.reshape(nt, m),
+                w=w.reshape(nt, m), coords=xc)

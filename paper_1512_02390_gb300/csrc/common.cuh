@@ -1,0 +1,75 @@
+// Device-side views shared by the kernels of the Schwarz/multigrid solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sem {
+
+// One direction of one multigrid level, as the kernels see it.
+template <typename T>
+struct DirView {
+  int p;          // polynomial order of the level
+  int n;          // elements
+  int N;          // global nodes (periodic: n p; Dirichlet: n p + 1)
+  int periodic;   // 1 periodic, 0 Dirichlet walls
+  int n_o, m;     // overlap layers, window size p + 1 + 2 n_o
+  const T* Le;    // n x (p+1)^2 element stiffness
+  const T* Mg;    // N assembled mass diagonal
+  const int* tab; // n subdomain table ids
+  const T* S;     // tables x m x m eigenvectors (padded)
+  const T* lam;   // tables x m eigenvalues (padded with 1)
+  const T* w;     // tables x m weights (padded with 0)
+};
+
+// wrap/validate a global node index of a direction; returns -1 if the node
+// does not exist or is a Dirichlet wall node (value 0 there)
+__device__ __forceinline__ int node_or_wall(int g, int N, int periodic) {
+  if (periodic) {
+    g %= N;
+    return g < 0 ? g + N : g;
+  }
+  return (g > 0 && g < N - 1) ? g : -1;
+}
+
+constexpr int kRedThreads = 256;
+
+// Deterministic block sum of one double per thread (fixed tree order).
+__device__ __forceinline__ double block_sum(double v, double* sbuf) {
+  const int t = threadIdx.x;
+  sbuf[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) sbuf[t] += sbuf[t + s];
+    __syncthreads();
+  }
+  double r = sbuf[0];
+  __syncthreads();
+  return r;
+}
+
+// Sum of n partials in a fixed order, identical in every block that calls it.
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* sbuf) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  return block_sum(v, sbuf);
+}
+
+}  // namespace sem
+
+namespace sem {
+
+// floor(a / b) for b > 0 and any sign of a
+__device__ __forceinline__ int floordiv(int a, int b) {
+  int q = a / b;
+  return (q * b > a) ? q - 1 : q;
+}
+
+// one-time opt-in to more than 48 KB of dynamic shared memory
+template <typename K>
+inline cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace sem

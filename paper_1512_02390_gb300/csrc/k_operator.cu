@@ -1,0 +1,184 @@
+// Sum-factorised SEM Laplacian, Eq. (system matrix): A = M_y (x) L_x + L_y (x) M_x.
+//
+// Node-centric form: for node (j, i) of the global grid
+//   (A u)_{ji} = Mg_y[j] * sum_k Lg_x[i, k] u_{jk} + Mg_x[i] * sum_k Lg_y[j, k] u_{ki}
+// where the assembled 1D stiffness row Lg[i, .] is the element row of the
+// element holding i, plus the last row of the left neighbour when i sits on an
+// element interface.  A CTA owns a tile of TE x TE elements (32 x 32 nodes),
+// stages the tile plus one element of halo on the low side in shared memory,
+// and writes every owned node exactly once: no atomics, deterministic.
+#include "kernels.h"
+
+namespace sem {
+
+namespace {
+
+template <int P>
+struct Tile {
+  static constexpr int TE = (P >= 32) ? 1 : 32 / P;  // elements per direction
+  static constexpr int TN = TE * P;                  // owned nodes per direction
+  static constexpr int LN = TN + P + 1;              // staged nodes per direction
+  static constexpr int LP = LN + 1;                  // padded row pitch
+  static constexpr int NP = P + 1;
+};
+
+template <typename T, int P>
+size_t apply_smem() {
+  using Tl = Tile<P>;
+  return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1)) +
+         sizeof(double) * kRedThreads;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
+                                               const T* __restrict__ f, T* __restrict__ out, int dot,
+                                               double* __restrict__ part) {
+  using Tl = Tile<P>;
+  constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);          // LN x LP staged u
+  T* sLx = su + LN * LP;                           // (TE+1) x NP x NP
+  T* sLy = sLx + (TE + 1) * NP * NP;
+  T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
+  T* sMy = sMx + (TN + 1);
+  double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
+
+  const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
+  const int Nx = dx.N, Ny = dy.N;
+  const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic);
+    su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
+  }
+  // element stiffness of the tile and of its low-side neighbour (slot 0)
+  for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
+    const int le = idx / (NP * NP), ab = idx - le * NP * NP;
+    int exx = ex0 + le - 1, eyy = ey0 + le - 1;
+    if (dx.periodic) exx = (exx + dx.n) % dx.n;
+    if (dy.periodic) eyy = (eyy + dy.n) % dy.n;
+    sLx[idx] = (exx >= 0 && exx < dx.n) ? dx.Le[(long)exx * NP * NP + ab] : T(0);
+    sLy[idx] = (eyy >= 0 && eyy < dy.n) ? dy.Le[(long)eyy * NP * NP + ab] : T(0);
+  }
+  for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
+    const int gx = ex0 * P + idx, gy = ey0 * P + idx;
+    sMx[idx] = gx < Nx ? dx.Mg[gx] : T(0);
+    sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
+  }
+  __syncthreads();
+
+  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
+  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
+    const int gi = ex0 * P + ix, gj = ey0 * P + jy;
+    const long o = (long)gj * Nx + gi;
+    const bool wall = (!dx.periodic && (gi == 0 || gi == Nx - 1)) || (!dy.periodic && (gj == 0 || gj == Ny - 1));
+    T val = T(0);
+    if (!wall) {
+      const int lex = ix / P, a = ix - lex * P;
+      const int ley = jy / P, b = jy - ley * P;
+      const T* row = su + (jy + P) * LP;          // staged row of node (j, .)
+      // x direction: element row a of element lex (+ left neighbour's last row)
+      T xs = T(0), ys = T(0);
+      {
+        const T* L = sLx + (lex + 1) * NP * NP + a * NP;
+        const T* uu = row + lex * P + P;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) xs += L[k] * uu[k];
+        if (a == 0) {
+          const T* Ll = sLx + lex * NP * NP + P * NP;
+          const T* ul = row + lex * P;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) xs += Ll[k] * ul[k];
+        }
+      }
+      {
+        const T* L = sLy + (ley + 1) * NP * NP + b * NP;
+        const T* uu = su + (ley * P + P) * LP + ix + P;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ys += L[k] * uu[k * LP];
+        if (b == 0) {
+          const T* Ll = sLy + ley * NP * NP + P * NP;
+          const T* ul = su + (ley * P) * LP + ix + P;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) ys += Ll[k] * ul[k * LP];
+        }
+      }
+      val = sMy[jy] * xs + sMx[ix] * ys;
+      if (f) val = f[o] - val;
+    }
+    out[o] = val;
+    if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
+    else if (dot == 2) acc += (double)val * (double)val;
+  }
+  if (dot) {
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double> dy, const double* __restrict__ f,
+                                               double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double sred[kRedThreads];
+  const long n = (long)dx.N * dy.N;
+  double acc = 0.0;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+    const int gj = (int)(idx / dx.N), gi = (int)(idx - (long)gj * dx.N);
+    const bool wall = (!dx.periodic && (gi == 0 || gi == dx.N - 1)) || (!dy.periodic && (gj == 0 || gj == dy.N - 1));
+    const double v = wall ? 0.0 : dy.Mg[gj] * dx.Mg[gi] * f[idx];
+    b[idx] = v;
+    acc += v;
+  }
+  const double s = block_sum(acc, sred);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T, int P>
+cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f, T* out, int dot,
+                    double* part, int* nparts, cudaStream_t s) {
+  using Tl = Tile<P>;
+  const size_t sm = apply_smem<T, P>();
+  cudaError_t e = allow_smem(k_apply<T, P>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((dx.n + Tl::TE - 1) / Tl::TE, (dy.n + Tl::TE - 1) / Tl::TE);
+  if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
+  if (nparts) *nparts = grid.x * grid.y;
+  k_apply<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f, T* out, int dot,
+                         double* part, int* nparts, cudaStream_t s) {
+  switch (dx.p) {
+    case 1: return apply_p<T, 1>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 2: return apply_p<T, 2>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 4: return apply_p<T, 4>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 8: return apply_p<T, 8>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 16: return apply_p<T, 16>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 32: return apply_p<T, 32>(dx, dy, u, f, out, dot, part, nparts, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_apply<double>(const DirView<double>&, const DirView<double>&, const double*,
+                                          const double*, double*, int, double*, int*, cudaStream_t);
+template cudaError_t launch_apply<float>(const DirView<float>&, const DirView<float>&, const float*,
+                                         const float*, float*, int, double*, int*, cudaStream_t);
+
+cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f, double* b,
+                        double* part, int* nparts, cudaStream_t s) {
+  const int grid = 256;
+  if (nparts) *nparts = grid;
+  k_mass<<<grid, kRedThreads, 0, s>>>(dx, dy, f, b, part);
+  return cudaGetLastError();
+}
+
+}  // namespace sem

@@ -1,0 +1,87 @@
+// Host launchers of the CUDA kernels (one translation unit per kernel family).
+// Every launcher enqueues on `s` and returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sem {
+
+// Number of partial sums a reduction-producing launch writes (one per CTA).
+constexpr int kMaxPartials = 8192;
+
+// ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
+// out = A u (f == nullptr) or out = f - A u.  dot: 0 none, 1 part[cta] = sum
+// u.out, 2 part[cta] = sum out.out over the CTA's nodes.  *nparts receives
+// the number of partials written.
+template <typename T>
+cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f,
+                         T* out, int dot, double* part, int* nparts, cudaStream_t s);
+
+// b = (M_y (x) M_x) f_nodal, walls 0; part[cta] = sum of b (for the periodic
+// mean projection).
+cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f,
+                        double* b, double* part, int* nparts, cudaStream_t s);
+
+// ---- weighted additive Schwarz sweep (Alg. 2), k_schwarz.cu ---------------
+// E[s] = W_s A_ss^{-1} R_s r for every subdomain s (element-blocked m x m).
+// mode: 0 SIMT in T, 1 tensor cores TF32, 2 tensor cores BF16 (T = float).
+template <typename T, typename TIn>
+cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
+                         const float* nu_inv, cudaStream_t s);
+// u = (accum ? u : 0) + sum_s R_s^T E[s]  (deterministic node-centric sum).
+template <typename T, typename TOut>
+cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* E, TOut* u,
+                           bool accum, cudaStream_t s);
+
+// ---- grid transfer (Sec. 3.2), k_transfer.cu ------------------------------
+// fc = I^T rf from order pf to pf/2 on the same mesh (coarse walls 0).
+template <typename T>
+cudaError_t launch_restrict(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                            const DirView<T>& cy, const T* J, const T* rf, T* fc, cudaStream_t s);
+// out = in + I uc (in may alias out; in == nullptr means 0).
+template <typename T, typename TOut>
+cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                           const DirView<T>& cy, const T* J, const T* uc, const T* in, TOut* out,
+                           cudaStream_t s);
+
+// ---- coarse solve u0 = A_0^+ f0 by global fast diagonalisation ------------
+struct CoarseView {
+  int nux, nuy, firstx, firsty, Nx, Ny, periodic;
+  const double *Sx, *Sy, *lx, *ly, *cx, *cy;
+  double* T2;  // nuy x nux scratch
+};
+template <typename T>
+cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s);
+
+// ---- Krylov vector kernels (Alg. 4), k_krylov.cu -------------------------
+struct PcgState {
+  double* alpha;   // [i_max + 2] per-iteration scalars
+  double* beta;
+  double* delta;
+  double* pq;
+  double* rr;
+  int* flags;      // [0] done, [1] status
+  double* rmax;    // threshold on ||r||
+};
+int elementwise_grid(long n);
+cudaError_t launch_pcg_update_ur(long n, double* u, double* r, const double* p, const double* q,
+                                 const double* part_pq, int npq, PcgState st, int it, double* part_rr,
+                                 cudaStream_t s);
+cudaError_t launch_pcg_check(const double* part_rr, int nrr, PcgState st, int it, int i_max,
+                             cudaStream_t s);
+cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old,
+                        double* part, cudaStream_t s);
+cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
+                                const double* part, int np, PcgState st, int it, cudaStream_t s);
+cudaError_t launch_pcg_start(long n, const double* z, const double* r, double* p, double* r_old,
+                             const double* part_zr, int nzr, const double* part_rr, int nrr,
+                             PcgState st, double tol, cudaStream_t s);
+template <typename TA, typename TB>
+cudaError_t launch_convert(long n, const TA* a, TB* b, cudaStream_t s);
+cudaError_t launch_axpy(long n, double alpha, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_sub_mean(long n, double* b, const double* part, int np, cudaStream_t s);
+cudaError_t launch_norm2(long n, const double* x, double* part, cudaStream_t s);
+
+}  // namespace sem

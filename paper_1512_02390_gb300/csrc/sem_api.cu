@@ -1,0 +1,676 @@
+// C ABI of the GB300 Schwarz/multigrid spectral-element solver (include/sem_schwarz.h).
+//
+// A handle holds the level hierarchy p_l = 2^l, l = 0..L (Sec. 3.2), the
+// device tables built by the FP64 host set-up, the work vectors of every
+// level, and the FP64 vectors of the MGCG iteration (Alg. 4).  Every step of
+// the solve runs in the CUDA kernels of this library; the host only enqueues
+// launches and, once per MGCG iteration, reads the convergence flag.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "kernels.h"
+#include "sem_schwarz.h"
+#include "setup.h"
+
+using namespace sem;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return fail(SEM_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+struct Level {
+  int p = 0, n_o = 0, m = 0, Nx = 0, Ny = 0;
+  long nodes = 0;
+  DirView<double> x64{}, y64{};
+  DirView<float> x32{}, y32{};
+  double* J64 = nullptr;  // interpolation from level l-1 to l
+  float* J32 = nullptr;
+  void* u = nullptr;      // level vectors in the V-cycle type
+  void* f = nullptr;
+  void* r = nullptr;
+  void* E = nullptr;      // element-blocked Schwarz corrections
+};
+
+}  // namespace
+
+struct sem_handle {
+  sem_config cfg{};
+  int device = 0;
+  int L = 0;
+  bool mixed = false;
+  int sweep_mode = 0;
+  Mesh1D mx, my;
+  std::vector<Level> lev;
+  CoarseView coarse{};
+  std::vector<int> ns1, ns2;
+  long n = 0, n_unknowns = 0;
+  double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *r_old = nullptr;
+  double* part = nullptr;
+  PcgState st{};
+  int* flags_host = nullptr;
+  std::vector<double> xc, yc;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+int dev_alloc(sem_handle* h, T** ptr, size_t count) {
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SEM_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(d);
+  *ptr = static_cast<T*>(d);
+  return SEM_OK;
+}
+
+template <typename T, typename S>
+int upload(sem_handle* h, T** ptr, const std::vector<S>& v) {
+  std::vector<T> tmp(v.begin(), v.end());
+  int rc = dev_alloc(h, ptr, tmp.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(*ptr, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SEM_OK;
+}
+
+template <typename T>
+int upload_dir(sem_handle* h, const Dir1D& d, DirView<T>& v) {
+  v.p = d.p;
+  v.n = d.n;
+  v.N = d.N;
+  v.periodic = d.periodic ? 1 : 0;
+  v.n_o = d.n_o;
+  v.m = d.m;
+  std::vector<double> S, lam, w;
+  for (const auto& t : d.tables) {
+    S.insert(S.end(), t.S.begin(), t.S.end());
+    lam.insert(lam.end(), t.lam.begin(), t.lam.end());
+    w.insert(w.end(), t.w.begin(), t.w.end());
+  }
+  int rc;
+  T *Le, *Mg, *Sd, *ld, *wd;
+  int* tab;
+  if ((rc = upload(h, &Le, d.Le))) return rc;
+  if ((rc = upload(h, &Mg, d.Mglob))) return rc;
+  if ((rc = upload(h, &tab, d.tab))) return rc;
+  if ((rc = upload(h, &Sd, S))) return rc;
+  if ((rc = upload(h, &ld, lam))) return rc;
+  if ((rc = upload(h, &wd, w))) return rc;
+  v.Le = Le;
+  v.Mg = Mg;
+  v.tab = tab;
+  v.S = Sd;
+  v.lam = ld;
+  v.w = wd;
+  return SEM_OK;
+}
+
+int overlap_for(const sem_config& c, int pl) {
+  int n;
+  switch (c.overlap_rule) {
+    case SEM_OVERLAP_FIXED: n = c.overlap; break;
+    case SEM_OVERLAP_FLOOR8: n = pl / 8; break;
+    case SEM_OVERLAP_CEIL8: n = (pl + 7) / 8; break;
+    case SEM_OVERLAP_CEIL2: n = (pl + 1) / 2; break;
+    default: n = -1;
+  }
+  if (n < 0) return -1;
+  return std::min(n, pl - 1);
+}
+
+bool valid_weight(int w) {
+  return w == 1 || w == 3 || w == 5 || w == 7 || w == SEM_W_TOPHAT || w == SEM_W_ARITH || w == SEM_W_IDENTITY;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// ---- one level's smoothing (Alg. 2) --------------------------------------
+
+template <typename T>
+const DirView<T>& DX(const Level& l) {
+  if constexpr (std::is_same<T, double>::value) return l.x64; else return l.x32;
+}
+template <typename T>
+const DirView<T>& DY(const Level& l) {
+  if constexpr (std::is_same<T, double>::value) return l.y64; else return l.y32;
+}
+template <typename T>
+const T* JL(const Level& l) {
+  if constexpr (std::is_same<T, double>::value) return l.J64; else return l.J32;
+}
+
+// u = (accum ? u : 0) + sum_s R_s^T W A_ss^{-1} R_s r  (one additive sweep on r)
+template <typename T, typename TIn, typename TU>
+int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaStream_t s) {
+  T* E = static_cast<T*>(l.E);
+  CK((launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, nullptr, s)));
+  CK((launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
+  return SEM_OK;
+}
+
+// n Schwarz steps from u = 0: the first residual is f itself
+template <typename T>
+int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
+  if (n <= 0) {
+    CK(cudaMemsetAsync(u, 0, l.nodes * sizeof(T), s));
+    return SEM_OK;
+  }
+  int rc = sweep<T, T, T>(h, l, f, u, false, s);
+  if (rc) return rc;
+  T* r = static_cast<T*>(l.r);
+  for (int k = 1; k < n; ++k) {
+    CK(launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
+    if ((rc = sweep<T, T, T>(h, l, r, u, true, s))) return rc;
+  }
+  return SEM_OK;
+}
+
+template <typename T>
+int smooth(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
+  T* r = static_cast<T*>(l.r);
+  for (int k = 0; k < n; ++k) {
+    CK(launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
+    int rc = sweep<T, T, T>(h, l, r, u, true, s);
+    if (rc) return rc;
+  }
+  return SEM_OK;
+}
+
+// z = MultigridCycle(0, rtop), Alg. 3, with the level vectors in type T
+template <typename T>
+int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
+  const int L = h->L;
+  auto& lv = h->lev;
+  const T* fL;
+  T* uL;
+  if constexpr (std::is_same<T, double>::value) {
+    fL = rtop;
+    uL = zout;
+  } else {
+    CK((launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
+    fL = static_cast<const T*>(lv[L].f);
+    uL = static_cast<T*>(lv[L].u);
+  }
+  int rc;
+  for (int l = L; l >= 1; --l) {
+    const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
+    T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
+    if ((rc = smooth_from_zero<T>(h, lv[l], fl, ul, h->ns1[l], s))) return rc;
+    T* rl = static_cast<T*>(lv[l].r);
+    CK(launch_apply<T>(DX<T>(lv[l]), DY<T>(lv[l]), ul, fl, rl, 0, nullptr, nullptr, s));
+    CK(launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
+                          static_cast<T*>(lv[l - 1].f), s));
+  }
+  CK(launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
+  bool z_written = std::is_same<T, double>::value;
+  for (int l = 1; l <= L; ++l) {
+    const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
+    T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
+    const T* uc = static_cast<const T*>(lv[l - 1].u);
+    if (l == L && !z_written && h->ns2[l] == 0) {
+      CK((launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
+                                     uc, ul, zout, s)));
+      z_written = true;
+      continue;
+    }
+    CK((launch_prolong<T, T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc, ul,
+                              ul, s)));
+    if ((rc = smooth<T>(h, lv[l], fl, ul, h->ns2[l], s))) return rc;
+  }
+  if (!z_written) CK((launch_convert<float, double>(lv[L].nodes, static_cast<const float*>(lv[L].u), zout, s)));
+  return SEM_OK;
+}
+
+int precond(sem_handle* h, const double* r, double* z, cudaStream_t s) {
+  return h->mixed ? vcycle_z<float>(h, r, z, s) : vcycle_z<double>(h, r, z, s);
+}
+
+const Level& top(const sem_handle* h) { return h->lev[h->L]; }
+
+int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s) {
+  CK(launch_apply<double>(top(h).x64, top(h).y64, u, f, out, dot, h->part, np, s));
+  return SEM_OK;
+}
+
+int sync_flags(sem_handle* h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->flags_host, h->st.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SEM_OK;
+}
+
+int check_handle(const sem_handle* h) {
+  if (!h) return fail(SEM_BAD_ARG, "null handle");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) {
+    cudaGetLastError();
+    return fail(SEM_BAD_ARG, "the current CUDA device is not the handle's device");
+  }
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sem_default_config(sem_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->nx = c->ny = 4;
+  c->p = 4;
+  c->periodic = 0;
+  c->lx = c->ly = 1.0;
+  c->overlap_rule = SEM_OVERLAP_FIXED;
+  c->overlap = 1;
+  c->weight = SEM_W_QUINTIC;
+  c->ns1 = 1;
+  c->ns2 = 0;
+  c->variable_cycle = 0;
+  c->precision = SEM_PREC_FP64;
+  c->tol = 1e-10;
+  c->i_max = 200;
+}
+
+const char* sem_status_string(int32_t s) {
+  switch (s) {
+    case SEM_OK: return "SEM_OK";
+    case SEM_NOT_CONVERGED: return "SEM_NOT_CONVERGED";
+    case SEM_BREAKDOWN: return "SEM_BREAKDOWN";
+    case SEM_TIMEOUT: return "SEM_TIMEOUT";
+    case SEM_BAD_ARG: return "SEM_BAD_ARG";
+    case SEM_CUDA_ERROR: return "SEM_CUDA_ERROR";
+    case SEM_OOM: return "SEM_OOM";
+    default: return "unknown";
+  }
+}
+
+const char* sem_last_error(void) { return g_err.c_str(); }
+
+void sem_destroy(sem_handle* h) {
+  if (!h) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->flags_host) cudaFreeHost(h->flags_host);
+  if (prev >= 0) cudaSetDevice(prev);
+  cudaGetLastError();
+  delete h;
+}
+
+static int validate(const sem_config& c, int& L) {
+  L = 0;
+  while ((1 << L) < c.p) ++L;
+  if (c.p < 2 || c.p > 32 || (1 << L) != c.p) return fail(SEM_BAD_ARG, "p must be a power of two in [2, 32]");
+  if (c.nx < 2 || c.ny < 2 || c.nx > 4096 || c.ny > 4096) return fail(SEM_BAD_ARG, "nx, ny must be in [2, 4096]");
+  if (!valid_weight(c.weight)) return fail(SEM_BAD_ARG, "unknown weight function");
+  if (c.overlap_rule < 0 || c.overlap_rule > 3 || (c.overlap_rule == SEM_OVERLAP_FIXED && c.overlap < 0))
+    return fail(SEM_BAD_ARG, "invalid overlap rule");
+  if (c.precision < 0 || c.precision > 3) return fail(SEM_BAD_ARG, "invalid precision");
+  if (c.ns1 < 0 || c.ns2 < 0 || c.ns1 + c.ns2 < 1 || c.ns1 > 64 || c.ns2 > 64)
+    return fail(SEM_BAD_ARG, "need 0 <= ns1, ns2 <= 64 and ns1 + ns2 >= 1");
+  if (!(c.tol >= 0.0) || c.i_max < 1 || c.i_max > 100000) return fail(SEM_BAD_ARG, "invalid tol or i_max");
+  if (!c.x_edges && !(c.lx > 0)) return fail(SEM_BAD_ARG, "lx must be positive");
+  if (!c.y_edges && !(c.ly > 0)) return fail(SEM_BAD_ARG, "ly must be positive");
+  if (c.periodic && (c.nx + 1 > 1024 || c.ny > 65535)) return fail(SEM_BAD_ARG, "coarse grid too large");
+  if (!c.periodic && (c.nx - 1 > 1024)) return fail(SEM_BAD_ARG, "coarse grid too large");
+  return SEM_OK;
+}
+
+static bool make_mesh(int n, double len, const double* edges, bool periodic, Mesh1D& m) {
+  m.n = n;
+  m.periodic = periodic;
+  m.edges.resize(n + 1);
+  for (int i = 0; i <= n; ++i) m.edges[i] = edges ? edges[i] : len * i / n;
+  for (int i = 0; i < n; ++i)
+    if (!(m.edges[i + 1] > m.edges[i])) return false;
+  return true;
+}
+
+int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info, int32_t* tab_x, double* S_x,
+                      double* lam_x, double* w_x, double* coords_x) {
+  g_err.clear();
+  if (!cfg || !info) return fail(SEM_BAD_ARG, "null argument");
+  int L, rc;
+  if ((rc = validate(*cfg, L))) return rc;
+  if (level < 1 || level > L) return fail(SEM_BAD_ARG, "level must be in [1, L]");
+  Mesh1D mx;
+  if (!make_mesh(cfg->nx, cfg->lx, cfg->x_edges, cfg->periodic != 0, mx)) return fail(SEM_BAD_ARG, "mesh edges must increase");
+  const int p = 1 << level;
+  const int no = overlap_for(*cfg, p);
+  Dir1D d;
+  std::string err = build_dir(mx, p, no, cfg->weight, d);
+  if (!err.empty()) return fail(SEM_BAD_ARG, err);
+  info->p = p;
+  info->n_o = no;
+  info->m = d.m;
+  info->n_tables_x = (int)d.tables.size();
+  info->nx_nodes = d.N;
+  const int m = d.m;
+  for (size_t t = 0; t < d.tables.size(); ++t) {
+    if (S_x) std::memcpy(S_x + t * m * m, d.tables[t].S.data(), m * m * sizeof(double));
+    if (lam_x) std::memcpy(lam_x + t * m, d.tables[t].lam.data(), m * sizeof(double));
+    if (w_x) std::memcpy(w_x + t * m, d.tables[t].w.data(), m * sizeof(double));
+  }
+  if (tab_x)
+    for (int e = 0; e < d.n; ++e) tab_x[e] = d.tab[e];
+  if (coords_x) std::memcpy(coords_x, d.coords.data(), d.N * sizeof(double));
+  return SEM_OK;
+}
+
+int sem_create(const sem_config* cfg, sem_handle** out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(SEM_BAD_ARG, "null argument");
+  const sem_config& c = *cfg;
+  int L = 0;
+  {
+    int rc0 = validate(c, L);
+    if (rc0) return rc0;
+  }
+  auto mesh = make_mesh;
+  sem_handle* h = new sem_handle();
+  h->cfg = c;
+  h->cfg.x_edges = h->cfg.y_edges = nullptr;
+  if (!mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, h->mx) || !mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, h->my)) {
+    delete h;
+    return fail(SEM_BAD_ARG, "mesh edges must increase");
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(SEM_CUDA_ERROR, "no usable CUDA device");
+  }
+  h->L = L;
+  h->mixed = c.precision != SEM_PREC_FP64;
+  h->sweep_mode = c.precision == SEM_PREC_TF32 ? 1 : (c.precision == SEM_PREC_BF16 ? 2 : 0);
+  h->ns1.assign(L + 1, 0);
+  h->ns2.assign(L + 1, 0);
+  for (int l = 1; l <= L; ++l) {
+    const int f = c.variable_cycle ? (1 << (L - l)) : 1;
+    h->ns1[l] = c.ns1 * f;
+    h->ns2[l] = c.ns2 * f;
+  }
+  int rc = SEM_OK;
+  auto bail = [&](int code) {
+    sem_destroy(h);
+    return code;
+  };
+  const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+  h->lev.resize(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    Level& lv = h->lev[l];
+    lv.p = 1 << l;
+    lv.n_o = l > 0 ? overlap_for(c, lv.p) : 0;
+    lv.m = lv.p + 1 + 2 * lv.n_o;
+    Dir1D dx, dy;
+    std::string err = build_dir(h->mx, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dx);
+    if (err.empty()) err = build_dir(h->my, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dy);
+    if (!err.empty()) {
+      sem_destroy(h);
+      return fail(SEM_BAD_ARG, "level p=" + std::to_string(lv.p) + ": " + err);
+    }
+    lv.Nx = dx.N;
+    lv.Ny = dy.N;
+    lv.nodes = (long)dx.N * dy.N;
+    if ((rc = upload_dir(h, dx, lv.x64)) || (rc = upload_dir(h, dy, lv.y64)) || (rc = upload_dir(h, dx, lv.x32)) ||
+        (rc = upload_dir(h, dy, lv.y32)))
+      return bail(rc);
+    if (l > 0) {
+      std::vector<double> J;
+      interp_matrix(lv.p, lv.p / 2, J);
+      if ((rc = upload(h, &lv.J64, J)) || (rc = upload(h, &lv.J32, J))) return bail(rc);
+    }
+    if (l == L) {
+      h->xc = dx.coords;
+      h->yc = dy.coords;
+    }
+    char* b;
+    if ((rc = dev_alloc(h, &b, lv.nodes * tsz))) return bail(rc);
+    lv.u = b;
+    if ((rc = dev_alloc(h, &b, lv.nodes * tsz))) return bail(rc);
+    lv.f = b;
+    CK(cudaMemset(lv.u, 0, lv.nodes * tsz));
+    CK(cudaMemset(lv.f, 0, lv.nodes * tsz));
+    if (l > 0) {
+      if ((rc = dev_alloc(h, &b, lv.nodes * tsz))) return bail(rc);
+      lv.r = b;
+      if ((rc = dev_alloc(h, &b, (size_t)c.nx * c.ny * lv.m * lv.m * tsz))) return bail(rc);
+      lv.E = b;
+    }
+  }
+  // coarse factors
+  {
+    Coarse1D cx, cy;
+    std::string err = build_coarse(h->mx, cx);
+    if (err.empty()) err = build_coarse(h->my, cy);
+    if (!err.empty()) {
+      sem_destroy(h);
+      return fail(SEM_BAD_ARG, err);
+    }
+    CoarseView& cv = h->coarse;
+    cv.nux = cx.nu;
+    cv.nuy = cy.nu;
+    cv.firstx = cx.first;
+    cv.firsty = cy.first;
+    cv.Nx = h->lev[0].Nx;
+    cv.Ny = h->lev[0].Ny;
+    cv.periodic = c.periodic ? 1 : 0;
+    double *Sx, *Sy, *lx, *ly, *ccx, *ccy, *T2;
+    if ((rc = upload(h, &Sx, cx.S)) || (rc = upload(h, &Sy, cy.S)) || (rc = upload(h, &lx, cx.lam)) ||
+        (rc = upload(h, &ly, cy.lam)) || (rc = upload(h, &ccx, cx.c)) || (rc = upload(h, &ccy, cy.c)) ||
+        (rc = dev_alloc(h, &T2, (size_t)cx.nu * cy.nu)))
+      return bail(rc);
+    cv.Sx = Sx;
+    cv.Sy = Sy;
+    cv.lx = lx;
+    cv.ly = ly;
+    cv.cx = ccx;
+    cv.cy = ccy;
+    cv.T2 = T2;
+  }
+  // MGCG vectors, partial sums, per-iteration scalars
+  h->n = top(h).nodes;
+  h->n_unknowns = (long)(c.periodic ? h->mx.n * c.p : h->mx.n * c.p - 1) *
+                  (long)(c.periodic ? h->my.n * c.p : h->my.n * c.p - 1);
+  double** vecs[] = {&h->u, &h->r, &h->p, &h->q, &h->z, &h->r_old};
+  for (double** v : vecs) {
+    if ((rc = dev_alloc(h, v, h->n))) return bail(rc);
+    CK(cudaMemset(*v, 0, h->n * sizeof(double)));
+  }
+  if ((rc = dev_alloc(h, &h->part, 4 * kMaxPartials))) return bail(rc);
+  const int ni = c.i_max + 2;
+  double* sc;
+  if ((rc = dev_alloc(h, &sc, 5 * ni + 1))) return bail(rc);
+  CK(cudaMemset(sc, 0, (5 * ni + 1) * sizeof(double)));
+  h->st.alpha = sc;
+  h->st.beta = sc + ni;
+  h->st.delta = sc + 2 * ni;
+  h->st.pq = sc + 3 * ni;
+  h->st.rr = sc + 4 * ni;
+  h->st.rmax = sc + 5 * ni;
+  int* fl;
+  if ((rc = dev_alloc(h, &fl, 2))) return bail(rc);
+  h->st.flags = fl;
+  if (cudaMallocHost(&h->flags_host, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    h->flags_host = nullptr;
+    sem_destroy(h);
+    return fail(SEM_OOM, "cudaMallocHost failed");
+  }
+  CK(cudaDeviceSynchronize());
+  *out = h;
+  return SEM_OK;
+}
+
+int sem_sizes(const sem_handle* h, int64_t* n_unknowns, int64_t* nx_nodes, int64_t* ny_nodes) {
+  if (!h) return fail(SEM_BAD_ARG, "null handle");
+  if (n_unknowns) *n_unknowns = h->n_unknowns;
+  if (nx_nodes) *nx_nodes = top(h).Nx;
+  if (ny_nodes) *ny_nodes = top(h).Ny;
+  return SEM_OK;
+}
+
+int sem_coords(const sem_handle* h, double* x, double* y) {
+  if (!h) return fail(SEM_BAD_ARG, "null handle");
+  if (x) std::memcpy(x, h->xc.data(), h->xc.size() * sizeof(double));
+  if (y) std::memcpy(y, h->yc.data(), h->yc.size() * sizeof(double));
+  return SEM_OK;
+}
+
+int sem_mass(sem_handle* h, const double* f, double* b, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!f || !b) return fail(SEM_BAD_ARG, "null vector");
+  cudaStream_t s = as_stream(stream);
+  int np = 0;
+  CK(launch_mass(top(h).x64, top(h).y64, f, b, h->part, &np, s));
+  if (h->cfg.periodic) CK(launch_sub_mean(h->n, b, h->part, np, s));
+  return SEM_OK;
+}
+
+int sem_apply(sem_handle* h, const double* u, double* Au, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !Au) return fail(SEM_BAD_ARG, "null vector");
+  return apply64(h, u, nullptr, Au, 0, nullptr, as_stream(stream));
+}
+
+int sem_smooth(sem_handle* h, double* u, const double* f, int32_t n_it, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !f || n_it < 0) return fail(SEM_BAD_ARG, "invalid argument");
+  cudaStream_t s = as_stream(stream);
+  const Level& lv = top(h);
+  for (int k = 0; k < n_it; ++k) {
+    if ((rc = apply64(h, u, f, h->r, 0, nullptr, s))) return rc;
+    rc = h->mixed ? sweep<float, double, double>(h, lv, h->r, u, true, s)
+                  : sweep<double, double, double>(h, lv, h->r, u, true, s);
+    if (rc) return rc;
+  }
+  return SEM_OK;
+}
+
+int sem_vcycle(sem_handle* h, double* u, const double* f, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !f) return fail(SEM_BAD_ARG, "null vector");
+  cudaStream_t s = as_stream(stream);
+  // MultigridCycle(u, f) = u + MultigridCycle(0, f - A u): the cycle is affine
+  if ((rc = apply64(h, u, f, h->r, 0, nullptr, s))) return rc;
+  if ((rc = precond(h, h->r, h->z, s))) return rc;
+  CK(launch_axpy(h->n, 1.0, h->z, u, s));
+  return SEM_OK;
+}
+
+int sem_mg_solve(sem_handle* h, double* u, const double* f, sem_result* res, double* history, int32_t hlen,
+                 void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !f || !res) return fail(SEM_BAD_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  std::vector<double> part(kMaxPartials);
+  auto norm = [&](double& out) -> int {
+    int np = 0;
+    if ((rc = apply64(h, u, f, h->r, 2, &np, s))) return rc;
+    CK(cudaMemcpyAsync(part.data(), h->part, np * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double a = 0.0;
+    for (int i = 0; i < np; ++i) a += part[i];
+    out = std::sqrt(a);
+    return SEM_OK;
+  };
+  double r0, rn;
+  if ((rc = norm(r0))) return rc;
+  if (history && hlen > 0) history[0] = r0;
+  rn = r0;
+  int it = 0;
+  int status = SEM_NOT_CONVERGED;
+  if (!(r0 > 0)) status = std::isfinite(r0) ? SEM_OK : SEM_BREAKDOWN;
+  while (status == SEM_NOT_CONVERGED && it < h->cfg.i_max) {
+    if ((rc = precond(h, h->r, h->z, s))) return rc;
+    CK(launch_axpy(h->n, 1.0, h->z, u, s));
+    ++it;
+    if ((rc = norm(rn))) return rc;
+    if (history && it < hlen) history[it] = rn;
+    if (!std::isfinite(rn)) status = SEM_BREAKDOWN;
+    else if (rn <= h->cfg.tol * r0) status = SEM_OK;
+  }
+  res->iterations = it;
+  res->status = status;
+  res->res0 = r0;
+  res->res = rn;
+  res->rbar = (it > 0 && rn > 0) ? std::log10(r0 / rn) / it : 0.0;
+  return status;
+}
+
+int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, double* history, int32_t hlen,
+                  void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !f || !res) return fail(SEM_BAD_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  const long n = h->n;
+  const int G = elementwise_grid(n);
+  int np = 0;
+  // r = f - A u; rr_0
+  if ((rc = apply64(h, u, f, h->r, 2, &np, s))) return rc;
+  CK(cudaMemcpyAsync(h->part + 2 * kMaxPartials, h->part, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const int nrr0 = np;
+  // p = MG(0, r); delta = p.r
+  if ((rc = precond(h, h->r, h->z, s))) return rc;
+  CK(launch_dot2(n, h->z, h->r, h->r, h->part, s));
+  CK(launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, G, h->part + 2 * kMaxPartials, nrr0, h->st,
+                      h->cfg.tol, s));
+  if ((rc = sync_flags(h, s))) return rc;
+  int it = 0;
+  int status = h->flags_host[0] ? h->flags_host[1] : SEM_NOT_CONVERGED;
+  while (!h->flags_host[0]) {
+    ++it;
+    // q = A p, p.q
+    if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s))) return rc;
+    CK(launch_pcg_update_ur(n, u, h->r, h->p, h->q, h->part, np, h->st, it, h->part + kMaxPartials, s));
+    CK(launch_pcg_check(h->part + kMaxPartials, G, h->st, it, h->cfg.i_max, s));
+    if ((rc = sync_flags(h, s))) return rc;
+    if (h->flags_host[0]) {
+      status = h->flags_host[1];
+      break;
+    }
+    if ((rc = precond(h, h->r, h->z, s))) return rc;
+    CK(launch_dot2(n, h->z, h->r, h->r_old, h->part, s));
+    CK(launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, G, h->st, it, s));
+  }
+  std::vector<double> rr(it + 1);
+  CK(cudaMemcpyAsync(rr.data(), h->st.rr, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (history)
+    for (int i = 0; i <= it && i < hlen; ++i) history[i] = std::sqrt(rr[i]);
+  res->iterations = it;
+  res->status = status;
+  res->res0 = std::sqrt(rr[0]);
+  res->res = std::sqrt(rr[it]);
+  res->rbar = (it > 0 && rr[it] > 0) ? std::log10(std::sqrt(rr[0] / rr[it])) / it : 0.0;
+  return status;
+}
+
+}  // extern "C"

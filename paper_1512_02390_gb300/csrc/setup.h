@@ -1,0 +1,82 @@
+// Host-side FP64 set-up of the Schwarz/multigrid solver: 1D spectral basics
+// (Sec. 2), subdomain factors and weights (Sec. 3.1), interpolation and coarse
+// factors (Sec. 3.2).  Runs once per handle; the results are uploaded as small
+// device tables.
+#pragma once
+
+#include <string>
+#include <vector>
+
+namespace sem {
+
+struct Mesh1D {
+  int n = 0;                  // elements
+  bool periodic = false;
+  std::vector<double> edges;  // n + 1 increasing coordinates
+  double h(int e) const { return edges[e + 1] - edges[e]; }
+  int nodes(int p) const { return periodic ? n * p : n * p + 1; }
+  // neighbour of element e on side -1/+1; -1 at a Dirichlet wall
+  int neighbour(int e, int side) const {
+    int f = e + side;
+    if (f >= 0 && f < n) return f;
+    if (!periodic) return -1;
+    return (f % n + n) % n;
+  }
+};
+
+// GLL nodes and weights on [-1, 1] (Newton iteration on the Legendre recurrence).
+void gll(int p, std::vector<double>& xi, std::vector<double>& w);
+// D[i*(p+1) + j] = phi_j'(xi_i).
+void deriv_matrix(const std::vector<double>& xi, std::vector<double>& D);
+// Lagrange basis on nodes xi evaluated at points x: out[i*n + k] = phi_k(x_i).
+void lagrange_eval(const std::vector<double>& xi, const std::vector<double>& x,
+                   std::vector<double>& out);
+// 1D element mass (GLL diagonal, p+1) and stiffness ((p+1)^2) of width h.
+void element_matrices(int p, double h, std::vector<double>& M, std::vector<double>& L);
+// Symmetric-definite eigenproblem A s = lambda diag(b) s by cyclic Jacobi on
+// diag(b)^{-1/2} A diag(b)^{-1/2}.  S (n x n, row-major, columns = vectors with
+// S^T diag(b) S = I), lam ascending.  Returns false if Jacobi did not converge.
+bool gen_eig_diag(int n, const std::vector<double>& A, const std::vector<double>& b,
+                  std::vector<double>& S, std::vector<double>& lam);
+
+// Shape function phi_kappa of Eq. (shape function) for weight id kappa.
+double shape_phi(int kappa, double x);
+
+// Factors of the extended-element subdomains of one direction of one level,
+// padded to the interior window size m = p + 1 + 2 n_o.  Window slot a holds
+// element-local node k = a - n_o; slots outside the mesh (Dirichlet walls)
+// have zero rows in S, zero weight, and their eigen-slots carry lam = 1.
+struct SubTable {
+  std::vector<double> S;    // m x m, S[a*m + b] = b-th eigenvector at slot a
+  std::vector<double> lam;  // m
+  std::vector<double> w;    // m, 1D weights (Eq. (weight function))
+};
+
+struct Dir1D {
+  int n = 0, p = 0, n_o = 0, m = 0, N = 0;
+  bool periodic = false;
+  std::vector<double> Me;     // n x (p+1): element mass diagonals
+  std::vector<double> Le;     // n x (p+1)^2: element stiffness
+  std::vector<double> Mglob;  // N: assembled mass diagonal (walls included)
+  std::vector<double> coords; // N
+  std::vector<int> tab;       // n: subdomain table id per element
+  std::vector<SubTable> tables;
+};
+
+// Build one direction of one level.  weight: sem_weight id.  Returns "" or an
+// error message.
+std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& out);
+
+// Coarse (p = 1) factors: generalised eigenpairs of the assembled 1D pair over
+// the unknowns (Dirichlet: nodes 1..n-1; periodic: 0..n-1), and c = S^T 1.
+struct Coarse1D {
+  int nu = 0;                 // unknowns per direction
+  int first = 0;              // global index of the first unknown
+  std::vector<double> S, lam, c;
+};
+std::string build_coarse(const Mesh1D& mesh, Coarse1D& out);
+
+// Interpolation J[i*(pc+1) + k] = phi_k^{(pc)}(xi_i^{(pf)}).
+void interp_matrix(int pf, int pc, std::vector<double>& J);
+
+}  // namespace sem

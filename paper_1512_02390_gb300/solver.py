@@ -1,0 +1,78 @@
+"""Convenience wrapper around one sem_handle (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+
+_WEIGHTS = {1: B.SEM_W_LINEAR, 3: B.SEM_W_CUBIC, 5: B.SEM_W_QUINTIC, 7: B.SEM_W_SEPTIC,
+            "t": B.SEM_W_TOPHAT, "a": B.SEM_W_ARITH, "I": B.SEM_W_IDENTITY}
+_OVERLAP = {"floor8": B.SEM_OVERLAP_FLOOR8, "ceil8": B.SEM_OVERLAP_CEIL8, "ceil2": B.SEM_OVERLAP_CEIL2}
+_PREC = {"fp64": B.SEM_PREC_FP64, "fp32": B.SEM_PREC_FP32, "tf32": B.SEM_PREC_TF32, "bf16": B.SEM_PREC_BF16}
+
+
+def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weight=5, ns1=1, ns2=0,
+                variable_cycle=False, precision="fp64", tol=1e-10, i_max=200, x_edges=None, y_edges=None):
+    cfg = B.sem_default_config()
+    cfg.nx, cfg.ny, cfg.p, cfg.periodic = nx, ny, p, int(bool(periodic))
+    cfg.lx, cfg.ly = lx, ly
+    if isinstance(overlap, str):
+        cfg.overlap_rule, cfg.overlap = _OVERLAP[overlap], 0
+    else:
+        cfg.overlap_rule, cfg.overlap = B.SEM_OVERLAP_FIXED, int(overlap)
+    cfg.weight = _WEIGHTS[weight]
+    cfg.ns1, cfg.ns2, cfg.variable_cycle = ns1, ns2, int(bool(variable_cycle))
+    cfg.precision = _PREC[precision]
+    cfg.tol, cfg.i_max = tol, i_max
+    keep = []
+    for name, e in (("x_edges", x_edges), ("y_edges", y_edges)):
+        if e is not None:
+            arr = np.ascontiguousarray(e, dtype=np.float64)
+            keep.append(arr)
+            setattr(cfg, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    cfg._keep = keep  # keep edge arrays alive while the config is in use
+    return cfg
+
+
+class Solver:
+    """One solver handle on the current CUDA device."""
+
+    def __init__(self, **kw):
+        self.cfg = make_config(**kw)
+        self.h = B.sem_create(self.cfg)
+        self.n_unknowns, self.nx_nodes, self.ny_nodes = B.sem_sizes(self.h)
+        self.shape = (self.ny_nodes, self.nx_nodes)
+
+    def close(self):
+        if self.h is not None:
+            B.sem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coords(self):
+        return B.sem_coords(self.h)
+
+    def mass(self, f_nodal, b, stream=None):
+        B.sem_mass(self.h, f_nodal, b, stream)
+
+    def apply(self, u, Au, stream=None):
+        B.sem_apply(self.h, u, Au, stream)
+
+    def smooth(self, u, f, n_it=1, stream=None):
+        B.sem_smooth(self.h, u, f, n_it, stream)
+
+    def vcycle(self, u, f, stream=None):
+        B.sem_vcycle(self.h, u, f, stream)
+
+    def mg_solve(self, u, f, history_len=0, stream=None):
+        return B.sem_mg_solve(self.h, u, f, history_len, stream)
+
+    def pcg_solve(self, u, f, history_len=0, stream=None):
+        return B.sem_pcg_solve(self.h, u, f, history_len, stream)

@@ -1,0 +1,88 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/sem_schwarz.h declares, validates configurations, and its host FP64
+set-up tables (GLL coordinates, fast-diagonalisation factors, weights) agree
+with the oracle.  No GPU is needed; no kernel is launched."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import sem_oracle as O
+
+P = pytest.importorskip("paper_1512_02390_gb300")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(sem_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        return P.load_library()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    decl = _declared_symbols()
+    assert len(decl) >= 13
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert decl <= set(P.EXPORTS)
+
+
+def test_bad_configs_are_rejected_on_the_host(lib):
+    for kw in [dict(p=6), dict(p=64), dict(nx=1), dict(weight=2), dict(precision=9), dict(tol=-1.0)]:
+        cfg = P.sem_default_config()
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        with pytest.raises(P.SemError) as ei:
+            P.sem_inspect_level(cfg, 1)
+        assert ei.value.status == P.SEM_BAD_ARG
+
+
+def _oracle_level(periodic, nx, p, n_o, weight, edges=None, length=1.0):
+    mx = O.Mesh1D.uniform(nx, length, periodic) if edges is None else O.Mesh1D(np.asarray(edges), periodic)
+    return O.Level(mx, O.Mesh1D.uniform(3, 1.0, periodic), p, n_o, weight=weight)
+
+
+@pytest.mark.parametrize("periodic,nx,p,overlap,weight,edges", [
+    (False, 4, 4, 1, 5, None), (True, 8, 16, 2, 5, None), (False, 5, 8, 3, "a", None),
+    (False, 4, 32, 4, 7, None), (True, 6, 4, 1, "t", None), (False, 4, 8, 2, 3, [0.0, 0.1, 0.4, 0.45, 1.0]),
+    (False, 3, 2, 1, 1, None)])
+def test_host_tables_match_oracle(lib, periodic, nx, p, overlap, weight, edges):
+    cfg = P.make_config(nx=nx, ny=3, p=p, periodic=periodic, overlap=overlap, weight=weight, x_edges=edges)
+    L = int(np.log2(p))
+    t = P.sem_inspect_level(cfg, L)
+    lev = _oracle_level(periodic, nx, p, t["n_o"], weight, edges)
+    assert t["p"] == p and t["m"] == p + 1 + 2 * t["n_o"]
+    np.testing.assert_allclose(t["coords"], lev.mx.coords(p), atol=1e-14)
+    m, no = t["m"], t["n_o"]
+    for e in range(nx):
+        s = lev.sub_x[e]
+        slots = s.k + no
+        tid = t["tab"][e]
+        # weights over the valid window slots, zero elsewhere
+        w = np.zeros(m)
+        w[slots] = s.w
+        np.testing.assert_allclose(t["w"][tid], w, atol=1e-14)
+        # eigen-decomposition of the restricted pair: same spectrum, and the
+        # library's vectors diagonalise the oracle's restricted (L~, M~)
+        mv = len(slots)
+        np.testing.assert_allclose(t["lam"][tid][:mv], s.lam, rtol=1e-11, atol=1e-11 * s.lam.max())
+        Sv = t["S"][tid][slots][:, :mv]
+        Mt = np.diag(lev.Mx_glob[s.g])
+        Lt = lev.Lx_glob[np.ix_(s.g, s.g)]
+        np.testing.assert_allclose(Sv.T @ Mt @ Sv, np.eye(mv), atol=1e-11)
+        np.testing.assert_allclose(Sv.T @ Lt @ Sv, np.diag(s.lam), atol=1e-10 * s.lam.max())
+        # padding: zero rows outside the window, unit eigenvalue slots
+        pad = np.setdiff1d(np.arange(m), slots)
+        assert np.all(t["S"][tid][pad] == 0) and np.all(t["lam"][tid][mv:] == 1.0)
