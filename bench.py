@@ -1,0 +1,342 @@
+"""Benchmark: DOFs solved per second to a 1e-10 relative residual, mixed
+precision versus plain FP64, on the 64 x 64-element, p = 16 Dirichlet unit
+square (1,046,529 unknowns) with a seeded U[-1, 1] nodal right side, MGCG(1,0)
+with quintic weights (Alg. 4 preconditioned by Alg. 3 with Alg. 2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one complete sem_pcg_solve from u = 0 with the right side resident
+in device memory.  Steps are timed one by one with CUDA events on the solve's
+stream; L2 is flushed (512 MB write) between steps, outside the events.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOFs solved/s to 1e-10 rel. residual: mixed/learned vs plain FP64, same GB300"
+NX = NY = 64
+P_ORDER = 16
+N_O = 2
+SEED = 1
+TOL = 1e-10
+HEADLINE = "fp32"
+WORKLOAD = ("64x64 uniform elements, p=16, n_o=2 (also 1), Dirichlet unit square, seeded U[-1,1] RHS at the "
+            "GLL nodes (b = M f), MGCG(1,0) with w_5 weights from u=0 to ||r|| <= 1e-10 ||b||")
+
+# FP64 and FP32-SIMT peaks of GB300: nominal FP64 1.25 TFLOP/s; FP32 from the
+# unit counts 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_job(nx, ny, p, n_o, seed, tol, reps):
+    """Oracle MGCG solves of the workload in a single-threaded child process."""
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "from oracle import sem_oracle as O\n"
+        "import sem_inputs as SI\n"
+        "H = O.uniform_hierarchy(%d, %d, %d, periodic=False, overlap=%d, weight=5)\n"
+        "lev = H.top\n"
+        "f = lev.mass(SI.uniform_nodal(%d, (lev.NY, lev.NX), -1.0, 1.0))\n"
+        "ts = []\n"
+        "for _ in range(%d):\n"
+        "    t = time.perf_counter(); u, it, hist = H.mgcg(np.zeros_like(f), f, tol=%r); ts.append(time.perf_counter() - t)\n"
+        "print(json.dumps({'times': ts, 'iterations': it, 'unknowns': int(lev.unknown.sum())}))\n"
+    ) % (ROOT, nx, ny, p, n_o, seed, reps, tol)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _level_work(p, n_o_fixed, ne):
+    """Algorithmic flops per V-cycle launch per kernel class, summed over levels l >= 1."""
+    L = int(np.log2(p))
+    sweep_flops = 0.0
+    for l in range(1, L + 1):
+        pl = 2**l
+        no = min(n_o_fixed, pl - 1)
+        m = pl + 1 + 2 * no
+        sweep_flops += 8.0 * m**3 * ne  # four m^3 contractions per subdomain
+    return {"sweep_flops_per_cycle": sweep_flops, "sweep_launches_per_cycle": L}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec, n_o):
+        S = P.Solver(nx=NX, ny=NY, p=P_ORDER, overlap=n_o, weight=5, precision=prec, tol=TOL, i_max=100)
+        fn = SI.uniform_nodal(SEED + rank, S.shape)  # each replica solves its own problem
+        b = torch.empty(S.nx_nodes * S.ny_nodes, dtype=torch.float64, device="cuda")
+        S.mass(torch.from_numpy(fn.ravel()).cuda(), b)
+        return S, b
+
+    def timed(S, b, steps, warmup, profile=False):
+        u = torch.zeros_like(b)
+        res = None
+        for _ in range(warmup):
+            u.zero_()
+            res, _ = S.pcg_solve(u, b)
+        torch.cuda.synchronize()
+        S.profile(profile)
+        times = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            u.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, _ = S.pcg_solve(u, b)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return times, res, S.profile_read()
+
+    variants = {}
+    head = None
+    for prec, n_o in [("fp64", N_O), (HEADLINE, N_O), ("fp64", 1), (HEADLINE, 1)] + \
+            [(pr, N_O) for pr in ("fp32", "tf32", "bf16") if pr != HEADLINE]:
+        key = "%s_no%d" % (prec, n_o)
+        if key in variants:
+            continue
+        S, b = make(prec, n_o)
+        is_head = prec == HEADLINE and n_o == N_O
+        steps = args.steps if is_head or prec == "fp64" else max(3, min(args.steps, 5))
+        if is_head:
+            with ClockSampler(local) as clk:
+                times, res, prof = timed(S, b, steps, args.warmup)
+            clocks = clk.summary()
+        else:
+            times, res, prof = timed(S, b, steps, max(1, min(args.warmup, 3)))
+        ms = float(np.mean(times))
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
+                         "iterations": res.iterations, "status": res.status,
+                         "final_rel_residual": res.res / res.res0 if res.res0 else 0.0}
+        if is_head:
+            head = (S, b, times, res, prof, ms, clocks)
+        elif prec != HEADLINE:
+            S.close()
+    S, b, times, res, prof, ms, clocks = head
+
+    # kernels launched in the timed region (the library counts its launches)
+    gpu_launches = int(sum(c for _, c in prof.values()))
+
+    # e2e: host buffers through the public API, copies inside the timed region
+    bh = b.cpu().pin_memory()
+    uh = torch.empty_like(bh).pin_memory()
+    bd = torch.empty_like(b)
+    ud = torch.empty_like(b)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd.copy_(bh, non_blocking=True)
+        ud.zero_()
+        S.pcg_solve(ud, bd)
+        uh.copy_(ud, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_t.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_t))
+
+    # roofline of the dominant kernel class, from a profiled pass (same steps)
+    _, _, kprof = timed(S, b, args.steps, 1, profile=True)
+    S.profile(False)
+    dom = max(kprof, key=lambda k: kprof[k][0])
+    peaks, src = _peaks()
+    total_ms = sum(v[0] for v in kprof.values())
+    iters = res.iterations
+    ne = NX * NY
+    roof = None
+    if dom == "apply_fp64":
+        flops = (4 * (P_ORDER + 1) + 3) * S.n_unknowns * kprof[dom][1]
+        ach = flops / (kprof[dom][0] * 1e-3) / 1e12
+        roof = {"kernel": "k_apply<double,16> (q = A p, Eq. (system matrix))", "bound": "alu",
+                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "nominal FP64 rate of GB300"}
+    elif dom == "sweep":
+        w = _level_work(P_ORDER, N_O, ne)
+        cycles = kprof[dom][1] / w["sweep_launches_per_cycle"]
+        flops = w["sweep_flops_per_cycle"] * cycles
+        ach = flops / (kprof[dom][0] * 1e-3) / 1e12
+        pk = FP64_PEAK_TFLOPS if HEADLINE == "fp64" else FP32_PEAK_TFLOPS
+        roof = {"kernel": "k_sweep_simt (gather + FDM + weights, Alg. 2)", "bound": "alu", "achieved": ach,
+                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                "peak_source": "FP32 SIMT from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None}
+    roof["share_of_device_time"] = kprof[dom][0] / total_ms if total_ms else None
+    roof["class_ms"] = {k: round(v[0] / args.steps, 4) for k, v in kprof.items()}
+    roof["class_launches_per_step"] = {k: v[1] / args.steps for k, v in kprof.items()}
+
+    line = {
+        "metric": METRIC, "value": variants["%s_no%d" % (HEADLINE, N_O)]["dof_per_s"], "unit": "DOF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 outer MGCG + %s V-cycle" % HEADLINE, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": S.n_unknowns, "precision": HEADLINE, "n_o": N_O,
+                   "iterations": iters, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (512 MB write)", "seed": SEED},
+        "variants": variants,
+        "fp64_value": variants["fp64_no%d" % N_O]["dof_per_s"],
+        "speedup_vs_fp64": variants["%s_no%d" % (HEADLINE, N_O)]["dof_per_s"] / variants["fp64_no%d" % N_O]["dof_per_s"],
+        "e2e": {"value": world * S.n_unknowns / (e2e_ms * 1e-3), "unit": "DOF/s",
+                "h2d_bytes_per_step": int(b.numel() * 8), "d2h_bytes_per_step": int(b.numel() * 8)},
+        "gpu_launches": gpu_launches,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
+        line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                                "sample": "one full oracle MGCG solve of the same workload (%d iterations), "
+                                          "numpy FP64, single thread" % o["iterations"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, args.warmup + args.steps)
+    ts = o["times"][args.warmup:]
+    ms = 1e3 * float(np.mean(ts))
+    v = o["unknowns"] / (ms * 1e-3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": o["unknowns"], "iterations": o["iterations"]},
+        "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step one full oracle MGCG solve of the workload, numpy FP64, one thread"},
+        "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,29 @@ typedef struct sem_level_info {
 int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info, int32_t* tab_x,
                       double* S_x, double* lam_x, double* w_x, double* coords_x);
 
+/* Kernel classes of the tracing counters. */
+typedef enum sem_kernel_class {
+  SEM_K_APPLY_FP64 = 0, /* FP64 operator / residual on the finest level (Eq. (system matrix)) */
+  SEM_K_APPLY_MG = 1,   /* level residuals inside the V-cycle                               */
+  SEM_K_SWEEP = 2,      /* gather + FDM + weights of Alg. 2                                 */
+  SEM_K_SCATTER = 3,    /* R_s^T sum of Alg. 2                                              */
+  SEM_K_RESTRICT = 4,   /* I_l^T                                                            */
+  SEM_K_PROLONG = 5,    /* I_l                                                              */
+  SEM_K_COARSE = 6,     /* A_0^+ (two kernels per solve)                                    */
+  SEM_K_VECTOR = 7,     /* MGCG vector updates, dots, conversions                           */
+  SEM_K_NCLASS = 8
+} sem_kernel_class;
+
+/* Tracing.  sem_profile resets the per-class kernel-launch counters of the
+ * handle and switches CUDA-event timing of every launch on (enable = 1) or off
+ * (0).  With timing on, each launch is bracketed by two events on its stream
+ * (adds a little host overhead).  sem_profile_read (sync on the recorded
+ * events) fills ms[SEM_K_NCLASS] with the summed device time and
+ * launches[SEM_K_NCLASS] with the kernel counts since sem_profile; either
+ * pointer may be NULL (HOST arrays). */
+int sem_profile(sem_handle* h, int32_t enable);
+int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
+
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);
 

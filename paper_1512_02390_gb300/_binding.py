@@ -29,8 +29,10 @@ SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_TF32, SEM_PREC_BF16 = range(4)
 EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
-    "sem_inspect_level", "sem_status_string", "sem_last_error",
+    "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_status_string", "sem_last_error",
 ]
+# sem_kernel_class
+KERNEL_CLASSES = ["apply_fp64", "apply_mg", "sweep", "scatter", "restrict", "prolong", "coarse", "vector"]
 
 
 class sem_config(ctypes.Structure):
@@ -88,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_pcg_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), dp, i32, vp]),
         "sem_inspect_level": (i32, [ctypes.POINTER(sem_config), i32, ctypes.POINTER(sem_level_info),
                                     ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]),
+        "sem_profile": (i32, [vp, i32]),
+        "sem_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -226,3 +230,17 @@ def sem_inspect_level(cfg: sem_config, level: int):
                                  tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), d(S), d(lam), d(w), d(xc)))
     return dict(p=info.p, n_o=info.n_o, m=m, tab=tab, S=S.reshape(nt, m, m), lam=lam.reshape(nt, m),
                 w=w.reshape(nt, m), coords=xc)
+
+
+def sem_profile(h, enable: bool) -> None:
+    _check(load_library().sem_profile(h, int(bool(enable))))
+
+
+def sem_profile_read(h):
+    """{class: (ms, launches)} since the last sem_profile call."""
+    n = len(KERNEL_CLASSES)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(load_library().sem_profile_read(h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}

@@ -68,6 +68,12 @@ struct sem_handle {
   int* flags_host = nullptr;
   std::vector<double> xc, yc;
   std::vector<void*> allocs;
+  // tracing: launches per kernel class, optional CUDA-event timing
+  long long launches[SEM_K_NCLASS] = {};
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, end)
+  std::vector<int> ev_cls;
+  int ev_used = 0;
 };
 
 namespace {
@@ -145,6 +151,43 @@ bool valid_weight(int w) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+constexpr int kMaxEventPairs = 1 << 15;
+
+// kernels per launcher call of each class (the coarse solve is two kernels)
+int kernels_of(int cls) { return cls == SEM_K_COARSE ? 2 : 1; }
+
+void prof_begin(sem_handle* h, int cls, cudaStream_t s) {
+  h->launches[cls] += kernels_of(cls);
+  if (!h->prof || h->ev_used >= kMaxEventPairs) return;
+  if ((int)h->ev.size() < 2 * (h->ev_used + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      h->prof = false;
+      return;
+    }
+    h->ev.push_back(a);
+    h->ev.push_back(b);
+    h->ev_cls.push_back(cls);
+  }
+  h->ev_cls[h->ev_used] = cls;
+  cudaEventRecord(h->ev[2 * h->ev_used], s);
+}
+
+void prof_end(sem_handle* h, cudaStream_t s) {
+  if (!h->prof || h->ev_used >= kMaxEventPairs) return;
+  cudaEventRecord(h->ev[2 * h->ev_used + 1], s);
+  h->ev_used++;
+}
+
+// launch with tracing: count, and time with events when profiling is on
+#define KL(h, cls, s, call)        \
+  do {                             \
+    prof_begin((h), (cls), (s));   \
+    CK(call);                      \
+    prof_end((h), (s));            \
+  } while (0)
+
 // ---- one level's smoothing (Alg. 2) --------------------------------------
 
 template <typename T>
@@ -164,8 +207,8 @@ const T* JL(const Level& l) {
 template <typename T, typename TIn, typename TU>
 int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
-  CK((launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, nullptr, s)));
-  CK((launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, nullptr, s)));
+  KL(h, SEM_K_SCATTER, s, (launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
   return SEM_OK;
 }
 
@@ -180,7 +223,7 @@ int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cud
   if (rc) return rc;
   T* r = static_cast<T*>(l.r);
   for (int k = 1; k < n; ++k) {
-    CK(launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
+    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
     if ((rc = sweep<T, T, T>(h, l, r, u, true, s))) return rc;
   }
   return SEM_OK;
@@ -190,7 +233,7 @@ template <typename T>
 int smooth(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
   T* r = static_cast<T*>(l.r);
   for (int k = 0; k < n; ++k) {
-    CK(launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
+    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
     int rc = sweep<T, T, T>(h, l, r, u, true, s);
     if (rc) return rc;
   }
@@ -208,7 +251,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
     fL = rtop;
     uL = zout;
   } else {
-    CK((launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
+    KL(h, SEM_K_VECTOR, s, (launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
     fL = static_cast<const T*>(lv[L].f);
     uL = static_cast<T*>(lv[L].u);
   }
@@ -218,27 +261,27 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     if ((rc = smooth_from_zero<T>(h, lv[l], fl, ul, h->ns1[l], s))) return rc;
     T* rl = static_cast<T*>(lv[l].r);
-    CK(launch_apply<T>(DX<T>(lv[l]), DY<T>(lv[l]), ul, fl, rl, 0, nullptr, nullptr, s));
-    CK(launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
+    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(lv[l]), DY<T>(lv[l]), ul, fl, rl, 0, nullptr, nullptr, s));
+    KL(h, SEM_K_RESTRICT, s, launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
                           static_cast<T*>(lv[l - 1].f), s));
   }
-  CK(launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
+  KL(h, SEM_K_COARSE, s, launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
   bool z_written = std::is_same<T, double>::value;
   for (int l = 1; l <= L; ++l) {
     const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
     if (l == L && !z_written && h->ns2[l] == 0) {
-      CK((launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
+      KL(h, SEM_K_PROLONG, s, (launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
                                      uc, ul, zout, s)));
       z_written = true;
       continue;
     }
-    CK((launch_prolong<T, T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc, ul,
+    KL(h, SEM_K_PROLONG, s, (launch_prolong<T, T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc, ul,
                               ul, s)));
     if ((rc = smooth<T>(h, lv[l], fl, ul, h->ns2[l], s))) return rc;
   }
-  if (!z_written) CK((launch_convert<float, double>(lv[L].nodes, static_cast<const float*>(lv[L].u), zout, s)));
+  if (!z_written) KL(h, SEM_K_VECTOR, s, (launch_convert<float, double>(lv[L].nodes, static_cast<const float*>(lv[L].u), zout, s)));
   return SEM_OK;
 }
 
@@ -249,7 +292,7 @@ int precond(sem_handle* h, const double* r, double* z, cudaStream_t s) {
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
 
 int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s) {
-  CK(launch_apply<double>(top(h).x64, top(h).y64, u, f, out, dot, h->part, np, s));
+  KL(h, SEM_K_APPLY_FP64, s, launch_apply<double>(top(h).x64, top(h).y64, u, f, out, dot, h->part, np, s));
   return SEM_OK;
 }
 
@@ -313,6 +356,7 @@ void sem_destroy(sem_handle* h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->flags_host) cudaFreeHost(h->flags_host);
   if (prev >= 0) cudaSetDevice(prev);
   cudaGetLastError();
@@ -544,8 +588,8 @@ int sem_mass(sem_handle* h, const double* f, double* b, void* stream) {
   if (!f || !b) return fail(SEM_BAD_ARG, "null vector");
   cudaStream_t s = as_stream(stream);
   int np = 0;
-  CK(launch_mass(top(h).x64, top(h).y64, f, b, h->part, &np, s));
-  if (h->cfg.periodic) CK(launch_sub_mean(h->n, b, h->part, np, s));
+  KL(h, SEM_K_VECTOR, s, launch_mass(top(h).x64, top(h).y64, f, b, h->part, &np, s));
+  if (h->cfg.periodic) KL(h, SEM_K_VECTOR, s, launch_sub_mean(h->n, b, h->part, np, s));
   return SEM_OK;
 }
 
@@ -579,7 +623,7 @@ int sem_vcycle(sem_handle* h, double* u, const double* f, void* stream) {
   // MultigridCycle(u, f) = u + MultigridCycle(0, f - A u): the cycle is affine
   if ((rc = apply64(h, u, f, h->r, 0, nullptr, s))) return rc;
   if ((rc = precond(h, h->r, h->z, s))) return rc;
-  CK(launch_axpy(h->n, 1.0, h->z, u, s));
+  KL(h, SEM_K_VECTOR, s, launch_axpy(h->n, 1.0, h->z, u, s));
   return SEM_OK;
 }
 
@@ -609,7 +653,7 @@ int sem_mg_solve(sem_handle* h, double* u, const double* f, sem_result* res, dou
   if (!(r0 > 0)) status = std::isfinite(r0) ? SEM_OK : SEM_BREAKDOWN;
   while (status == SEM_NOT_CONVERGED && it < h->cfg.i_max) {
     if ((rc = precond(h, h->r, h->z, s))) return rc;
-    CK(launch_axpy(h->n, 1.0, h->z, u, s));
+    KL(h, SEM_K_VECTOR, s, launch_axpy(h->n, 1.0, h->z, u, s));
     ++it;
     if ((rc = norm(rn))) return rc;
     if (history && it < hlen) history[it] = rn;
@@ -639,8 +683,8 @@ int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, do
   const int nrr0 = np;
   // p = MG(0, r); delta = p.r
   if ((rc = precond(h, h->r, h->z, s))) return rc;
-  CK(launch_dot2(n, h->z, h->r, h->r, h->part, s));
-  CK(launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, G, h->part + 2 * kMaxPartials, nrr0, h->st,
+  KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r, h->part, s));
+  KL(h, SEM_K_VECTOR, s, launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, G, h->part + 2 * kMaxPartials, nrr0, h->st,
                       h->cfg.tol, s));
   if ((rc = sync_flags(h, s))) return rc;
   int it = 0;
@@ -649,16 +693,16 @@ int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, do
     ++it;
     // q = A p, p.q
     if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s))) return rc;
-    CK(launch_pcg_update_ur(n, u, h->r, h->p, h->q, h->part, np, h->st, it, h->part + kMaxPartials, s));
-    CK(launch_pcg_check(h->part + kMaxPartials, G, h->st, it, h->cfg.i_max, s));
+    KL(h, SEM_K_VECTOR, s, launch_pcg_update_ur(n, u, h->r, h->p, h->q, h->part, np, h->st, it, h->part + kMaxPartials, s));
+    KL(h, SEM_K_VECTOR, s, launch_pcg_check(h->part + kMaxPartials, G, h->st, it, h->cfg.i_max, s));
     if ((rc = sync_flags(h, s))) return rc;
     if (h->flags_host[0]) {
       status = h->flags_host[1];
       break;
     }
     if ((rc = precond(h, h->r, h->z, s))) return rc;
-    CK(launch_dot2(n, h->z, h->r, h->r_old, h->part, s));
-    CK(launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, G, h->st, it, s));
+    KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r_old, h->part, s));
+    KL(h, SEM_K_VECTOR, s, launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, G, h->st, it, s));
   }
   std::vector<double> rr(it + 1);
   CK(cudaMemcpyAsync(rr.data(), h->st.rr, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -671,6 +715,31 @@ int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, do
   res->res = std::sqrt(rr[it]);
   res->rbar = (it > 0 && rr[it] > 0) ? std::log10(std::sqrt(rr[0] / rr[it])) / it : 0.0;
   return status;
+}
+
+int sem_profile(sem_handle* h, int32_t enable) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  for (auto& c : h->launches) c = 0;
+  h->ev_used = 0;
+  h->prof = enable != 0;
+  return SEM_OK;
+}
+
+int sem_profile_read(sem_handle* h, double* ms, int64_t* launches) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (ms)
+    for (int c = 0; c < SEM_K_NCLASS; ++c) ms[c] = 0.0;
+  for (int k = 0; k < h->ev_used; ++k) {
+    CK(cudaEventSynchronize(h->ev[2 * k + 1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->ev[2 * k], h->ev[2 * k + 1]));
+    if (ms) ms[h->ev_cls[k]] += t;
+  }
+  if (launches)
+    for (int c = 0; c < SEM_K_NCLASS; ++c) launches[c] = h->launches[c];
+  return SEM_OK;
 }
 
 }  // extern "C"

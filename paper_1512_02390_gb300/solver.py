@@ -76,3 +76,9 @@ class Solver:
 
     def pcg_solve(self, u, f, history_len=0, stream=None):
         return B.sem_pcg_solve(self.h, u, f, history_len, stream)
+
+    def profile(self, enable=True):
+        B.sem_profile(self.h, enable)
+
+    def profile_read(self):
+        return B.sem_profile_read(self.h)

@@ -47,6 +47,14 @@ def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def _tol(H):
+    """FP64 bar for results that pass through the FDM: four length-m
+    contractions per output plus a residual summed in another order; their
+    rounding is bounded by eps * m^3 (m = window size of the finest level)."""
+    m = H.top.p + 1 + 2 * H.top.n_o
+    return max(1e-12, np.finfo(np.float64).eps * m**3)
+
+
 CASES = [
     dict(nx=4, ny=4, p=4),                                  # the 4x4, p = 4 Dirichlet unit square
     dict(nx=5, ny=3, p=4, overlap=2),                       # ragged tiles (5 is not a multiple of 8)
@@ -97,7 +105,7 @@ def test_schwarz_sweep_matches_oracle(case):
     ud = _dev(u0).reshape(-1)
     S.smooth(ud, _dev(f).reshape(-1), 2)
     want = lev.wschwarz(u0, f, 2)
-    assert _rel(_host(ud).reshape(lev.NY, lev.NX), want) < 1e-12
+    assert _rel(_host(ud).reshape(lev.NY, lev.NX), want) < _tol(H)
 
 
 @pytest.mark.parametrize("case", CASES, ids=_ids)
@@ -114,7 +122,7 @@ def test_vcycle_matches_oracle(case):
     got = _host(ud).reshape(lev.NY, lev.NX)
     if H.mx.periodic:  # periodic solutions are defined up to a constant
         got, want = got - got.mean(), want - want.mean()
-    assert _rel(got, want) < 1e-12
+    assert _rel(got, want) < _tol(H)
 
 
 def test_vcycle_with_post_smoothing_and_variable_cycle():
@@ -160,7 +168,7 @@ def test_pcg_matches_oracle(case):
     got = _host(ud).reshape(lev.NY, lev.NX)
     if H.mx.periodic:
         got, want = got - got.mean(), want - want.mean()
-    assert _rel(got, want) < 1e-12
+    assert _rel(got, want) < _tol(H)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
