@@ -231,5 +231,7 @@ def test_mg_solve_rate_matches_oracle():
     ud = _dev(u0).reshape(-1)
     res, hist = S.mg_solve(ud, _dev(f).reshape(-1), history_len=64)
     assert res.iterations == len(hist_o) - 1
-    np.testing.assert_allclose(hist, hist_o, rtol=1e-8)
+    # rounding of the residual itself is ~eps * ||A|| ||u||, so compare on the
+    # scale of the initial residual
+    np.testing.assert_allclose(hist, hist_o, rtol=1e-8, atol=1e-13 * hist_o[0])
     assert abs(res.rbar - 1.29) < 0.05  # Table 1, p = 8, w_5
