@@ -206,6 +206,46 @@ typedef enum sem_kernel_class {
 int sem_profile(sem_handle* h, int32_t enable);
 int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
 
+/* Allocation-free Schwarz correction.  The paper has no counterpart: this is a
+ * deployment variant of the correction step of Alg. 2,
+ *     u += sum_s R_s^T W A_ss^{-1} R_s r      (Eq. (correction:global)),
+ * for callers that cannot call cudaMalloc: code that runs inside a host
+ * framework which owns the device memory through its own pool and forbids
+ * other allocators, code with a fixed memory budget, and latency-critical
+ * loops in which cudaMalloc/cudaFree would synchronise the device.  It needs
+ * no sem_handle and allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call); the caller passes every input and output.
+ *
+ * Tables (one per direction, DEVICE arrays owned by the caller, in the layout
+ * sem_inspect_level reports for level log2(p)): tab[n] table id per element,
+ * S[tables * m * m], lam[tables * m], w[tables * m], m = p + 1 + 2 n_o.  The
+ * two directions must agree on p, n_o and periodic.  r and u are DEVICE node
+ * grids of (n_y p [+1]) x (n_x p [+1]) doubles as for the other calls; u is
+ * updated in place (async on `stream`).
+ *
+ * Scratch: the element-blocked corrections (n_x n_y m^2 doubles) live in one
+ * static device array of 2^21 doubles (16 MiB) that every GPU loading this
+ * library holds until the process exits.  Larger problems are rejected with
+ * SEM_BAD_ARG and a message giving the size needed.  The first call on a
+ * device (with that device current) looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (every entry a
+ * call reads is first written by the same call, so nothing needs clearing);
+ * calls that overlap on the GPU, e.g. on two streams at once, race on it.
+ * Errors: SEM_BAD_ARG, SEM_CUDA_ERROR (message in sem_last_error). */
+typedef struct sem_sweep_tables {
+  int32_t n;           /* elements in this direction                            */
+  int32_t p;           /* polynomial order (power of two in [2, 32])            */
+  int32_t n_o;         /* overlap layers, 0 <= n_o <= p - 1                     */
+  int32_t periodic;    /* 1 periodic, 0 Dirichlet walls                         */
+  const int32_t* tab;  /* DEVICE: n table ids                                   */
+  const double* S;     /* DEVICE: tables x m x m padded eigenvectors            */
+  const double* lam;   /* DEVICE: tables x m eigenvalues                        */
+  const double* w;     /* DEVICE: tables x m weights                            */
+} sem_sweep_tables;
+int sem_schwarz_correction_noalloc(const sem_sweep_tables* x, const sem_sweep_tables* y, const double* r,
+                                   double* u, void* stream);
+
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);
 

@@ -29,7 +29,8 @@ SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_TF32, SEM_PREC_BF16 = range(4)
 EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
-    "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_status_string", "sem_last_error",
+    "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
+    "sem_status_string", "sem_last_error",
 ]
 # sem_kernel_class
 KERNEL_CLASSES = ["apply_fp64", "apply_mg", "sweep", "scatter", "restrict", "prolong", "coarse", "vector"]
@@ -54,6 +55,11 @@ class sem_result(ctypes.Structure):
 class sem_level_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("n_o", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("n_tables_x", ctypes.c_int32), ("nx_nodes", ctypes.c_int32)]
+
+
+class sem_sweep_tables(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32), ("n_o", ctypes.c_int32), ("periodic", ctypes.c_int32),
+                ("tab", ctypes.c_void_p), ("S", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("w", ctypes.c_void_p)]
 
 
 class SemError(RuntimeError):
@@ -92,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]),
         "sem_profile": (i32, [vp, i32]),
         "sem_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "sem_schwarz_correction_noalloc": (i32, [ctypes.POINTER(sem_sweep_tables), ctypes.POINTER(sem_sweep_tables),
+                                                 vp, vp, vp]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -244,3 +252,9 @@ def sem_profile_read(h):
     _check(load_library().sem_profile_read(h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def sem_schwarz_correction_noalloc(tx: sem_sweep_tables, ty: sem_sweep_tables, r, u, stream=None) -> None:
+    """u += sum_s R_s^T W A_ss^{-1} R_s r without any allocation (see the C header for who needs this)."""
+    _check(load_library().sem_schwarz_correction_noalloc(ctypes.byref(tx), ctypes.byref(ty), _ptr(r), _ptr(u),
+                                                         _stream(stream)))

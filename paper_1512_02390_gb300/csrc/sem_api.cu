@@ -51,6 +51,11 @@ struct Level {
 
 }  // namespace
 
+namespace sem {
+// error message for sem_last_error from other translation units
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sem
+
 struct sem_handle {
   sem_config cfg{};
   int device = 0;
