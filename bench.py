@@ -192,8 +192,10 @@ def run_ours(args):
 
     variants = {}
     head = None
-    for prec, n_o in [("fp64", N_O), (HEADLINE, N_O), ("fp64", 1), (HEADLINE, 1)] + \
-            [(pr, N_O) for pr in ("fp32", "tf32", "bf16") if pr != HEADLINE]:
+    todo = [("fp64", N_O), (HEADLINE, N_O)]
+    if args.variants == "all":
+        todo += [("fp64", 1), (HEADLINE, 1)] + [(pr, N_O) for pr in ("fp32", "tf32", "bf16") if pr != HEADLINE]
+    for prec, n_o in todo:
         key = "%s_no%d" % (prec, n_o)
         if key in variants:
             continue
@@ -329,6 +331,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="all", choices=["all", "headline"],
+                    help="headline: time only the headline precision and the FP64 reference variant")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
