@@ -191,7 +191,7 @@ typedef enum sem_kernel_class {
   SEM_K_SCATTER = 3,    /* R_s^T sum of Alg. 2                                              */
   SEM_K_RESTRICT = 4,   /* I_l^T                                                            */
   SEM_K_PROLONG = 5,    /* I_l                                                              */
-  SEM_K_COARSE = 6,     /* A_0^+ (two kernels per solve)                                    */
+  SEM_K_COARSE = 6,     /* A_0^+ (four kernels per solve)                                   */
   SEM_K_VECTOR = 7,     /* MGCG vector updates, dots, conversions                           */
   SEM_K_NCLASS = 8
 } sem_kernel_class;

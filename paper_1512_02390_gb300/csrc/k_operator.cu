@@ -7,6 +7,8 @@
 // element interface.  A CTA owns a tile of TE x TE elements (32 x 32 nodes),
 // stages the tile plus one element of halo on the low side in shared memory,
 // and writes every owned node exactly once: no atomics, deterministic.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace sem {
@@ -122,6 +124,168 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
   }
 }
 
+// Even-odd variant of the same operator.  The 1D element stiffness of GLL
+// collocation is centro-symmetric, L[p-a][p-b] = L[a][b] (D[p-i][p-j] = -D[i][j]
+// and w_{p-q} = w_q), so the element-row product y = L x splits into
+//   e_k = x_k + x_{p-k},  o_k = x_k - x_{p-k}   (k < p/2),  e_{p/2} = x_{p/2}
+//   ye_a = sum_{k<=p/2} E[a][k] e_k,  yo_a = sum_{k<p/2} O[a][k] o_k
+//   y_a = ye_a + yo_a,  y_{p-a} = ye_a - yo_a
+// with E[a][k] = (L[a][k] + L[a][p-k]) / 2 (E[a][p/2] = L[a][p/2]) and
+// O[a][k] = (L[a][k] - L[a][p-k]) / 2: (p/2+1)^2 + (p/2)^2 FMAs per element
+// row instead of (p+1)^2.  This halves the work of the FP64 operator, which is
+// bound by the FP64 pipe on GB300.  Phases per CTA: build E/O of the tile's
+// elements; x-products of every owned row (one thread per (a, row), rows
+// across the warp so E/O are broadcast); y-products of every owned column;
+// combine with the mass diagonals.
+template <int P>
+struct EOTile {
+  static constexpr int H = P / 2;
+  static constexpr int TE = Tile<P>::TE, TN = Tile<P>::TN, LN = Tile<P>::LN, NP = P + 1;
+  static constexpr int LP = LN | 1;                       // odd pitch: conflict-free column reads
+  static constexpr int NE = (H + 1) * (H + 1), NO = H * H;  // E and O table sizes
+  static constexpr int EO = NE + NO;
+};
+
+template <typename T, int P>
+size_t apply_eo_smem() {
+  using Q = EOTile<P>;
+  const size_t t = (size_t)Q::LN * Q::LP                 // staged u
+                   + 2 * (Q::TE + 1) * Q::EO                // E/O per element, x and y
+                   + 2 * (size_t)Q::TN * (Q::TE + 1) * Q::NP  // element-local row / column products
+                   + 2 * (Q::TN + 1);                      // mass diagonals
+  return sizeof(T) * t + sizeof(double) * kRedThreads;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
+                                                  const T* __restrict__ f, T* __restrict__ out, int dot,
+                                                  double* __restrict__ part) {
+  using Q = EOTile<P>;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);   // LN x LP
+  T* eox = su + LN * LP;                      // (TE+1) x EO
+  T* eoy = eox + (TE + 1) * EO;
+  T* xb = eoy + (TE + 1) * EO;                // [row 0..TN) [slot 0..TE] [a 0..P]  x-products
+  T* yb = xb + TN * (TE + 1) * NP;            // [slot 0..TE] [b 0..P] [col 0..TN)  y-products
+  T* sMx = yb + TN * (TE + 1) * NP;
+  T* sMy = sMx + (TN + 1);
+  double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
+
+  const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
+  const int Nx = dx.N, Ny = dy.N;
+  const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic);
+    su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
+  }
+  // E/O tables of slot s = element ex0 + s - 1 (slot 0: low-side neighbour)
+  for (int idx = threadIdx.x; idx < 2 * (TE + 1) * EO; idx += blockDim.x) {
+    const int dir = idx / ((TE + 1) * EO);
+    const int rem = idx - dir * (TE + 1) * EO;
+    const int sl = rem / EO, t = rem - sl * EO;
+    const DirView<T>& d = dir ? dy : dx;
+    int e = (dir ? ey0 : ex0) + sl - 1;
+    if (d.periodic) e = (e + d.n) % d.n;
+    T v = T(0);
+    if (e >= 0 && e < d.n) {
+      const T* L = d.Le + (long)e * NP * NP;
+      if (t < NE) {
+        const int a = t / (H + 1), k = t - a * (H + 1);
+        v = (k == H) ? L[a * NP + H] : T(0.5) * (L[a * NP + k] + L[a * NP + P - k]);
+      } else {
+        const int a = (t - NE) / H, k = (t - NE) - a * H;
+        v = T(0.5) * (L[a * NP + k] - L[a * NP + P - k]);
+      }
+    }
+    (dir ? eoy : eox)[sl * EO + t] = v;
+  }
+  for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
+    const int gx = ex0 * P + idx, gy = ey0 * P + idx;
+    sMx[idx] = gx < Nx ? dx.Mg[gx] : T(0);
+    sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
+  }
+  __syncthreads();
+
+  // x products: item (slot, a, row); slot 0 needs only a = 0 (its y_P)
+  constexpr int XI = TN * (1 + TE * (H + 1));
+  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
+    const int row = idx % TN;
+    const int q = idx / TN;  // 0: slot 0 / a 0; then (slot, a) pairs
+    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
+    const int a = q == 0 ? 0 : (q - 1) % (H + 1);
+    const T* x = su + (row + P) * LP + sl * P;  // element-local node 0 of this slot
+    const T* E = eox + sl * EO + a * (H + 1);
+    const T* O = eox + sl * EO + NE + min(a, H - 1) * H;  // row a = H of O is zero, not stored
+    T ye = E[H] * x[H], yo = T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const T xk = x[k], xm = x[P - k];
+      ye += E[k] * (xk + xm);
+      yo += O[k] * (xk - xm);
+    }
+    if (a == H) yo = T(0);
+    T* dst = xb + (row * (TE + 1) + sl) * NP;
+    if (a < H) dst[P - a] = ye - yo;
+    dst[a] = ye + yo;
+  }
+  // y products: item (slot, b, col)
+  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
+    const int col = idx % TN;
+    const int q = idx / TN;
+    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
+    const int b = q == 0 ? 0 : (q - 1) % (H + 1);
+    const T* x = su + (sl * P) * LP + col + P;
+    const T* E = eoy + sl * EO + b * (H + 1);
+    const T* O = eoy + sl * EO + NE + min(b, H - 1) * H;
+    T ye = E[H] * x[H * LP], yo = T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const T xk = x[k * LP], xm = x[(P - k) * LP];
+      ye += E[k] * (xk + xm);
+      yo += O[k] * (xk - xm);
+    }
+    if (b == H) yo = T(0);
+    T* dst = yb + (sl * NP) * TN + col;
+    if (b < H) dst[(P - b) * TN] = ye - yo;
+    dst[b * TN] = ye + yo;
+  }
+  __syncthreads();
+
+  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
+  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
+    const int gi = ex0 * P + ix, gj = ey0 * P + jy;
+    const long o = (long)gj * Nx + gi;
+    const bool wall = (!dx.periodic && (gi == 0 || gi == Nx - 1)) || (!dy.periodic && (gj == 0 || gj == Ny - 1));
+    T val = T(0);
+    if (!wall) {
+      const int lex = ix / P, a = ix - lex * P;
+      const int ley = jy / P, b = jy - ley * P;
+      const T* xr = xb + (jy * (TE + 1) + lex + 1) * NP;
+      T xs = xr[a];
+      if (a == 0) xs += xr[P - NP];  // y_P of the left slot
+      const T* yc = yb + ((ley + 1) * NP) * TN + ix;
+      T ys = yc[b * TN];
+      if (b == 0) ys += yc[(P - NP) * TN];
+      val = sMy[jy] * xs + sMx[ix] * ys;
+      if (f) val = f[o] - val;
+    }
+    out[o] = val;
+    if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
+    else if (dot == 2) acc += (double)val * (double)val;
+  }
+  if (dot) {
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double> dy, const double* __restrict__ f,
                                                double* __restrict__ b, double* __restrict__ part) {
   __shared__ double sred[kRedThreads];
@@ -142,13 +306,20 @@ template <typename T, int P>
 cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f, T* out, int dot,
                     double* part, int* nparts, cudaStream_t s) {
   using Tl = Tile<P>;
-  const size_t sm = apply_smem<T, P>();
-  cudaError_t e = allow_smem(k_apply<T, P>, sm);
-  if (e != cudaSuccess) return e;
   dim3 grid((dx.n + Tl::TE - 1) / Tl::TE, (dy.n + Tl::TE - 1) / Tl::TE);
   if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
   if (nparts) *nparts = grid.x * grid.y;
-  k_apply<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+  if constexpr (std::is_same<T, double>::value && P >= 4) {
+    const size_t sm = apply_eo_smem<T, P>();
+    cudaError_t e = allow_smem(k_apply_eo<T, P>, sm);
+    if (e != cudaSuccess) return e;
+    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+  } else {
+    const size_t sm = apply_smem<T, P>();
+    cudaError_t e = allow_smem(k_apply<T, P>, sm);
+    if (e != cudaSuccess) return e;
+    k_apply<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+  }
   return cudaGetLastError();
 }
 

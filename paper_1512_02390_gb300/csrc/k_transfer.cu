@@ -150,64 +150,80 @@ __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, D
   }
 }
 
-// Coarse step 1, one CTA per eigen-row a:
-// T2[a][b] = (sum_j S_y[j][a] (F - mu)[j][.]) S_x[.][b] / (lam_y[a] + lam_x[b]).
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_a(CoarseView c, const T* __restrict__ f0) {
-  __shared__ double srow[1024];
-  __shared__ double sred[kRedThreads];
-  const int a = blockIdx.x;
-  double mu = 0.0;
-  if (c.periodic) {
-    double acc = 0.0;
-    for (int idx = threadIdx.x; idx < c.nux * c.nuy; idx += blockDim.x) {
-      const int j = idx / c.nux, i = idx - j * c.nux;
-      acc += (double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i];
-    }
-    mu = block_sum(acc, sred) / ((double)c.nux * c.nuy);
-  }
-  for (int i = threadIdx.x; i < c.nux; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < c.nuy; ++j)
-      s += c.Sy[j * c.nuy + a] * ((double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i] - mu);
-    srow[i] = s;
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < c.nux; b += blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < c.nux; ++i) s += srow[i] * c.Sx[i * c.nux + b];
-    const bool null_pair = c.periodic && a == 0 && b == 0;
-    c.T2[(long)a * c.nux + b] = null_pair ? 0.0 : s / (c.ly[a] + c.lx[b]);
-  }
-}
+// Coarse solve as four small FP64 products over the unknowns (F: nuy x nux):
+//   T1 = S_y^T (F - mu),  T2 = (T1 S_x) ./ (lam_y + lam_x^T),  T3 = S_y T2,
+//   U  = T3 S_x^T - mean(U)
+// (mu, the mean and the dropped (0,0) pair only for the periodic, singular
+// A_0).  One generic kernel: a CTA computes an 8 x 8 output tile with the
+// reduction dimension split over 4 thread groups (256 threads), so ~64 CTAs
+// share the FP64 work of a 63^3 product instead of one CTA per row.
+enum CoarseStep { kStep1 = 0, kStep2 = 1, kStep3 = 2, kStep4 = 3 };
 
-// Coarse step 2, one CTA per output row j: U[j][.] = (sum_a S_y[j][a] T2[a][.]) S_x^T,
-// minus the mean of U for the periodic case.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_b(CoarseView c, T* __restrict__ u0) {
-  __shared__ double srow[1024];
+__global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, const T* __restrict__ f0,
+                                                     T* __restrict__ u0) {
+  constexpr int TM = 8, TK = 4;
   __shared__ double sred[kRedThreads];
-  const int j = blockIdx.x;
-  double mean = 0.0;
-  if (c.periodic) {
-    // mean(U) = (c_y^T T2 c_x) / N with c = S^T 1
+  __shared__ double part[TK][TM][TM + 1];
+  const int nux = c.nux, nuy = c.nuy;
+  // output shape: steps 1-3 produce nuy x nux (a or j rows, i or b columns)
+  const int rows = nuy, cols = nux;
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TM;
+  const int t = threadIdx.x, kg = t / (TM * TM), rr = (t / TM) % TM, cc = t % TM;
+  const int row = r0 + rr, col = c0 + cc;
+  double shift = 0.0;
+  if (c.periodic && (step == kStep1 || step == kStep4)) {
     double acc = 0.0;
-    for (int idx = threadIdx.x; idx < c.nux * c.nuy; idx += blockDim.x) {
-      const int a = idx / c.nux, b = idx - a * c.nux;
-      acc += c.cy[a] * c.T2[idx] * c.cx[b];
+    if (step == kStep1) {
+      for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
+        const int j = idx / nux, i = idx - j * nux;
+        acc += (double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i];
+      }
+    } else {  // mean(U) = c_y^T T2 c_x / N (T2 is intact: step 3 wrote T1)
+      for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
+        const int a = idx / nux, b = idx - a * nux;
+        acc += c.cy[a] * c.T2[idx] * c.cx[b];
+      }
     }
-    mean = block_sum(acc, sred) / ((double)c.nux * c.nuy);
+    shift = block_sum(acc, sred) / ((double)nux * nuy);
   }
-  for (int b = threadIdx.x; b < c.nux; b += blockDim.x) {
-    double s = 0.0;
-    for (int a = 0; a < c.nuy; ++a) s += c.Sy[j * c.nuy + a] * c.T2[(long)a * c.nux + b];
-    srow[b] = s;
+  // reduction length: steps 1 and 3 contract over y (nuy), steps 2 and 4 over x (nux)
+  const int K = (step == kStep1 || step == kStep3) ? nuy : nux;
+  double s = 0.0;
+  if (row < rows && col < cols) {
+    for (int k = kg; k < K; k += TK) {
+      double a, b;
+      switch (step) {
+        case kStep1:  // T1[a][i] = sum_j S_y[j][a] (F[j][i] - mu)
+          a = c.Sy[k * nuy + row];
+          b = (double)f0[(long)(c.firsty + k) * c.Nx + c.firstx + col] - shift;
+          break;
+        case kStep2:  // T2[a][b] = sum_i T1[a][i] S_x[i][b]
+          a = c.T1[(long)row * nux + k];
+          b = c.Sx[k * nux + col];
+          break;
+        case kStep3:  // T3[j][b] = sum_a S_y[j][a] T2[a][b]
+          a = c.Sy[row * nuy + k];
+          b = c.T2[(long)k * nux + col];
+          break;
+        default:      // U[j][i] = sum_b T3[j][b] S_x[i][b]
+          a = c.T1[(long)row * nux + k];
+          b = c.Sx[col * nux + k];
+      }
+      s += a * b;
+    }
   }
+  part[kg][rr][cc] = s;
   __syncthreads();
-  for (int i = threadIdx.x; i < c.nux; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < c.nux; ++b) s += srow[b] * c.Sx[i * c.nux + b];
-    u0[(long)(c.firsty + j) * c.Nx + c.firstx + i] = T(s - mean);
+  if (kg == 0 && row < rows && col < cols) {
+    double v = part[0][rr][cc] + part[1][rr][cc] + part[2][rr][cc] + part[3][rr][cc];
+    const long o = (long)row * nux + col;
+    switch (step) {
+      case kStep1: c.T1[o] = v; break;
+      case kStep2: c.T2[o] = (c.periodic && row == 0 && col == 0) ? 0.0 : v / (c.ly[row] + c.lx[col]); break;
+      case kStep3: c.T1[o] = v; break;  // T3 reuses the T1 buffer
+      default: u0[(long)(c.firsty + row) * c.Nx + c.firstx + col] = T(v - shift);
+    }
   }
 }
 
@@ -267,12 +283,13 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s) {
-  if (c.nux > 1024 || c.nuy > 65535) return cudaErrorInvalidValue;
-  k_coarse_a<T><<<c.nuy, 256, 0, s>>>(c, f0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_coarse_b<T><<<c.nuy, 256, 0, s>>>(c, u0);
-  return cudaGetLastError();
+  dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8);
+  for (int step = kStep1; step <= kStep4; ++step) {
+    k_coarse_gemm<T><<<grid, 256, 0, s>>>(c, step, f0, u0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_restrict<double>(const DirView<double>&, const DirView<double>&, const DirView<double>&,

@@ -50,6 +50,7 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 struct CoarseView {
   int nux, nuy, firstx, firsty, Nx, Ny, periodic;
   const double *Sx, *Sy, *lx, *ly, *cx, *cy;
+  double* T1;  // nuy x nux scratch (also holds S_y T2)
   double* T2;  // nuy x nux scratch
 };
 template <typename T>

@@ -159,7 +159,7 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 constexpr int kMaxEventPairs = 1 << 15;
 
 // kernels per launcher call of each class (the coarse solve is two kernels)
-int kernels_of(int cls) { return cls == SEM_K_COARSE ? 2 : 1; }
+int kernels_of(int cls) { return cls == SEM_K_COARSE ? 4 : 1; }
 
 void prof_begin(sem_handle* h, int cls, cudaStream_t s) {
   h->launches[cls] += kernels_of(cls);
@@ -525,11 +525,12 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     cv.Nx = h->lev[0].Nx;
     cv.Ny = h->lev[0].Ny;
     cv.periodic = c.periodic ? 1 : 0;
-    double *Sx, *Sy, *lx, *ly, *ccx, *ccy, *T2;
+    double *Sx, *Sy, *lx, *ly, *ccx, *ccy, *T1, *T2;
     if ((rc = upload(h, &Sx, cx.S)) || (rc = upload(h, &Sy, cy.S)) || (rc = upload(h, &lx, cx.lam)) ||
         (rc = upload(h, &ly, cy.lam)) || (rc = upload(h, &ccx, cx.c)) || (rc = upload(h, &ccy, cy.c)) ||
-        (rc = dev_alloc(h, &T2, (size_t)cx.nu * cy.nu)))
+        (rc = dev_alloc(h, &T1, (size_t)cx.nu * cy.nu)) || (rc = dev_alloc(h, &T2, (size_t)cx.nu * cy.nu)))
       return bail(rc);
+    cv.T1 = T1;
     cv.Sx = Sx;
     cv.Sy = Sy;
     cv.lx = lx;
