@@ -125,6 +125,24 @@ def test_vcycle_matches_oracle(case):
     assert _rel(got, want) < _tol(H)
 
 
+@pytest.mark.parametrize("prec,u_in", [("fp32", 2.0**-24), ("tf32", 2.0**-11), ("bf16", 2.0**-8)])
+@pytest.mark.parametrize("case", [dict(nx=5, ny=4, p=16, overlap=2), dict(nx=4, ny=4, p=8, periodic=True, overlap=1),
+                                  dict(nx=3, ny=3, p=32, overlap=4), dict(nx=6, ny=3, p=4, overlap=1)], ids=_ids)
+def test_reduced_precision_sweep_matches_oracle(case, prec, u_in):
+    """One Schwarz correction from u = 0 in FP32 SIMT or on the tensor cores
+    (TF32 / BF16 operands, FP32 accumulation).  Four contractions each round
+    their operands once (unit roundoff u_in); with orthonormal-like S the
+    error stays within 64 u_in of max|correction|."""
+    S, H = _pair(precision=prec, **case)
+    lev = H.top
+    f = lev.mass(SI.uniform_nodal(12, (lev.NY, lev.NX)))
+    ud = torch.zeros(lev.NY * lev.NX, dtype=torch.float64, device="cuda")
+    S.smooth(ud, _dev(f).reshape(-1), 1)
+    want = lev.wschwarz(np.zeros_like(f), f, 1)
+    err = _rel(_host(ud).reshape(lev.NY, lev.NX), want)
+    assert err < 64 * u_in, err
+
+
 def test_vcycle_with_post_smoothing_and_variable_cycle():
     S, H = _pair(nx=4, ny=4, p=8, overlap=2, ns1=1, ns2=1, variable_cycle=True)
     lev = H.top
