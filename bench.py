@@ -209,6 +209,9 @@ def run_ours(args):
         else:
             times, res, prof = timed(S, b, steps, max(1, min(args.warmup, 3)))
         ms = float(np.mean(times))
+        if not is_head:
+            _, _, vprof = timed(S, b, 2, 0, profile=True)
+            S.profile(False)
         if dist:
             t = torch.tensor([ms], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -216,6 +219,8 @@ def run_ours(args):
         variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
                          "iterations": res.iterations, "status": res.status,
                          "final_rel_residual": res.res / res.res0 if res.res0 else 0.0}
+        if not is_head:
+            variants[key]["class_ms_per_solve"] = {k: round(v[0] / 2, 4) for k, v in vprof.items()}
         if is_head:
             head = (S, b, times, res, prof, ms, clocks)
         elif prec != HEADLINE:

@@ -141,19 +141,84 @@ template <int P>
 struct EOTile {
   static constexpr int H = P / 2;
   static constexpr int TE = Tile<P>::TE, TN = Tile<P>::TN, LN = Tile<P>::LN, NP = P + 1;
-  static constexpr int LP = LN | 1;                       // odd pitch: conflict-free column reads
+  static constexpr int LP = LN | 1;                         // odd pitch: conflict-free column reads
   static constexpr int NE = (H + 1) * (H + 1), NO = H * H;  // E and O table sizes
   static constexpr int EO = NE + NO;
+  static constexpr int NV = 2 * H + 1;                      // e_0..e_H, o_0..o_{H-1} per element row
 };
 
 template <typename T, int P>
 size_t apply_eo_smem() {
   using Q = EOTile<P>;
-  const size_t t = (size_t)Q::LN * Q::LP                 // staged u
-                   + 2 * (Q::TE + 1) * Q::EO                // E/O per element, x and y
+  const size_t t = (size_t)Q::LN * Q::LP                     // staged u
+                   + 2 * (Q::TE + 1) * Q::EO                  // E/O per element, x and y
+                   + (size_t)(Q::TE + 1) * Q::NV * Q::TN      // e/o vectors of one direction
                    + 2 * (size_t)Q::TN * (Q::TE + 1) * Q::NP  // element-local row / column products
-                   + 2 * (Q::TN + 1);                      // mass diagonals
+                   + 2 * (Q::TN + 1);                        // mass diagonals
   return sizeof(T) * t + sizeof(double) * kRedThreads;
+}
+
+// e/o vectors of one direction: ev[(slot * NV + k) * TN + lane-index], formed
+// once per element row (x) or column (y) and shared by all its outputs
+template <typename T, int P, bool XDIR>
+__device__ __forceinline__ void form_eo(const T* su, T* ev) {
+  using Q = EOTile<P>;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LP = Q::LP, NV = Q::NV;
+  for (int idx = threadIdx.x; idx < (TE + 1) * H * TN; idx += blockDim.x) {
+    const int w = idx % TN;                 // owned row (x) or column (y)
+    const int q = idx / TN;
+    const int sl = q / H, k = q - sl * H;
+    T xk, xm;
+    if (XDIR) {
+      const T* x = su + (w + P) * LP + sl * P;
+      xk = x[k];
+      xm = x[P - k];
+    } else {
+      const T* x = su + (sl * P) * LP + w + P;
+      xk = x[k * LP];
+      xm = x[(P - k) * LP];
+    }
+    ev[(sl * NV + k) * TN + w] = xk + xm;
+    ev[(sl * NV + H + 1 + k) * TN + w] = xk - xm;
+  }
+  for (int idx = threadIdx.x; idx < (TE + 1) * TN; idx += blockDim.x) {
+    const int w = idx % TN, sl = idx / TN;
+    ev[(sl * NV + H) * TN + w] = XDIR ? su[(w + P) * LP + sl * P + H] : su[(sl * P + H) * LP + w + P];
+  }
+}
+
+// element-local products of one direction from the e/o vectors; item (slot, a, w):
+// slot 0 (low-side neighbour) needs only a = 0 (its y_P)
+template <typename T, int P, bool XDIR>
+__device__ __forceinline__ void eo_products(const T* eo, const T* ev, T* dst_base) {
+  using Q = EOTile<P>;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, NP = Q::NP, EO = Q::EO, NE = Q::NE, NV = Q::NV;
+  constexpr int XI = TN * (1 + TE * (H + 1));
+  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
+    const int w = idx % TN;
+    const int q = idx / TN;
+    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
+    const int a = q == 0 ? 0 : (q - 1) % (H + 1);
+    const T* E = eo + sl * EO + a * (H + 1);
+    const T* O = eo + sl * EO + NE + min(a, H - 1) * H;  // row H of O is zero and not stored
+    const T* e = ev + (sl * NV) * TN + w;
+    const T* o = ev + (sl * NV + H + 1) * TN + w;
+    T ye = T(0), yo = T(0);
+#pragma unroll
+    for (int k = 0; k <= H; ++k) ye += E[k] * e[k * TN];
+#pragma unroll
+    for (int k = 0; k < H; ++k) yo += O[k] * o[k * TN];
+    if (a == H) yo = T(0);
+    if (XDIR) {
+      T* dst = dst_base + (w * (TE + 1) + sl) * NP;  // [row][slot][a]
+      if (a < H) dst[P - a] = ye - yo;
+      dst[a] = ye + yo;
+    } else {
+      T* dst = dst_base + (sl * NP) * TN + w;         // [slot][b][col]
+      if (a < H) dst[(P - a) * TN] = ye - yo;
+      dst[a * TN] = ye + yo;
+    }
+  }
 }
 
 template <typename T, int P>
@@ -161,13 +226,15 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
                                                   const T* __restrict__ f, T* __restrict__ out, int dot,
                                                   double* __restrict__ part) {
   using Q = EOTile<P>;
-  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE,
+                NV = Q::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // LN x LP
   T* eox = su + LN * LP;                      // (TE+1) x EO
   T* eoy = eox + (TE + 1) * EO;
-  T* xb = eoy + (TE + 1) * EO;                // [row 0..TN) [slot 0..TE] [a 0..P]  x-products
-  T* yb = xb + TN * (TE + 1) * NP;            // [slot 0..TE] [b 0..P] [col 0..TN)  y-products
+  T* ev = eoy + (TE + 1) * EO;                // (TE+1) x NV x TN, reused by x then y
+  T* xb = ev + (TE + 1) * NV * TN;            // [row][slot][a]  x-products
+  T* yb = xb + TN * (TE + 1) * NP;            // [slot][b][col]  y-products
   T* sMx = yb + TN * (TE + 1) * NP;
   T* sMy = sMx + (TN + 1);
   double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
@@ -208,50 +275,13 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
   }
   __syncthreads();
-
-  // x products: item (slot, a, row); slot 0 needs only a = 0 (its y_P)
-  constexpr int XI = TN * (1 + TE * (H + 1));
-  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
-    const int row = idx % TN;
-    const int q = idx / TN;  // 0: slot 0 / a 0; then (slot, a) pairs
-    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
-    const int a = q == 0 ? 0 : (q - 1) % (H + 1);
-    const T* x = su + (row + P) * LP + sl * P;  // element-local node 0 of this slot
-    const T* E = eox + sl * EO + a * (H + 1);
-    const T* O = eox + sl * EO + NE + min(a, H - 1) * H;  // row a = H of O is zero, not stored
-    T ye = E[H] * x[H], yo = T(0);
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const T xk = x[k], xm = x[P - k];
-      ye += E[k] * (xk + xm);
-      yo += O[k] * (xk - xm);
-    }
-    if (a == H) yo = T(0);
-    T* dst = xb + (row * (TE + 1) + sl) * NP;
-    if (a < H) dst[P - a] = ye - yo;
-    dst[a] = ye + yo;
-  }
-  // y products: item (slot, b, col)
-  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
-    const int col = idx % TN;
-    const int q = idx / TN;
-    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
-    const int b = q == 0 ? 0 : (q - 1) % (H + 1);
-    const T* x = su + (sl * P) * LP + col + P;
-    const T* E = eoy + sl * EO + b * (H + 1);
-    const T* O = eoy + sl * EO + NE + min(b, H - 1) * H;
-    T ye = E[H] * x[H * LP], yo = T(0);
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const T xk = x[k * LP], xm = x[(P - k) * LP];
-      ye += E[k] * (xk + xm);
-      yo += O[k] * (xk - xm);
-    }
-    if (b == H) yo = T(0);
-    T* dst = yb + (sl * NP) * TN + col;
-    if (b < H) dst[(P - b) * TN] = ye - yo;
-    dst[b * TN] = ye + yo;
-  }
+  form_eo<T, P, true>(su, ev);
+  __syncthreads();
+  eo_products<T, P, true>(eox, ev, xb);
+  __syncthreads();
+  form_eo<T, P, false>(su, ev);
+  __syncthreads();
+  eo_products<T, P, false>(eoy, ev, yb);
   __syncthreads();
 
   const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;

@@ -14,6 +14,8 @@
 // lam_x^T)] S_x^T, FP64.  For a periodic (singular) A_0 the right side is
 // projected to zero mean, the (0, 0) eigen-pair is dropped and the result is
 // made orthogonal to the constants: the Moore-Penrose solution A_0^+ f_0.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace sem {
@@ -165,12 +167,15 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
   constexpr int TM = 8, TK = 4;
   __shared__ double sred[kRedThreads];
   __shared__ double part[TK][TM][TM + 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nux = c.nux, nuy = c.nuy;
-  // output shape: steps 1-3 produce nuy x nux (a or j rows, i or b columns)
+  // steps 1 and 3 contract over y (nuy), steps 2 and 4 over x (nux)
+  const int K = (step == kStep1 || step == kStep3) ? nuy : nux;
+  double* sA = reinterpret_cast<double*>(smem_raw);  // TM x K
+  double* sB = sA + TM * K;                           // K x TM
   const int rows = nuy, cols = nux;
   const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TM;
   const int t = threadIdx.x, kg = t / (TM * TM), rr = (t / TM) % TM, cc = t % TM;
-  const int row = r0 + rr, col = c0 + cc;
   double shift = 0.0;
   if (c.periodic && (step == kStep1 || step == kStep4)) {
     double acc = 0.0;
@@ -187,41 +192,52 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
     }
     shift = block_sum(acc, sred) / ((double)nux * nuy);
   }
-  // reduction length: steps 1 and 3 contract over y (nuy), steps 2 and 4 over x (nux)
-  const int K = (step == kStep1 || step == kStep3) ? nuy : nux;
-  double s = 0.0;
-  if (row < rows && col < cols) {
-    for (int k = kg; k < K; k += TK) {
-      double a, b;
-      switch (step) {
-        case kStep1:  // T1[a][i] = sum_j S_y[j][a] (F[j][i] - mu)
-          a = c.Sy[k * nuy + row];
-          b = (double)f0[(long)(c.firsty + k) * c.Nx + c.firstx + col] - shift;
-          break;
-        case kStep2:  // T2[a][b] = sum_i T1[a][i] S_x[i][b]
-          a = c.T1[(long)row * nux + k];
-          b = c.Sx[k * nux + col];
-          break;
-        case kStep3:  // T3[j][b] = sum_a S_y[j][a] T2[a][b]
-          a = c.Sy[row * nuy + k];
-          b = c.T2[(long)k * nux + col];
-          break;
-        default:      // U[j][i] = sum_b T3[j][b] S_x[i][b]
-          a = c.T1[(long)row * nux + k];
-          b = c.Sx[col * nux + k];
-      }
-      s += a * b;
+  // stage the operand panels (coalesced along the contiguous index)
+  for (int idx = t; idx < TM * K; idx += blockDim.x) {
+    int r, k;
+    double a = 0.0;
+    if (step == kStep1) {  // a(row, k) = S_y[k][row]: contiguous in row
+      k = idx / TM;
+      r = idx - k * TM;
+      if (r0 + r < rows) a = c.Sy[k * nuy + r0 + r];
+    } else {                 // rows of T1 / S_y: contiguous in k
+      r = idx / K;
+      k = idx - r * K;
+      if (r0 + r < rows) a = (step == kStep3) ? c.Sy[(r0 + r) * nuy + k] : c.T1[(long)(r0 + r) * nux + k];
     }
+    sA[r * K + k] = a;
   }
+  for (int idx = t; idx < TM * K; idx += blockDim.x) {
+    int k, q;
+    double b = 0.0;
+    if (step == kStep4) {  // b(k, col) = S_x[col][k]: contiguous in k
+      q = idx / K;
+      k = idx - q * K;
+      if (c0 + q < cols) b = c.Sx[(c0 + q) * nux + k];
+    } else {                 // rows of F / S_x / T2: contiguous in col
+      k = idx / TM;
+      q = idx - k * TM;
+      if (c0 + q < cols) {
+        if (step == kStep1) b = (double)f0[(long)(c.firsty + k) * c.Nx + c.firstx + c0 + q] - shift;
+        else if (step == kStep2) b = c.Sx[k * nux + c0 + q];
+        else b = c.T2[(long)k * nux + c0 + q];
+      }
+    }
+    sB[k * TM + q] = b;
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int k = kg; k < K; k += TK) s += sA[rr * K + k] * sB[k * TM + cc];
   part[kg][rr][cc] = s;
   __syncthreads();
+  const int row = r0 + rr, col = c0 + cc;
   if (kg == 0 && row < rows && col < cols) {
     double v = part[0][rr][cc] + part[1][rr][cc] + part[2][rr][cc] + part[3][rr][cc];
     const long o = (long)row * nux + col;
     switch (step) {
       case kStep1: c.T1[o] = v; break;
       case kStep2: c.T2[o] = (c.periodic && row == 0 && col == 0) ? 0.0 : v / (c.ly[row] + c.lx[col]); break;
-      case kStep3: c.T1[o] = v; break;  // T3 reuses the T1 buffer
+      case kStep3: c.T1[o] = v; break;  // S_y T2 reuses the T1 buffer
       default: u0[(long)(c.firsty + row) * c.Nx + c.firstx + col] = T(v - shift);
     }
   }
@@ -284,8 +300,11 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s) {
   dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8);
+  const size_t sm = 2 * 8 * sizeof(double) * (size_t)std::max(c.nux, c.nuy);
+  cudaError_t e0 = allow_smem(k_coarse_gemm<T>, sm);
+  if (e0 != cudaSuccess) return e0;
   for (int step = kStep1; step <= kStep4; ++step) {
-    k_coarse_gemm<T><<<grid, 256, 0, s>>>(c, step, f0, u0);
+    k_coarse_gemm<T><<<grid, 256, sm, s>>>(c, step, f0, u0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

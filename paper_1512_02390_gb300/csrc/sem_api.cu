@@ -382,8 +382,9 @@ static int validate(const sem_config& c, int& L) {
   if (!(c.tol >= 0.0) || c.i_max < 1 || c.i_max > 100000) return fail(SEM_BAD_ARG, "invalid tol or i_max");
   if (!c.x_edges && !(c.lx > 0)) return fail(SEM_BAD_ARG, "lx must be positive");
   if (!c.y_edges && !(c.ly > 0)) return fail(SEM_BAD_ARG, "ly must be positive");
-  if (c.periodic && (c.nx + 1 > 1024 || c.ny > 65535)) return fail(SEM_BAD_ARG, "coarse grid too large");
-  if (!c.periodic && (c.nx - 1 > 1024)) return fail(SEM_BAD_ARG, "coarse grid too large");
+  // the coarse solve stages one panel of up to 1024 unknowns per direction
+  const int cux = c.periodic ? c.nx : c.nx - 1, cuy = c.periodic ? c.ny : c.ny - 1;
+  if (cux > 1024 || cuy > 1024) return fail(SEM_BAD_ARG, "coarse grid too large (at most 1024 unknowns per direction)");
   return SEM_OK;
 }
 
