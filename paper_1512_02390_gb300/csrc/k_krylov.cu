@@ -16,18 +16,33 @@ constexpr int kElemGrid = 4 * 152;
 
 __device__ __forceinline__ bool bad(double x) { return !(fabs(x) <= 1.7976931348623157e308); }
 
-// alpha = delta_{i-1} / (p.q);  u += alpha p;  r -= alpha q;  part_rr = sum r.r
-__global__ void __launch_bounds__(256) k_update_ur(long n, double* __restrict__ u, double* __restrict__ r,
-                                                   const double* __restrict__ p, const double* __restrict__ q,
-                                                   const double* __restrict__ part_pq, int npq, PcgState st, int it,
-                                                   double* __restrict__ part_rr) {
+// Sum of n partials written by other CTAs of the same launch (read through
+// L2, fixed order): used by the last CTA of a launch.
+__device__ __forceinline__ double sum_partials_cg(const double* part, int n, double* sbuf) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+  return block_sum(v, sbuf);
+}
+
+// Iteration i = iter[0]:  alpha = delta_{i-1} / (p.q);  u += alpha p;
+// r -= alpha q;  then the last CTA to finish reduces ||r||^2 in fixed order,
+// records the scalars, sets done / status (convergence ||r|| <= r_max,
+// breakdown, i_max), advances the counter and, inside a graph, sets the
+// condition of the enclosing WHILE node.
+__global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restrict__ u, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         const double* __restrict__ part_pq, int npq, PcgState st,
+                                                         double* __restrict__ part_rr, int i_max,
+                                                         cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sred[kRedThreads];
+  __shared__ int am_last;
+  if (st.flags[0]) {  // finished before this iteration (zero or invalid start)
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  const int it = st.iter[0];
   const double pq = sum_partials(part_pq, npq, sred);
   const double alpha = st.delta[it - 1] / pq;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st.pq[it] = pq;
-    st.alpha[it] = alpha;
-  }
   double acc = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     u[i] += alpha * p[i];
@@ -36,29 +51,37 @@ __global__ void __launch_bounds__(256) k_update_ur(long n, double* __restrict__ 
     acc += ri * ri;
   }
   const double s = block_sum(acc, sred);
-  if (threadIdx.x == 0) part_rr[blockIdx.x] = s;
-}
-
-// rr_i = sum partials; convergence / breakdown flags
-__global__ void __launch_bounds__(256) k_check(const double* __restrict__ part_rr, int nrr, PcgState st, int it,
-                                               int i_max) {
-  __shared__ double sred[kRedThreads];
-  const double rr = sum_partials(part_rr, nrr, sred);
   if (threadIdx.x == 0) {
+    part_rr[blockIdx.x] = s;
+    __threadfence();
+    const unsigned ticket = atomicAdd(st.ticket, 1u);
+    am_last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const double rr = sum_partials_cg(part_rr, gridDim.x, sred);
+  if (threadIdx.x == 0) {
+    st.pq[it] = pq;
+    st.alpha[it] = alpha;
     st.rr[it] = rr;
     int done = 0, status = 0;
-    if (bad(rr) || bad(st.alpha[it]) || !(st.pq[it] > 0.0)) {
+    if (bad(rr) || bad(alpha) || !(pq > 0.0)) {
       done = 1;
       status = 2;  // SEM_BREAKDOWN
     } else if (sqrt(rr) <= st.rmax[0]) {
       done = 1;
-      status = 0;
     } else if (it >= i_max) {
       done = 1;
       status = 1;  // SEM_NOT_CONVERGED
     }
     st.flags[0] = done;
     st.flags[1] = status;
+    st.iter[1] = it;      // index for the rest of this iteration (beta, delta)
+    st.iter[2] = it;      // iterations completed
+    st.iter[0] = it + 1;  // next iteration's update
+    *st.ticket = 0u;
+    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
   }
 }
 
@@ -80,11 +103,13 @@ __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__
   }
 }
 
-// beta = z.(r - r_old) / delta_{i-1};  delta_i = z.r;  p = z + beta p;  r_old = r
+// i = iter[1]:  beta = z.(r - r_old) / delta_{i-1};  delta_i = z.r;
+// p = z + beta p;  r_old = r
 __global__ void __launch_bounds__(256) k_update_p(long n, const double* __restrict__ z, double* __restrict__ p,
                                                   const double* __restrict__ r, double* __restrict__ r_old,
-                                                  const double* __restrict__ part, int np, PcgState st, int it) {
+                                                  const double* __restrict__ part, int np, PcgState st) {
   __shared__ double sred[kRedThreads];
+  const int it = st.iter[1];
   const double zd = sum_partials(part, np, sred);
   const double zr = sum_partials(part + np, np, sred);
   const double beta = zd / st.delta[it - 1];
@@ -111,9 +136,13 @@ __global__ void __launch_bounds__(256) k_start(long n, const double* __restrict_
     st.delta[0] = zr;
     st.rr[0] = rr;
     st.rmax[0] = tol * sqrt(rr);
-    st.flags[0] = (rr == 0.0) ? 1 : 0;
-    st.flags[1] = (bad(rr) || bad(zr)) ? 2 : 0;
-    if (bad(rr) || bad(zr)) st.flags[0] = 1;
+    const bool broken = bad(rr) || bad(zr);
+    st.flags[0] = (broken || rr == 0.0) ? 1 : 0;
+    st.flags[1] = broken ? 2 : 0;
+    st.iter[0] = 1;
+    st.iter[1] = 0;
+    st.iter[2] = 0;
+    *st.ticket = 0u;
   }
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     p[i] = z[i];
@@ -153,15 +182,11 @@ __global__ void __launch_bounds__(256) k_norm2(long n, const double* __restrict_
 
 int elementwise_grid(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, kElemGrid)); }
 
-cudaError_t launch_pcg_update_ur(long n, double* u, double* r, const double* p, const double* q,
-                                 const double* part_pq, int npq, PcgState st, int it, double* part_rr,
-                                 cudaStream_t s) {
-  k_update_ur<<<elementwise_grid(n), 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, it, part_rr);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pcg_check(const double* part_rr, int nrr, PcgState st, int it, int i_max, cudaStream_t s) {
-  k_check<<<1, 256, 0, s>>>(part_rr, nrr, st, it, i_max);
+cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
+                                       const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
+                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  k_update_ur_check<<<elementwise_grid(n), 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond,
+                                                        use_cond);
   return cudaGetLastError();
 }
 
@@ -172,8 +197,8 @@ cudaError_t launch_dot2(long n, const double* z, const double* r, const double* 
 }
 
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
-                                const double* part, int np, PcgState st, int it, cudaStream_t s) {
-  k_update_p<<<elementwise_grid(n), 256, 0, s>>>(n, z, p, r, r_old, part, np, st, it);
+                                const double* part, int np, PcgState st, cudaStream_t s) {
+  k_update_p<<<elementwise_grid(n), 256, 0, s>>>(n, z, p, r, r_old, part, np, st);
   return cudaGetLastError();
 }
 

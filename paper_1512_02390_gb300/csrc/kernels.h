@@ -65,17 +65,17 @@ struct PcgState {
   double* rr;
   int* flags;      // [0] done, [1] status
   double* rmax;    // threshold on ||r||
+  int* iter;       // [0] index of the next update, [1] index of the current beta, [2] iterations done
+  unsigned* ticket;  // CTA completion counter of the fused update/check
 };
 int elementwise_grid(long n);
-cudaError_t launch_pcg_update_ur(long n, double* u, double* r, const double* p, const double* q,
-                                 const double* part_pq, int npq, PcgState st, int it, double* part_rr,
-                                 cudaStream_t s);
-cudaError_t launch_pcg_check(const double* part_rr, int nrr, PcgState st, int it, int i_max,
-                             cudaStream_t s);
+cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
+                                       const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
+                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old,
                         double* part, cudaStream_t s);
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
-                                const double* part, int np, PcgState st, int it, cudaStream_t s);
+                                const double* part, int np, PcgState st, cudaStream_t s);
 cudaError_t launch_pcg_start(long n, const double* z, const double* r, double* p, double* r_old,
                              const double* part_zr, int nzr, const double* part_rr, int nrr,
                              PcgState st, double tol, cudaStream_t s);

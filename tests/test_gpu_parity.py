@@ -180,10 +180,16 @@ def test_pcg_matches_oracle(case):
     lev = H.top
     f = lev.mass(SI.uniform_nodal(1, (lev.NY, lev.NX)))
     want, it_o, _ = H.mgcg(np.zeros_like(f), f, tol=1e-10)
+    fd = _dev(f).reshape(-1)
     ud = torch.zeros(lev.NY * lev.NX, dtype=torch.float64, device="cuda")
-    res, _ = S.pcg_solve(ud, _dev(f).reshape(-1))
+    res, h1 = S.pcg_solve(ud, fd, history_len=200)  # first solve: launch by launch
     assert res.status == P.SEM_OK and res.iterations == it_o
     got = _host(ud).reshape(lev.NY, lev.NX)
+    # second solve replays the captured graph (WHILE node): bitwise identical
+    ud2 = torch.zeros_like(ud)
+    res2, h2 = S.pcg_solve(ud2, fd, history_len=200)
+    assert res2.iterations == res.iterations and res2.status == res.status
+    assert np.array_equal(h1, h2) and np.array_equal(_host(ud2).reshape(lev.NY, lev.NX), got)
     if H.mx.periodic:
         got, want = got - got.mean(), want - want.mean()
     assert _rel(got, want) < _tol(H)
@@ -208,10 +214,11 @@ def test_mixed_precision_reaches_fp64_accuracy(prec):
 def test_zero_rhs_returns_immediately():
     S, H = _pair()
     n = H.top.NY * H.top.NX
-    ud = torch.zeros(n, dtype=torch.float64, device="cuda")
-    res, _ = S.pcg_solve(ud, torch.zeros(n, dtype=torch.float64, device="cuda"))
-    assert res.status == P.SEM_OK and res.iterations == 0
-    assert float(ud.abs().max()) == 0.0
+    for _ in range(2):  # launch by launch, then the captured graph
+        ud = torch.zeros(n, dtype=torch.float64, device="cuda")
+        res, _ = S.pcg_solve(ud, torch.zeros(n, dtype=torch.float64, device="cuda"))
+        assert res.status == P.SEM_OK and res.iterations == 0
+        assert float(ud.abs().max()) == 0.0
 
 
 def test_nan_rhs_reports_breakdown_and_device_stays_usable():
@@ -220,9 +227,10 @@ def test_nan_rhs_reports_breakdown_and_device_stays_usable():
     n = lev.NY * lev.NX
     f = np.ones((lev.NY, lev.NX))
     f[2, 2] = np.nan
-    ud = torch.zeros(n, dtype=torch.float64, device="cuda")
-    res, _ = S.pcg_solve(ud, _dev(f).reshape(-1))
-    assert res.status == P.SEM_BREAKDOWN
+    for _ in range(2):
+        ud = torch.zeros(n, dtype=torch.float64, device="cuda")
+        res, _ = S.pcg_solve(ud, _dev(f).reshape(-1))
+        assert res.status == P.SEM_BREAKDOWN
     # the context still works
     Au = torch.empty(n, dtype=torch.float64, device="cuda")
     S.apply(torch.ones(n, dtype=torch.float64, device="cuda"), Au)
@@ -233,9 +241,10 @@ def test_iteration_limit_reports_not_converged():
     S, H = _pair(i_max=2)
     lev = H.top
     f = lev.mass(_manufactured(lev))
-    ud = torch.zeros(lev.NY * lev.NX, dtype=torch.float64, device="cuda")
-    res, _ = S.pcg_solve(ud, _dev(f).reshape(-1))
-    assert res.status == P.SEM_NOT_CONVERGED and res.iterations == 2
+    for _ in range(2):
+        ud = torch.zeros(lev.NY * lev.NX, dtype=torch.float64, device="cuda")
+        res, _ = S.pcg_solve(ud, _dev(f).reshape(-1))
+        assert res.status == P.SEM_NOT_CONVERGED and res.iterations == 2
 
 
 def test_mg_solve_rate_matches_oracle():
