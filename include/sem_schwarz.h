@@ -100,6 +100,15 @@ typedef struct sem_config {
   int32_t precision;       /* sem_precision                                      */
   double tol;              /* MGCG stops when ||r_i|| <= tol * ||r_0||           */
   int32_t i_max;           /* MGCG iteration limit                               */
+  /* Variable diffusivity (Sec. 4.3, Eq. (diffusion)): -div(nu grad u) = f.
+   * nu_kind 0: Poisson (nu = 1).  1: nu = 1 + (a-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y),
+   * contrast a.  2: nu = 1 + a sin 2 pi (x-b) sin 2 pi (y-b) (the paper's study).
+   * nu is evaluated at the GLL nodes of every level; the residual uses B(nu),
+   * the local solves are divided by the element mean nu_bar_s
+   * (Eq. (subproblem:solution)) and the coarse problem is solved with a dense
+   * FP64 inverse of B_0(nu).  Dirichlet walls only. */
+  int32_t nu_kind;
+  double nu_a, nu_b;
 } sem_config;
 
 typedef struct sem_result {

@@ -44,6 +44,7 @@ class sem_config(ctypes.Structure):
         ("overlap_rule", ctypes.c_int32), ("overlap", ctypes.c_int32), ("weight", ctypes.c_int32),
         ("ns1", ctypes.c_int32), ("ns2", ctypes.c_int32), ("variable_cycle", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("i_max", ctypes.c_int32),
+        ("nu_kind", ctypes.c_int32), ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double),
     ]
 
 

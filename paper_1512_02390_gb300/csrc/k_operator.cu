@@ -7,6 +7,7 @@
 // element interface.  A CTA owns a tile of TE x TE elements (32 x 32 nodes),
 // stages the tile plus one element of halo on the low side in shared memory,
 // and writes every owned node exactly once: no atomics, deterministic.
+#include <algorithm>
 #include <type_traits>
 
 #include "kernels.h"
@@ -316,6 +317,97 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   }
 }
 
+// ---- variable diffusivity B(nu), Sec. 4.3, Eq. (diffusion) -------------------
+// Element-local weak form with GLL quadrature (U: element coefficients, rows
+// j = y, columns i = x, D the differentiation matrix):
+//   ux = U D^T,  uy = D U,  V = (G_x .* ux) D + D^T (G_y .* uy)
+// one CTA per element; V goes to the element-blocked scratch E, and a node
+// gather then sums the (at most 2 x 2) element contributions of every node.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_var_local(DirView<T> dx, DirView<T> dy, VarView<T> v,
+                                                   const T* __restrict__ u) {
+  constexpr int NP = P + 1, NN = NP * NP;
+  __shared__ T sU[NN], sD[NN], sA[NN], sB[NN];
+  const int ex = blockIdx.x, ey = blockIdx.y;
+  const long e = (long)ey * dx.n + ex;
+  for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+    const int j = idx / NP, i = idx - j * NP;
+    const int gx = node_or_wall(ex * P + i, dx.N, dx.periodic);
+    const int gy = node_or_wall(ey * P + j, dy.N, dy.periodic);
+    sU[idx] = (gx >= 0 && gy >= 0) ? u[(long)gy * dx.N + gx] : T(0);
+    sD[idx] = v.D[idx];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+    const int j = idx / NP, i = idx - j * NP;
+    T ax = T(0), ay = T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      ax += sD[i * NP + k] * sU[j * NP + k];
+      ay += sD[j * NP + k] * sU[k * NP + i];
+    }
+    sA[idx] = v.Gx[e * NN + idx] * ax;
+    sB[idx] = v.Gy[e * NN + idx] * ay;
+  }
+  __syncthreads();
+  T* Es = v.E + e * NN;
+  for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+    const int j = idx / NP, a = idx - j * NP;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) s += sA[j * NP + q] * sD[q * NP + a] + sD[q * NP + j] * sB[q * NP + a];
+    Es[idx] = s;
+  }
+}
+
+// out = (f ? f - sum : sum) over the elements that hold each node
+template <typename T>
+__global__ void __launch_bounds__(256) k_var_gather(DirView<T> dx, DirView<T> dy, const T* __restrict__ E,
+                                                    const T* __restrict__ u, const T* __restrict__ f,
+                                                    T* __restrict__ out, int dot, double* __restrict__ part) {
+  __shared__ double sred[kRedThreads];
+  const int p = dx.p, np1 = p + 1, nn = np1 * np1;
+  const long n = (long)dx.N * dy.N;
+  double acc = 0.0;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+    const int gj = (int)(idx / dx.N), gi = (int)(idx - (long)gj * dx.N);
+    const bool wall = (!dx.periodic && (gi == 0 || gi == dx.N - 1)) || (!dy.periodic && (gj == 0 || gj == dy.N - 1));
+    T val = T(0);
+    if (!wall) {
+      T s = T(0);
+      const int ey_hi = gj / p, ex_hi = gi / p;
+      for (int eyu = (gj % p == 0 ? ey_hi - 1 : ey_hi); eyu <= ey_hi; ++eyu) {
+        int ey = eyu;
+        if (dy.periodic) ey = ((ey % dy.n) + dy.n) % dy.n;
+        else if (ey < 0 || ey >= dy.n) continue;
+        const int b = gj - eyu * p;
+        for (int exu = (gi % p == 0 ? ex_hi - 1 : ex_hi); exu <= ex_hi; ++exu) {
+          int ex = exu;
+          if (dx.periodic) ex = ((ex % dx.n) + dx.n) % dx.n;
+          else if (ex < 0 || ex >= dx.n) continue;
+          const int a = gi - exu * p;
+          s += E[(long)(ey * dx.n + ex) * nn + b * np1 + a];
+        }
+      }
+      val = f ? f[idx] - s : s;
+    }
+    out[idx] = val;
+    if (dot == 1) acc += (double)u[idx] * (double)val;
+    else if (dot == 2) acc += (double)val * (double)val;
+  }
+  if (dot) {
+    const double sm = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = sm;
+  }
+}
+
+template <typename T, int P>
+cudaError_t var_p(const DirView<T>& dx, const DirView<T>& dy, const VarView<T>& v, const T* u, cudaStream_t s) {
+  dim3 grid(dx.n, dy.n);
+  k_var_local<T, P><<<grid, 256, 0, s>>>(dx, dy, v, u);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double> dy, const double* __restrict__ f,
                                                double* __restrict__ b, double* __restrict__ part) {
   __shared__ double sred[kRedThreads];
@@ -368,6 +460,32 @@ cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u,
     default: return cudaErrorInvalidValue;
   }
 }
+
+template <typename T>
+cudaError_t launch_apply_var(const DirView<T>& dx, const DirView<T>& dy, const VarView<T>& v, const T* u, const T* f,
+                             T* out, int dot, double* part, int* nparts, cudaStream_t s) {
+  cudaError_t e;
+  switch (dx.p) {
+    case 2: e = var_p<T, 2>(dx, dy, v, u, s); break;
+    case 4: e = var_p<T, 4>(dx, dy, v, u, s); break;
+    case 8: e = var_p<T, 8>(dx, dy, v, u, s); break;
+    case 16: e = var_p<T, 16>(dx, dy, v, u, s); break;
+    case 32: e = var_p<T, 32>(dx, dy, v, u, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const long n = (long)dx.N * dy.N;
+  const int grid = (int)std::max<long>(1, std::min<long>((n + 255) / 256, 4 * 152));
+  if (nparts) *nparts = grid;
+  k_var_gather<T><<<grid, 256, 0, s>>>(dx, dy, v.E, u, f, out, dot, part);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply_var<double>(const DirView<double>&, const DirView<double>&, const VarView<double>&,
+                                              const double*, const double*, double*, int, double*, int*,
+                                              cudaStream_t);
+template cudaError_t launch_apply_var<float>(const DirView<float>&, const DirView<float>&, const VarView<float>&,
+                                             const float*, const float*, float*, int, double*, int*, cudaStream_t);
 
 template cudaError_t launch_apply<double>(const DirView<double>&, const DirView<double>&, const double*,
                                           const double*, double*, int, double*, int*, cudaStream_t);

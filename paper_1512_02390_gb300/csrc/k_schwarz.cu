@@ -22,7 +22,7 @@ namespace {
 
 template <typename T, typename TIn>
 __global__ void __launch_bounds__(256) k_sweep_simt(DirView<T> dx, DirView<T> dy, const TIn* __restrict__ r,
-                                                    T* __restrict__ E, const float* __restrict__ nu_inv) {
+                                                    T* __restrict__ E, const T* __restrict__ nu_inv) {
   const int ex = blockIdx.x, ey = blockIdx.y;
   const int m = dx.m, mm = m * m, p = dx.p, no = dx.n_o;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_sweep_simt(DirView<T> dx, DirView<T> dy
   }
   __syncthreads();
   // X5 = X4 S_x^T, weighted: E[j][i] = w_y[j] w_x[i] sum_b Y[j][b] S_x[i][b]
-  const T scale = nu_inv ? T(nu_inv[ey * dx.n + ex]) : T(1);
+  const T scale = nu_inv ? nu_inv[ey * dx.n + ex] : T(1);
   T* Es = E + (long)(ey * dx.n + ex) * mm;
   for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) {
     const int j = idx / m, i = idx - j * m;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256) k_scatter(DirView<T> dx, DirView<T> dy, c
 
 template <typename T, typename TIn>
 cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
-                         const float* nu_inv, cudaStream_t s) {
+                         const T* nu_inv, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (mode == 1) return sweep_mma<TIn, 1>(dx, dy, r, E, nu_inv, s);
     if (mode == 2) return sweep_mma<TIn, 2>(dx, dy, r, E, nu_inv, s);
@@ -350,7 +350,7 @@ cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* 
 }
 
 template cudaError_t launch_sweep<double, double>(const DirView<double>&, const DirView<double>&, const double*,
-                                                  double*, int, const float*, cudaStream_t);
+                                                  double*, int, const double*, cudaStream_t);
 template cudaError_t launch_sweep<float, float>(const DirView<float>&, const DirView<float>&, const float*, float*,
                                                 int, const float*, cudaStream_t);
 template cudaError_t launch_sweep<float, double>(const DirView<float>&, const DirView<float>&, const double*,

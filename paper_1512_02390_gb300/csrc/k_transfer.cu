@@ -243,6 +243,28 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
   }
 }
 
+// u0 = Binv f0: one warp per unknown row, FP64 accumulation, coalesced reads
+// of the dense inverse (variable diffusivity, Dirichlet walls)
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_dense(CoarseView c, const double* __restrict__ Binv,
+                                                      const T* __restrict__ f0, T* __restrict__ u0) {
+  const int n = c.nux * c.nuy;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = Binv + (long)warp * n;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    const int j = k / c.nux, i = k - j * c.nux;
+    s += row[k] * (double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    const int j = warp / c.nux, i = warp - j * c.nux;
+    u0[(long)(c.firsty + j) * c.Nx + c.firstx + i] = T(s);
+  }
+}
+
 template <typename T, int PF>
 cudaError_t restrict_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,
                        const T* J, const T* rf, T* fc, cudaStream_t s) {
@@ -310,6 +332,15 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
   }
   return cudaSuccess;
 }
+
+template <typename T>
+cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s) {
+  const int n = c.nux * c.nuy;
+  k_coarse_dense<T><<<(n + 7) / 8, 256, 0, s>>>(c, Binv, f0, u0);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_dense<double>(const CoarseView&, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_coarse_dense<float>(const CoarseView&, const double*, const float*, float*, cudaStream_t);
 
 template cudaError_t launch_restrict<double>(const DirView<double>&, const DirView<double>&, const DirView<double>&,
                                              const DirView<double>&, const double*, const double*, double*,

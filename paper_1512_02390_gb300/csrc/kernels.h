@@ -19,6 +19,20 @@ template <typename T>
 cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f,
                          T* out, int dot, double* part, int* nparts, cudaStream_t s);
 
+// Variable-diffusivity operator B(nu) (Sec. 4.3): element data of one level.
+template <typename T>
+struct VarView {
+  const T* Gx;  // n_e x (p+1)^2: w_j w_i J nu (2/h_x)^2
+  const T* Gy;  // n_e x (p+1)^2: w_j w_i J nu (2/h_y)^2
+  const T* D;   // (p+1)^2 differentiation matrix
+  T* E;         // n_e x (p+1)^2 scratch: element-local products
+};
+// out = B u (f == nullptr) or f - B u; element-local weak form then a
+// deterministic node gather; dot as for launch_apply.
+template <typename T>
+cudaError_t launch_apply_var(const DirView<T>& dx, const DirView<T>& dy, const VarView<T>& v, const T* u, const T* f,
+                             T* out, int dot, double* part, int* nparts, cudaStream_t s);
+
 // b = (M_y (x) M_x) f_nodal, walls 0; part[cta] = sum of b (for the periodic
 // mean projection).
 cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f,
@@ -27,9 +41,10 @@ cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, co
 // ---- weighted additive Schwarz sweep (Alg. 2), k_schwarz.cu ---------------
 // E[s] = W_s A_ss^{-1} R_s r for every subdomain s (element-blocked m x m).
 // mode: 0 SIMT in T, 1 tensor cores TF32, 2 tensor cores BF16 (T = float).
+// nu_inv (may be null): 1 / nu_bar_s per subdomain (Eq. (subproblem:solution)).
 template <typename T, typename TIn>
 cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
-                         const float* nu_inv, cudaStream_t s);
+                         const T* nu_inv, cudaStream_t s);
 // u = (accum ? u : 0) + sum_s R_s^T E[s]  (deterministic node-centric sum).
 template <typename T, typename TOut>
 cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* E, TOut* u,
@@ -55,6 +70,9 @@ struct CoarseView {
 };
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s);
+// u0 = Binv f0 over the Dirichlet unknowns with a dense FP64 inverse (variable nu)
+template <typename T>
+cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s);
 
 // ---- Krylov vector kernels (Alg. 4), k_krylov.cu -------------------------
 struct PcgState {

@@ -43,6 +43,11 @@ struct Level {
   DirView<float> x32{}, y32{};
   double* J64 = nullptr;  // interpolation from level l-1 to l
   float* J32 = nullptr;
+  bool var = false;       // variable diffusivity: B(nu) operator, 1/nu_bar local solves
+  VarView<double> v64{};
+  VarView<float> v32{};
+  double* nu_inv64 = nullptr;
+  float* nu_inv32 = nullptr;
   void* u = nullptr;      // level vectors in the V-cycle type
   void* f = nullptr;
   void* r = nullptr;
@@ -69,6 +74,7 @@ struct sem_handle {
   long n = 0, n_unknowns = 0;
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *r_old = nullptr;
   double* fi = nullptr;  // right side of the running MGCG solve (internal copy)
+  double* Binv = nullptr;  // dense FP64 inverse of B_0(nu) (variable diffusivity)
   // the whole MGCG solve as one CUDA graph: prologue + WHILE node over one iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -165,11 +171,8 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 constexpr int kMaxEventPairs = 1 << 15;
 
-// kernels per launcher call of each class (the coarse solve is two kernels)
-int kernels_of(int cls) { return cls == SEM_K_COARSE ? 4 : 1; }
-
-void prof_begin(sem_handle* h, int cls, cudaStream_t s) {
-  h->launches[cls] += kernels_of(cls);
+void prof_begin(sem_handle* h, int cls, cudaStream_t s, int kernels = 1) {
+  h->launches[cls] += kernels;
   if (!h->prof || h->ev_used >= kMaxEventPairs) return;
   if ((int)h->ev.size() < 2 * (h->ev_used + 1)) {
     cudaEvent_t a, b;
@@ -199,6 +202,13 @@ void prof_end(sem_handle* h, cudaStream_t s) {
     CK(call);                      \
     prof_end((h), (s));            \
   } while (0)
+// the same for a launcher call that issues nk kernels
+#define KLN(h, cls, nk, s, call)        \
+  do {                                  \
+    prof_begin((h), (cls), (s), (nk));  \
+    CK(call);                           \
+    prof_end((h), (s));                 \
+  } while (0)
 
 // ---- one level's smoothing (Alg. 2) --------------------------------------
 
@@ -214,12 +224,32 @@ template <typename T>
 const T* JL(const Level& l) {
   if constexpr (std::is_same<T, double>::value) return l.J64; else return l.J32;
 }
+template <typename T>
+const VarView<T>& VV(const Level& l) {
+  if constexpr (std::is_same<T, double>::value) return l.v64; else return l.v32;
+}
+template <typename T>
+const T* NUI(const Level& l) {
+  if constexpr (std::is_same<T, double>::value) return l.nu_inv64; else return l.nu_inv32;
+}
+
+// out = A_l u (f null) or f - A_l u on level l; B_l(nu) when nu varies
+template <typename T>
+int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const T* f, T* out, int dot, double* part,
+                int* np, cudaStream_t s) {
+  if (l.var) {
+    KLN(h, cls, 2, s, launch_apply_var<T>(DX<T>(l), DY<T>(l), VV<T>(l), u, f, out, dot, part, np, s));
+  } else {
+    KL(h, cls, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s));
+  }
+  return SEM_OK;
+}
 
 // u = (accum ? u : 0) + sum_s R_s^T W A_ss^{-1} R_s r  (one additive sweep on r)
 template <typename T, typename TIn, typename TU>
 int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
-  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, nullptr, s)));
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, NUI<T>(l), s)));
   KL(h, SEM_K_SCATTER, s, (launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
   return SEM_OK;
 }
@@ -235,7 +265,7 @@ int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cud
   if (rc) return rc;
   T* r = static_cast<T*>(l.r);
   for (int k = 1; k < n; ++k) {
-    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
+    if ((rc = level_apply<T>(h, l, SEM_K_APPLY_MG, u, f, r, 0, nullptr, nullptr, s))) return rc;
     if ((rc = sweep<T, T, T>(h, l, r, u, true, s))) return rc;
   }
   return SEM_OK;
@@ -245,8 +275,9 @@ template <typename T>
 int smooth(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
   T* r = static_cast<T*>(l.r);
   for (int k = 0; k < n; ++k) {
-    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, r, 0, nullptr, nullptr, s));
-    int rc = sweep<T, T, T>(h, l, r, u, true, s);
+    int rc = level_apply<T>(h, l, SEM_K_APPLY_MG, u, f, r, 0, nullptr, nullptr, s);
+    if (rc) return rc;
+    rc = sweep<T, T, T>(h, l, r, u, true, s);
     if (rc) return rc;
   }
   return SEM_OK;
@@ -273,11 +304,16 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     if ((rc = smooth_from_zero<T>(h, lv[l], fl, ul, h->ns1[l], s))) return rc;
     T* rl = static_cast<T*>(lv[l].r);
-    KL(h, SEM_K_APPLY_MG, s, launch_apply<T>(DX<T>(lv[l]), DY<T>(lv[l]), ul, fl, rl, 0, nullptr, nullptr, s));
+    if ((rc = level_apply<T>(h, lv[l], SEM_K_APPLY_MG, ul, fl, rl, 0, nullptr, nullptr, s))) return rc;
     KL(h, SEM_K_RESTRICT, s, launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
                           static_cast<T*>(lv[l - 1].f), s));
   }
-  KL(h, SEM_K_COARSE, s, launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
+  if (h->Binv)
+    KL(h, SEM_K_COARSE, s,
+       launch_coarse_dense<T>(h->coarse, h->Binv, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
+  else
+    KLN(h, SEM_K_COARSE, 4, s,
+        launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
   bool z_written = std::is_same<T, double>::value;
   for (int l = 1; l <= L; ++l) {
     const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
@@ -305,9 +341,7 @@ const Level& top(const sem_handle* h) { return h->lev[h->L]; }
 
 int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s,
             double* part = nullptr) {
-  KL(h, SEM_K_APPLY_FP64, s,
-     launch_apply<double>(top(h).x64, top(h).y64, u, f, out, dot, part ? part : h->part, np, s));
-  return SEM_OK;
+  return level_apply<double>(h, top(h), SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s);
 }
 
 // ---- MGCG, Alg. 4, on the internal vectors h->u, h->fi ---------------------
@@ -489,6 +523,10 @@ static int validate(const sem_config& c, int& L) {
   if (c.ns1 < 0 || c.ns2 < 0 || c.ns1 + c.ns2 < 1 || c.ns1 > 64 || c.ns2 > 64)
     return fail(SEM_BAD_ARG, "need 0 <= ns1, ns2 <= 64 and ns1 + ns2 >= 1");
   if (!(c.tol >= 0.0) || c.i_max < 1 || c.i_max > 100000) return fail(SEM_BAD_ARG, "invalid tol or i_max");
+  if (c.nu_kind < 0 || c.nu_kind > 2) return fail(SEM_BAD_ARG, "unknown nu_kind");
+  if (c.nu_kind && c.periodic) return fail(SEM_BAD_ARG, "variable diffusivity needs Dirichlet walls");
+  if (c.nu_kind == 1 && !(c.nu_a >= 1.0)) return fail(SEM_BAD_ARG, "contrast must be >= 1");
+  if (c.nu_kind == 2 && !(std::fabs(c.nu_a) < 1.0)) return fail(SEM_BAD_ARG, "amplitude must be in (-1, 1)");
   if (!c.x_edges && !(c.lx > 0)) return fail(SEM_BAD_ARG, "lx must be positive");
   if (!c.y_edges && !(c.ly > 0)) return fail(SEM_BAD_ARG, "ly must be positive");
   // the coarse solve stages one panel of up to 1024 unknowns per direction
@@ -616,6 +654,29 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
       lv.r = b;
       if ((rc = dev_alloc(h, &b, (size_t)c.nx * c.ny * lv.m * lv.m * tsz))) return bail(rc);
       lv.E = b;
+      if (c.nu_kind) {
+        VarData vd;
+        build_var(h->mx, h->my, lv.p, c.nu_kind, c.nu_a, c.nu_b, vd);
+        std::vector<double> inv(vd.nu_bar.size());
+        for (size_t k = 0; k < inv.size(); ++k) inv[k] = 1.0 / vd.nu_bar[k];
+        double *gx, *gy, *dd;
+        float *gxf, *gyf, *ddf;
+        if ((rc = upload(h, &gx, vd.Gx)) || (rc = upload(h, &gy, vd.Gy)) || (rc = upload(h, &dd, vd.D)) ||
+            (rc = upload(h, &gxf, vd.Gx)) || (rc = upload(h, &gyf, vd.Gy)) || (rc = upload(h, &ddf, vd.D)) ||
+            (rc = upload(h, &lv.nu_inv64, inv)) || (rc = upload(h, &lv.nu_inv32, inv)))
+          return bail(rc);
+        lv.var = true;
+        lv.v64 = VarView<double>{gx, gy, dd, nullptr};
+        lv.v32 = VarView<float>{gxf, gyf, ddf, nullptr};
+        // the element products reuse the level's correction buffer (n_e m^2 >= n_e (p+1)^2)
+        if (h->mixed) lv.v32.E = static_cast<float*>(lv.E);
+        else lv.v64.E = static_cast<double*>(lv.E);
+        if (l == L && h->mixed) {  // FP64 operator of the outer MGCG on the finest level
+          double* e64;
+          if ((rc = dev_alloc(h, &e64, (size_t)c.nx * c.ny * (lv.p + 1) * (lv.p + 1)))) return bail(rc);
+          lv.v64.E = e64;
+        }
+      }
     }
   }
   // coarse factors
@@ -648,6 +709,15 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     cv.cx = ccx;
     cv.cy = ccy;
     cv.T2 = T2;
+  }
+  if (c.nu_kind) {
+    std::vector<double> inv;
+    std::string err = coarse_var_inverse(h->mx, h->my, c.nu_kind, c.nu_a, c.nu_b, inv);
+    if (!err.empty()) {
+      sem_destroy(h);
+      return fail(SEM_BAD_ARG, err);
+    }
+    if ((rc = upload(h, &h->Binv, inv))) return bail(rc);
   }
   // MGCG vectors, partial sums, per-iteration scalars
   h->n = top(h).nodes;

@@ -330,6 +330,108 @@ std::string build_coarse(const Mesh1D& mesh, Coarse1D& o) {
   return "";
 }
 
+double nu_value(int kind, double a, double b, double x, double y) {
+  if (kind == 1) return 1.0 + (a - 1.0) * (0.5 + 0.5 * std::sin(2.0 * M_PI * x) * std::cos(2.0 * M_PI * y));
+  if (kind == 2) return 1.0 + a * std::sin(2.0 * M_PI * (x - b)) * std::sin(2.0 * M_PI * (y - b));
+  return 1.0;
+}
+
+void build_var(const Mesh1D& mx, const Mesh1D& my, int p, int kind, double a, double b, VarData& o) {
+  std::vector<double> xi, w;
+  gll(p, xi, w);
+  deriv_matrix(xi, o.D);
+  const int np1 = p + 1, nn = np1 * np1;
+  o.Gx.assign((size_t)mx.n * my.n * nn, 0.0);
+  o.Gy.assign((size_t)mx.n * my.n * nn, 0.0);
+  o.nu_bar.assign((size_t)mx.n * my.n, 0.0);
+  double wsum = 0.0;
+  for (int j = 0; j < np1; ++j)
+    for (int i = 0; i < np1; ++i) wsum += w[j] * w[i];
+  for (int ey = 0; ey < my.n; ++ey)
+    for (int ex = 0; ex < mx.n; ++ex) {
+      const double hx = mx.h(ex), hy = my.h(ey), jac = 0.25 * hx * hy;
+      const size_t e = (size_t)ey * mx.n + ex;
+      double acc = 0.0;
+      for (int j = 0; j < np1; ++j)
+        for (int i = 0; i < np1; ++i) {
+          const double x = mx.edges[ex] + 0.5 * (1.0 + xi[i]) * hx;
+          const double y = my.edges[ey] + 0.5 * (1.0 + xi[j]) * hy;
+          const double nu = nu_value(kind, a, b, x, y);
+          const double q = w[j] * w[i] * jac * nu;
+          o.Gx[e * nn + j * np1 + i] = q * (2.0 / hx) * (2.0 / hx);
+          o.Gy[e * nn + j * np1 + i] = q * (2.0 / hy) * (2.0 / hy);
+          acc += w[j] * w[i] * nu;
+        }
+      o.nu_bar[e] = acc / wsum;
+    }
+}
+
+std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, double a, double b,
+                               std::vector<double>& inv) {
+  if (mx.periodic || my.periodic) return "variable diffusivity needs Dirichlet walls";
+  const int nux = mx.n - 1, nuy = my.n - 1, n = nux * nuy, bw = nux + 1;  // half bandwidth
+  VarData v;
+  build_var(mx, my, 1, kind, a, b, v);
+  // band storage: Bb[i][d] = B[i][i - d], d = 0..bw (lower band)
+  std::vector<double> Bb((size_t)n * (bw + 1), 0.0);
+  const double* D = v.D.data();  // 2 x 2
+  for (int ey = 0; ey < my.n; ++ey)
+    for (int ex = 0; ex < mx.n; ++ex) {
+      const size_t e = (size_t)ey * mx.n + ex;
+      // element matrix K[(j,i),(l,k)] = sum_q Gx[j][q] D[q][i] D[q][k] d_jl + sum_q Gy[q][i] D[q][j] D[q][l] d_ik
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i)
+          for (int l = 0; l < 2; ++l)
+            for (int k = 0; k < 2; ++k) {
+              double kv = 0.0;
+              if (j == l)
+                for (int q = 0; q < 2; ++q) kv += v.Gx[e * 4 + j * 2 + q] * D[q * 2 + i] * D[q * 2 + k];
+              if (i == k)
+                for (int q = 0; q < 2; ++q) kv += v.Gy[e * 4 + q * 2 + i] * D[q * 2 + j] * D[q * 2 + l];
+              const int gr_y = ey + j, gr_x = ex + i, gc_y = ey + l, gc_x = ex + k;
+              if (gr_y < 1 || gr_y > nuy || gr_x < 1 || gr_x > nux) continue;
+              if (gc_y < 1 || gc_y > nuy || gc_x < 1 || gc_x > nux) continue;
+              const int r = (gr_y - 1) * nux + gr_x - 1, c = (gc_y - 1) * nux + gc_x - 1;
+              if (c <= r) Bb[(size_t)r * (bw + 1) + (r - c)] += kv;
+            }
+    }
+  // banded Cholesky B = L L^T, L stored in the same band layout
+  for (int i = 0; i < n; ++i) {
+    for (int d = std::min(i, bw); d >= 0; --d) {
+      const int j = i - d;
+      double sum = Bb[(size_t)i * (bw + 1) + d];
+      const int k0 = std::max(0, i - bw);
+      for (int k = std::max(k0, j - bw); k < j; ++k)
+        sum -= Bb[(size_t)i * (bw + 1) + (i - k)] * Bb[(size_t)j * (bw + 1) + (j - k)];
+      if (d == 0) {
+        if (!(sum > 0.0)) return "coarse variable-diffusivity matrix is not positive definite";
+        Bb[(size_t)i * (bw + 1)] = std::sqrt(sum);
+      } else {
+        Bb[(size_t)i * (bw + 1) + d] = sum / Bb[(size_t)j * (bw + 1)];
+      }
+    }
+  }
+  // inverse column by column: L y = e_c, L^T x = y
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    std::fill(y.begin(), y.end(), 0.0);
+    y[c] = 1.0;
+    for (int i = c; i < n; ++i) {
+      double sum = y[i];
+      for (int k = std::max(c, i - bw); k < i; ++k) sum -= Bb[(size_t)i * (bw + 1) + (i - k)] * y[k];
+      y[i] = sum / Bb[(size_t)i * (bw + 1)];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double sum = y[i];
+      for (int k = i + 1; k <= std::min(n - 1, i + bw); ++k) sum -= Bb[(size_t)k * (bw + 1) + (k - i)] * y[k];
+      y[i] = sum / Bb[(size_t)i * (bw + 1)];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
+  }
+  return "";
+}
+
 void interp_matrix(int pf, int pc, std::vector<double>& J) {
   std::vector<double> xf, wf, xc, wc;
   gll(pf, xf, wf);

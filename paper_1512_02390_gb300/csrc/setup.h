@@ -76,6 +76,26 @@ struct Coarse1D {
 };
 std::string build_coarse(const Mesh1D& mesh, Coarse1D& out);
 
+// Variable diffusivity nu(x, y) (Sec. 4.3, Eq. (diffusion)); kind 1:
+// 1 + (a-1)(1/2 + 1/2 sin(2 pi x) cos(2 pi y)) (contrast a); kind 2:
+// 1 + a sin(2 pi (x - b)) sin(2 pi (y - b)) (amplitude a, shift b).
+double nu_value(int kind, double a, double b, double x, double y);
+
+// Element data of B(nu) at order p: G_x = w_j w_i J nu (2/h_x)^2 and
+// G_y = w_j w_i J nu (2/h_y)^2 at the element's GLL nodes (row j = y, col i = x),
+// and nu_bar, the GLL-quadrature mean of nu over the element (Sec. 4.3).
+struct VarData {
+  std::vector<double> Gx, Gy;  // (ny * nx) x (p+1)^2
+  std::vector<double> nu_bar;  // ny * nx
+  std::vector<double> D;       // (p+1)^2 differentiation matrix
+};
+void build_var(const Mesh1D& mx, const Mesh1D& my, int p, int kind, double a, double b, VarData& out);
+
+// Dense inverse of B(nu) at p = 1 over the Dirichlet unknowns (row-major,
+// (nx-1)(ny-1) squared), by a banded Cholesky factorisation.
+std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, double a, double b,
+                               std::vector<double>& inv);
+
 // Interpolation J[i*(pc+1) + k] = phi_k^{(pc)}(xi_i^{(pf)}).
 void interp_matrix(int pf, int pc, std::vector<double>& J);
 

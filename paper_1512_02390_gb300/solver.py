@@ -14,7 +14,9 @@ _PREC = {"fp64": B.SEM_PREC_FP64, "fp32": B.SEM_PREC_FP32, "tf32": B.SEM_PREC_TF
 
 
 def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weight=5, ns1=1, ns2=0,
-                variable_cycle=False, precision="fp64", tol=1e-10, i_max=200, x_edges=None, y_edges=None):
+                variable_cycle=False, precision="fp64", tol=1e-10, i_max=200, x_edges=None, y_edges=None,
+                nu=None):
+    """nu: None (Poisson), ("contrast", c) or ("paper", amplitude, shift)."""
     cfg = B.sem_default_config()
     cfg.nx, cfg.ny, cfg.p, cfg.periodic = nx, ny, p, int(bool(periodic))
     cfg.lx, cfg.ly = lx, ly
@@ -26,6 +28,13 @@ def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weig
     cfg.ns1, cfg.ns2, cfg.variable_cycle = ns1, ns2, int(bool(variable_cycle))
     cfg.precision = _PREC[precision]
     cfg.tol, cfg.i_max = tol, i_max
+    if nu is not None:
+        if nu[0] == "contrast":
+            cfg.nu_kind, cfg.nu_a, cfg.nu_b = 1, float(nu[1]), 0.0
+        elif nu[0] == "paper":
+            cfg.nu_kind, cfg.nu_a, cfg.nu_b = 2, float(nu[1]), float(nu[2])
+        else:
+            raise ValueError(nu)
     keep = []
     for name, e in (("x_edges", x_edges), ("y_edges", y_edges)):
         if e is not None:

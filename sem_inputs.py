@@ -43,3 +43,33 @@ def uniform_nodal(seed: int, shape, lo: float = -1.0, hi: float = 1.0) -> np.nda
     """Array of `shape` with i.i.d. U[lo, hi) entries, row-major draw order."""
     n = int(np.prod(shape))
     return (lo + (hi - lo) * uniform01(seed, n)).reshape(shape)
+
+
+def geometric_edges(n: int, first_width: float, length: float = 1.0) -> np.ndarray:
+    """n + 1 element edges on [0, length] whose widths grow geometrically from
+    `first_width` (the ratio is found by bisection so that the widths sum to
+    `length`).  Mesh geometry only: an input of the stretched-mesh workloads."""
+    if first_width * n >= length:
+        raise ValueError("first_width too large for a growing mesh")
+    lo, hi = 1.0, 2.0
+    while first_width * (hi**n - 1) / (hi - 1) < length:
+        hi *= 2
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        tot = first_width * n if mid == 1.0 else first_width * (mid**n - 1) / (mid - 1)
+        lo, hi = (mid, hi) if tot < length else (lo, mid)
+    r = 0.5 * (lo + hi)
+    w = first_width * r ** np.arange(n)
+    e = np.concatenate([[0.0], np.cumsum(w)])
+    e *= length / e[-1]
+    return e
+
+
+def nu_contrast(c: float):
+    """nu(x, y) = 1 + (c - 1)(1/2 + 1/2 sin(2 pi x) cos(2 pi y)) (contrast c)."""
+    return lambda x, y: 1.0 + (c - 1.0) * (0.5 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y))
+
+
+def nu_paper(amplitude: float, shift: float):
+    """nu(x, y) = 1 + a sin(2 pi (x - s)) sin(2 pi (y - s))."""
+    return lambda x, y: 1.0 + amplitude * np.sin(2 * np.pi * (x - shift)) * np.sin(2 * np.pi * (y - shift))

@@ -1,0 +1,89 @@
+"""Pins of the oracle's variable-diffusivity path (Sec. 4.3): operator
+identities, spectral convergence of a manufactured solution, and the values
+the paper prints for its variable-diffusion study."""
+import math
+
+import numpy as np
+import pytest
+
+import sem_inputs as SI
+from oracle import sem_oracle as O
+from tests._golden import rows
+
+
+def _lev(nu, p=6, edges=None, periodic=False):
+    mx = O.Mesh1D.uniform(3, 1.0, periodic) if edges is None else O.Mesh1D(np.asarray(edges), periodic)
+    return O.Level(mx, O.Mesh1D.uniform(2, 1.0, periodic), p, 1, nu=nu)
+
+
+def test_unit_and_constant_diffusivity_reduce_to_poisson():
+    edges = [0.0, 0.2, 0.7, 1.0]
+    A = _lev(None, edges=edges).dense_operator()
+    B1 = _lev(lambda x, y: 1.0 + 0 * x * y, edges=edges).dense_operator()
+    B3 = _lev(lambda x, y: 3.0 + 0 * x * y, edges=edges).dense_operator()
+    np.testing.assert_allclose(B1, A, atol=1e-12 * np.abs(A).max())
+    np.testing.assert_allclose(B3, 3 * A, atol=1e-12 * np.abs(A).max())
+
+
+def test_variable_operator_symmetric_positive_definite():
+    B = _lev(SI.nu_contrast(50.0), edges=[0.0, 0.1, 0.5, 1.0]).dense_operator()
+    assert np.abs(B - B.T).max() < 1e-11 * np.abs(B).max()
+    assert np.linalg.eigvalsh(B).min() > 0
+
+
+def test_variable_diffusion_spectral_convergence():
+    """-div(nu grad u) = f with u = sin(pi x) sin(pi y), nu = 2 + sin(x + 2y):
+    the dense-solve error decays exponentially in p."""
+    nu = lambda x, y: 2.0 + np.sin(x + 2 * y)
+
+    def f(x, y):
+        u = np.sin(np.pi * x) * np.sin(np.pi * y)
+        ux = np.pi * np.cos(np.pi * x) * np.sin(np.pi * y)
+        uy = np.pi * np.sin(np.pi * x) * np.cos(np.pi * y)
+        nux, nuy = np.cos(x + 2 * y), 2 * np.cos(x + 2 * y)
+        return nu(x, y) * 2 * np.pi**2 * u - (nux * ux + nuy * uy)
+
+    errs = []
+    for p in [2, 4, 6, 8, 10]:
+        lev = O.Level(O.Mesh1D.uniform(2, 1.0, False), O.Mesh1D.uniform(2, 1.0, False), p, 1, nu=nu)
+        X, Y = lev.mx.coords(p), lev.my.coords(p)
+        b = lev.mass(f(X[None, :], Y[:, None]))
+        B = lev.dense_operator()
+        idx = np.flatnonzero(lev.unknown.ravel())
+        x = np.linalg.solve(B, b.ravel()[idx])
+        ue = (np.sin(np.pi * X[None, :]) * np.sin(np.pi * Y[:, None])).ravel()[idx]
+        errs.append(np.abs(x - ue).max())
+    assert all(errs[i + 1] < 0.2 * errs[i] for i in range(4))
+    assert errs[-1] < 1e-7
+
+
+def _paper_case(nu_hat):
+    s0 = 0.2
+    nu = SI.nu_paper(nu_hat, s0)
+
+    def f(x, y):
+        u_lap = -2 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+        ux = 2 * np.pi * np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y)
+        uy = 2 * np.pi * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        nux = nu_hat * 2 * np.pi * np.cos(2 * np.pi * (x - s0)) * np.sin(2 * np.pi * (y - s0))
+        nuy = nu_hat * 2 * np.pi * np.sin(2 * np.pi * (x - s0)) * np.cos(2 * np.pi * (y - s0))
+        return -(nu(x, y) * u_lap + nux * ux + nuy * uy)
+
+    H = O.Hierarchy(O.Mesh1D.uniform(8, 1.0, True), O.Mesh1D.uniform(8, 1.0, True), 16, overlap="ceil8",
+                    weight=5, nu=nu)
+    lev = H.top
+    X, Y = lev.mx.coords(16), lev.my.coords(16)
+    b = lev.mass(f(X[None, :], Y[:, None]))
+    u0 = SI.uniform_nodal(1, b.shape, 0.0, 1.0)
+    _, it, hist = H.mgcg(u0, b, n1=1, n2=1, tol=1e-10, i_max=100)
+    return O.rate(hist)
+
+
+def test_variable_diffusion_matches_paper_values():
+    vals = {r[0]: float(r[1]) for r in rows("variable_diffusion.txt")}
+    r9 = _paper_case(0.9)
+    r0 = _paper_case(0.0)
+    want = vals["mgcg_rbar_at_nu_hat_0.9"]
+    assert abs(r9 - want) <= 0.05 * want + 0.02, r9
+    ratio = math.ceil(10 / r9) / math.ceil(10 / r0)
+    assert abs(ratio - vals["cycle_ratio_nu_hat_0.9_over_0"]) <= 0.25, ratio
