@@ -57,7 +57,8 @@ typedef enum sem_weight {
   SEM_W_SEPTIC = 7,
   SEM_W_TOPHAT = 100,
   SEM_W_ARITH = 101,
-  SEM_W_IDENTITY = 102
+  SEM_W_IDENTITY = 102,
+  SEM_W_LEARNED = 103   /* per-interface (s, kt) from sem_config.learned_x/y */
 } sem_weight;
 
 /* Overlap n_{o,l} per level (Sec. 4): a fixed count, floor(p_l/8),
@@ -109,6 +110,15 @@ typedef struct sem_config {
    * FP64 inverse of B_0(nu).  Dirichlet walls only. */
   int32_t nu_kind;
   double nu_a, nu_b;
+  /* SEM_W_LEARNED: optional HOST arrays [level 0..L][interface 0..n][2] of
+   * (s, kt) per interface line (interface i between elements i-1 and i;
+   * entries of wall interfaces are ignored).  The transition of Eq. (weight
+   * function) at the interface has half width s delta_O min(h_left, h_right)/2
+   * (s in (0, 1]) and shape degree kt in [1, 7], a convex blend of the
+   * neighbouring odd degrees of Table (weighting).  Both sides of an
+   * interface use the same pair, so the weights keep the partition of unity. */
+  const double* learned_x;
+  const double* learned_y;
 } sem_config;
 
 typedef struct sem_result {
@@ -254,6 +264,37 @@ typedef struct sem_sweep_tables {
 } sem_sweep_tables;
 int sem_schwarz_correction_noalloc(const sem_sweep_tables* x, const sem_sweep_tables* y, const double* r,
                                    double* u, void* stream);
+
+/* ---- learned weights: the MLP of the interface-line parameters -------------
+ * Not in the paper: a small FP32 network (4 -> 64 -> 64 -> 2, ReLU) maps the
+ * features of an interface line to the parameters (s, kt) of
+ * SEM_W_LEARNED, trained on convergence rates that the plain method measures
+ * in parameter sweeps; the quintic weights w_5 (s = 1, kt = 5) stay the
+ * fallback.  Parameter vector: SEM_MLP_PARAMS floats, W1 (64x4), b1 (64),
+ * W2 (64x64), b2 (64), W3 (2x64), b3 (2), row-major.  All pointers are DEVICE
+ * pointers; calls are async on `stream`.  Loss L = (1/2N) sum (o - t)^2.
+ * Errors: SEM_BAD_ARG, SEM_CUDA_ERROR. */
+#define SEM_MLP_PARAMS 4610
+/* Features per interface line (host, no device work), written for every
+ * level 0..L and interface 0..n of each direction ([level][interface][4]):
+ * log2(p_l)/5, delta_O/2, log2(AR)/5 with AR the largest element aspect
+ * ratio next to the line, log10(rho)/2 with rho the largest ratio of element
+ * mean diffusivities across the line.  Caller-owned HOST arrays. */
+int sem_learned_features(const sem_config* cfg, float* feat_x, float* feat_y);
+/* Y[n][2] = network outputs for X[n][4]; transform = 1 maps them to
+ * (s, kt) = (0.25 + 0.75 sigmoid(o0), 1 + 6 sigmoid(o1)). */
+int sem_mlp_forward(const float* params, const float* X, int32_t n, float* Y, int32_t transform, void* stream);
+/* Bytes of the caller-provided workspace for n samples. */
+int64_t sem_mlp_workspace_bytes(int32_t n);
+/* grad[SEM_MLP_PARAMS] and *loss (DEVICE) of the mean-squared loss against
+ * targets T[n][2] (backpropagation, deterministic reduction over samples). */
+int sem_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t n, float* grad, float* loss,
+                      void* workspace, void* stream);
+/* `steps` full-batch Adam steps (lr, beta = 0.9 / 0.999, eps 1e-8) from step
+ * count step0; adam_m / adam_v hold the moments (zero at the start);
+ * loss_hist (DEVICE, may be NULL) receives the loss before each step. */
+int sem_mlp_train(float* params, float* adam_m, float* adam_v, const float* X, const float* T, int32_t n,
+                  int32_t steps, float lr, int32_t step0, float* loss_hist, void* workspace, void* stream);
 
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);

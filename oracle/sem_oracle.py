@@ -235,6 +235,15 @@ def phi(kappa, x):
     return np.where(np.abs(x) < 1.0, phi_hat(kappa, np.clip(x, -1, 1)), np.sign(x))
 
 
+def phi_blend(kt, x):
+    """Shape function of continuous degree kt in [1, 7]: convex blend of the two
+    neighbouring odd degrees of Table (weighting) (learned weights, R15)."""
+    t = min(3.0, max(0.0, 0.5 * (kt - 1.0)))
+    k0 = min(2, int(t))
+    fr = t - k0
+    return (1 - fr) * phi(2 * k0 + 1, x) + fr * phi(2 * k0 + 3, x)
+
+
 # ---------------------------------------------------------------------------
 # One multigrid level: operator, subdomains, FDM factors, weights
 # ---------------------------------------------------------------------------
@@ -254,8 +263,11 @@ class Sub1D:
 class Level:
     """Operator and Schwarz data at polynomial order p on a Cartesian mesh."""
 
-    def __init__(self, mx: Mesh1D, my: Mesh1D, p: int, n_o: int, weight=5, nu=None):
+    def __init__(self, mx: Mesh1D, my: Mesh1D, p: int, n_o: int, weight=5, nu=None, learned=None):
         self.mx, self.my, self.p, self.n_o, self.weight = mx, my, p, n_o, weight
+        # learned weights: (params_x, params_y), each (n+1, 2) arrays of (s, kt)
+        # per interface i between elements i-1 and i
+        self.learned = learned
         self.NX, self.NY = mx.nodes(p), my.nodes(p)
         self.unknown = my.unknown(p)[:, None] & mx.unknown(p)[None, :]
         self.gx, self.gy = mx.gidx(p), my.gidx(p)
@@ -271,8 +283,8 @@ class Level:
         self.nu = None
         if nu is not None:
             self._setup_variable(nu)
-        self.sub_x = [self._sub1d(mx, e, self.Mx_glob, self.Lx_glob) for e in range(mx.n)]
-        self.sub_y = [self._sub1d(my, e, self.My_glob, self.Ly_glob) for e in range(my.n)]
+        self.sub_x = [self._sub1d(mx, e, self.Mx_glob, self.Lx_glob, 0) for e in range(mx.n)]
+        self.sub_y = [self._sub1d(my, e, self.My_glob, self.Ly_glob, 1) for e in range(my.n)]
         if weight == "a":
             self._arith_weights()
 
@@ -349,8 +361,8 @@ class Level:
                 s[t] = h[e] + (1.0 + xi[kk - p]) * hr / 2
         return s
 
-    def _weights_1d(self, mesh: Mesh1D, e: int, k: np.ndarray) -> np.ndarray:
-        """1D weights of Eq. (weight function), readings R3-R5."""
+    def _weights_1d(self, mesh: Mesh1D, e: int, k: np.ndarray, axis: int = 0) -> np.ndarray:
+        """1D weights of Eq. (weight function), readings R3-R5 (learned: R15)."""
         if self.weight == "I":
             return np.ones(len(k))
         if self.weight == "a":
@@ -360,19 +372,28 @@ class Level:
         h = mesh.h
         s = self._positions(mesh, e, k)
         left, right = mesh.neighbour(e, -1), mesh.neighbour(e, +1)
+        if self.weight == "learned":
+            prm = np.asarray(self.learned[axis])
+            il, ir = e, (e + 1) % mesh.n if mesh.periodic else e + 1
+            (sl, kl), (sr, kr) = prm[il], prm[ir]
+            shape_l = lambda x: phi_blend(kl, x)
+            shape_r = lambda x: phi_blend(kr, x)
+        else:
+            sl = sr = 1.0
+            shape_l = shape_r = lambda x: phi(self.weight, x)
         if left is None:
             tl = np.ones(len(k))
         else:
-            dl = dO * min(h[left], h[e]) / 2
-            tl = phi(self.weight, s / dl)
+            dl = sl * dO * min(h[left], h[e]) / 2
+            tl = shape_l(s / dl)
         if right is None:
             tr = -np.ones(len(k))
         else:
-            dr = dO * min(h[e], h[right]) / 2
-            tr = phi(self.weight, (s - h[e]) / dr)
+            dr = sr * dO * min(h[e], h[right]) / 2
+            tr = shape_r((s - h[e]) / dr)
         return 0.5 * (tl - tr)
 
-    def _sub1d(self, mesh: Mesh1D, e: int, Mg: np.ndarray, Lg: np.ndarray) -> Sub1D:
+    def _sub1d(self, mesh: Mesh1D, e: int, Mg: np.ndarray, Lg: np.ndarray, axis: int = 0) -> Sub1D:
         p, n_o = self.p, self.n_o
         k = np.arange(-n_o, p + n_o + 1)
         g = e * p + k
@@ -388,7 +409,7 @@ class Level:
         Lt = Lg[np.ix_(g, g)]            # restricted stiffness  R L R^T
         Mt = Mg[g]                       # restricted mass (diagonal)
         lam, S = sla.eigh(Lt, np.diag(Mt))   # L~ s = lambda M~ s,  S^T M~ S = I
-        return Sub1D(g=g, k=k, S=S, lam=lam, w=self._weights_1d(mesh, e, k))
+        return Sub1D(g=g, k=k, S=S, lam=lam, w=self._weights_1d(mesh, e, k, axis))
 
     def _arith_weights(self):
         """w_a: W = R_s C^+ R_s^T with C = sum_s R_s^T R_s (Sec. 3.1, R2)."""
@@ -486,6 +507,7 @@ class Hierarchy:
     weight: object = 5
     nu: object = None
     smoother: str = "add"
+    learned: object = None  # (params_x, params_y): arrays [level][interface][2]
     levels: list = field(default_factory=list)
 
     def __post_init__(self):
@@ -500,7 +522,8 @@ class Hierarchy:
             if l == 0:
                 lev = _CoarseLevel(self.mx, self.my, self.nu)
             else:
-                lev = Level(self.mx, self.my, pl, no, weight=self.weight, nu=self.nu)
+                lrn = None if self.learned is None else (self.learned[0][l], self.learned[1][l])
+                lev = Level(self.mx, self.my, pl, no, weight=self.weight, nu=self.nu, learned=lrn)
             self.levels.append(lev)
         self.Px = [None] + [prolongation_1d(self.mx, 2**l, 2**(l - 1)) for l in range(1, L + 1)]
         self.Py = [None] + [prolongation_1d(self.my, 2**l, 2**(l - 1)) for l in range(1, L + 1)]

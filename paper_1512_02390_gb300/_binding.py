@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsemschwarz.so")
 SEM_OK, SEM_NOT_CONVERGED, SEM_BREAKDOWN, SEM_TIMEOUT, SEM_BAD_ARG, SEM_CUDA_ERROR, SEM_OOM = range(7)
 # sem_weight
 SEM_W_LINEAR, SEM_W_CUBIC, SEM_W_QUINTIC, SEM_W_SEPTIC = 1, 3, 5, 7
-SEM_W_TOPHAT, SEM_W_ARITH, SEM_W_IDENTITY = 100, 101, 102
+SEM_W_TOPHAT, SEM_W_ARITH, SEM_W_IDENTITY, SEM_W_LEARNED = 100, 101, 102, 103
 # sem_overlap_rule
 SEM_OVERLAP_FIXED, SEM_OVERLAP_FLOOR8, SEM_OVERLAP_CEIL8, SEM_OVERLAP_CEIL2 = range(4)
 # sem_precision
@@ -30,8 +30,10 @@ EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
     "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
+    "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_status_string", "sem_last_error",
 ]
+SEM_MLP_PARAMS = 4610
 # sem_kernel_class
 KERNEL_CLASSES = ["apply_fp64", "apply_mg", "sweep", "scatter", "restrict", "prolong", "coarse", "vector"]
 
@@ -45,6 +47,7 @@ class sem_config(ctypes.Structure):
         ("ns1", ctypes.c_int32), ("ns2", ctypes.c_int32), ("variable_cycle", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("i_max", ctypes.c_int32),
         ("nu_kind", ctypes.c_int32), ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double),
+        ("learned_x", ctypes.POINTER(ctypes.c_double)), ("learned_y", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -101,6 +104,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "sem_schwarz_correction_noalloc": (i32, [ctypes.POINTER(sem_sweep_tables), ctypes.POINTER(sem_sweep_tables),
                                                  vp, vp, vp]),
+        "sem_learned_features": (i32, [ctypes.POINTER(sem_config), vp, vp]),
+        "sem_mlp_forward": (i32, [vp, vp, i32, vp, i32, vp]),
+        "sem_mlp_workspace_bytes": (ctypes.c_int64, [i32]),
+        "sem_mlp_loss_grad": (i32, [vp, vp, vp, i32, vp, vp, vp, vp]),
+        "sem_mlp_train": (i32, [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, i32, vp, vp, vp]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -259,3 +267,42 @@ def sem_schwarz_correction_noalloc(tx: sem_sweep_tables, ty: sem_sweep_tables, r
     """u += sum_s R_s^T W A_ss^{-1} R_s r without any allocation (see the C header for who needs this)."""
     _check(load_library().sem_schwarz_correction_noalloc(ctypes.byref(tx), ctypes.byref(ty), _ptr(r), _ptr(u),
                                                          _stream(stream)))
+
+
+def _fptr(t):
+    """Device address of a contiguous CUDA float32 tensor (None passes through)."""
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    return t.data_ptr()
+
+
+def sem_learned_features(cfg: sem_config):
+    """Features [level][interface][4] of the x and y interface lines (host)."""
+    L = int(np.log2(cfg.p))
+    fx = np.zeros((L + 1, cfg.nx + 1, 4), dtype=np.float32)
+    fy = np.zeros((L + 1, cfg.ny + 1, 4), dtype=np.float32)
+    _check(load_library().sem_learned_features(ctypes.byref(cfg), fx.ctypes.data, fy.ctypes.data))
+    return fx, fy
+
+
+def sem_mlp_forward(params, X, Y, transform=True, stream=None):
+    _check(load_library().sem_mlp_forward(_fptr(params), _fptr(X), int(X.shape[0]), _fptr(Y), int(bool(transform)),
+                                          _stream(stream)))
+
+
+def sem_mlp_workspace_bytes(n: int) -> int:
+    return int(load_library().sem_mlp_workspace_bytes(int(n)))
+
+
+def sem_mlp_loss_grad(params, X, T, grad, loss, workspace, stream=None):
+    _check(load_library().sem_mlp_loss_grad(_fptr(params), _fptr(X), _fptr(T), int(X.shape[0]), _fptr(grad),
+                                            _fptr(loss), _fptr(workspace), _stream(stream)))
+
+
+def sem_mlp_train(params, m, v, X, T, steps, lr, step0, loss_hist, workspace, stream=None):
+    _check(load_library().sem_mlp_train(_fptr(params), _fptr(m), _fptr(v), _fptr(X), _fptr(T), int(X.shape[0]),
+                                        int(steps), float(lr), int(step0), _fptr(loss_hist), _fptr(workspace),
+                                        _stream(stream)))

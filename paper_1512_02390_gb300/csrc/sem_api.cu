@@ -164,7 +164,8 @@ int overlap_for(const sem_config& c, int pl) {
 }
 
 bool valid_weight(int w) {
-  return w == 1 || w == 3 || w == 5 || w == 7 || w == SEM_W_TOPHAT || w == SEM_W_ARITH || w == SEM_W_IDENTITY;
+  return w == 1 || w == 3 || w == 5 || w == 7 || w == SEM_W_TOPHAT || w == SEM_W_ARITH || w == SEM_W_IDENTITY ||
+         w == SEM_W_LEARNED;
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -524,6 +525,17 @@ static int validate(const sem_config& c, int& L) {
     return fail(SEM_BAD_ARG, "need 0 <= ns1, ns2 <= 64 and ns1 + ns2 >= 1");
   if (!(c.tol >= 0.0) || c.i_max < 1 || c.i_max > 100000) return fail(SEM_BAD_ARG, "invalid tol or i_max");
   if (c.nu_kind < 0 || c.nu_kind > 2) return fail(SEM_BAD_ARG, "unknown nu_kind");
+  if (c.weight == SEM_W_LEARNED) {
+    if (!c.learned_x || !c.learned_y) return fail(SEM_BAD_ARG, "learned weights need learned_x and learned_y");
+    for (int lvl = 0; lvl <= L; ++lvl)
+      for (int dir = 0; dir < 2; ++dir) {
+        const int n = dir ? c.ny : c.nx;
+        const double* a = (dir ? c.learned_y : c.learned_x) + (size_t)lvl * (n + 1) * 2;
+        for (int i = 0; i <= n; ++i)
+          if (!(a[2 * i] > 0.0 && a[2 * i] <= 1.0) || !(a[2 * i + 1] >= 1.0 && a[2 * i + 1] <= 7.0))
+            return fail(SEM_BAD_ARG, "learned (s, kt) must satisfy 0 < s <= 1, 1 <= kt <= 7");
+      }
+  }
   if (c.nu_kind && c.periodic) return fail(SEM_BAD_ARG, "variable diffusivity needs Dirichlet walls");
   if (c.nu_kind == 1 && !(c.nu_a >= 1.0)) return fail(SEM_BAD_ARG, "contrast must be >= 1");
   if (c.nu_kind == 2 && !(std::fabs(c.nu_a) < 1.0)) return fail(SEM_BAD_ARG, "amplitude must be in (-1, 1)");
@@ -557,7 +569,8 @@ int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info
   const int p = 1 << level;
   const int no = overlap_for(*cfg, p);
   Dir1D d;
-  std::string err = build_dir(mx, p, no, cfg->weight, d);
+  const double* lx = cfg->learned_x ? cfg->learned_x + (size_t)level * (cfg->nx + 1) * 2 : nullptr;
+  std::string err = build_dir(mx, p, no, cfg->weight, d, lx);
   if (!err.empty()) return fail(SEM_BAD_ARG, err);
   info->p = p;
   info->n_o = no;
@@ -576,6 +589,63 @@ int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info
   return SEM_OK;
 }
 
+int sem_learned_features(const sem_config* cfg, float* feat_x, float* feat_y) {
+  g_err.clear();
+  if (!cfg || !feat_x || !feat_y) return fail(SEM_BAD_ARG, "null argument");
+  sem_config c = *cfg;
+  if (c.weight == SEM_W_LEARNED) c.weight = SEM_W_QUINTIC;  // features do not depend on the weights
+  int L, rc;
+  if ((rc = validate(c, L))) return rc;
+  Mesh1D mx, my;
+  if (!make_mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, mx) || !make_mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, my))
+    return fail(SEM_BAD_ARG, "mesh edges must increase");
+  for (int l = 0; l <= L; ++l) {
+    const int pl = 1 << l;
+    const int no = l > 0 ? overlap_for(c, pl) : 0;
+    std::vector<double> xi, w;
+    gll(pl, xi, w);
+    const double dO = xi[no + 1] + 1.0;
+    std::vector<double> nub((size_t)mx.n * my.n, 1.0);
+    if (c.nu_kind) {
+      VarData vd;
+      build_var(mx, my, pl, c.nu_kind, c.nu_a, c.nu_b, vd);
+      nub = vd.nu_bar;
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      const Mesh1D& ma = dir ? my : mx;  // direction across the line
+      const Mesh1D& mb = dir ? mx : my;  // direction along the line
+      float* out = (dir ? feat_y : feat_x) + (size_t)l * (ma.n + 1) * 4;
+      for (int i = 0; i <= ma.n; ++i) {
+        int e0 = i - 1, e1 = i;
+        if (ma.periodic) {
+          e0 = (e0 + ma.n) % ma.n;
+          e1 = e1 % ma.n;
+        }
+        double ar = 1.0, rho = 1.0;
+        for (int side = 0; side < 2; ++side) {
+          const int e = side ? e1 : e0;
+          if (e < 0 || e >= ma.n) continue;
+          for (int j = 0; j < mb.n; ++j) {
+            const double r = ma.h(e) / mb.h(j);
+            ar = std::max(ar, std::max(r, 1.0 / r));
+          }
+        }
+        if (e0 >= 0 && e0 < ma.n && e1 >= 0 && e1 < ma.n)
+          for (int j = 0; j < mb.n; ++j) {
+            const double a = dir ? nub[(size_t)e0 * mx.n + j] : nub[(size_t)j * mx.n + e0];
+            const double b = dir ? nub[(size_t)e1 * mx.n + j] : nub[(size_t)j * mx.n + e1];
+            rho = std::max(rho, std::max(a / b, b / a));
+          }
+        out[4 * i + 0] = (float)(l / 5.0);
+        out[4 * i + 1] = (float)(dO / 2.0);
+        out[4 * i + 2] = (float)(std::log2(ar) / 5.0);
+        out[4 * i + 3] = (float)(std::log10(rho) / 2.0);
+      }
+    }
+  }
+  return SEM_OK;
+}
+
 int sem_create(const sem_config* cfg, sem_handle** out) {
   g_err.clear();
   if (!cfg || !out) return fail(SEM_BAD_ARG, "null argument");
@@ -589,6 +659,7 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
   sem_handle* h = new sem_handle();
   h->cfg = c;
   h->cfg.x_edges = h->cfg.y_edges = nullptr;
+  h->cfg.learned_x = h->cfg.learned_y = nullptr;
   if (!mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, h->mx) || !mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, h->my)) {
     delete h;
     return fail(SEM_BAD_ARG, "mesh edges must increase");
@@ -621,8 +692,10 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     lv.n_o = l > 0 ? overlap_for(c, lv.p) : 0;
     lv.m = lv.p + 1 + 2 * lv.n_o;
     Dir1D dx, dy;
-    std::string err = build_dir(h->mx, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dx);
-    if (err.empty()) err = build_dir(h->my, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dy);
+    const double* lx = c.learned_x ? c.learned_x + (size_t)l * (c.nx + 1) * 2 : nullptr;
+    const double* ly = c.learned_y ? c.learned_y + (size_t)l * (c.ny + 1) * 2 : nullptr;
+    std::string err = build_dir(h->mx, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dx, lx);
+    if (err.empty()) err = build_dir(h->my, lv.p, lv.n_o, l > 0 ? c.weight : SEM_W_IDENTITY, dy, ly);
     if (!err.empty()) {
       sem_destroy(h);
       return fail(SEM_BAD_ARG, "level p=" + std::to_string(lv.p) + ": " + err);

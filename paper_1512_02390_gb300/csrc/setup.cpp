@@ -181,7 +181,15 @@ double shape_phi(int kappa, double x) {
   }
 }
 
-std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o) {
+double shape_phi_blend(double kt, double x) {
+  if (!(std::fabs(x) < 1.0)) return (x > 0) - (x < 0);
+  const double t = std::min(3.0, std::max(0.0, 0.5 * (kt - 1.0)));
+  const int k0 = std::min(2, (int)t);
+  const double fr = t - k0;
+  return (1.0 - fr) * shape_phi(2 * k0 + 1, x) + fr * shape_phi(2 * k0 + 3, x);
+}
+
+std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o, const double* learned) {
   const int n = mesh.n, N = mesh.nodes(p), np1 = p + 1, m = p + 1 + 2 * n_o;
   if (m > N) return "subdomain window larger than the periodic mesh";
   o.n = n; o.p = p; o.n_o = n_o; o.m = m; o.N = N; o.periodic = mesh.periodic;
@@ -236,7 +244,7 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o) 
       if (v) cnt[g]++;
     }
   const double dO = xi[n_o + 1] + 1.0;  // Eq. (overlap width)
-  std::map<std::tuple<int, int, double, double, double>, int> seen;
+  std::map<std::tuple<int, int, double, double, double, double, double, double, double>, int> seen;
   o.tab.assign(n, 0);
   o.tables.clear();
   for (int e = 0; e < n; ++e) {
@@ -244,7 +252,17 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o) 
     double hl = L >= 0 ? mesh.h(L) : 0.0, hr = R >= 0 ? mesh.h(R) : 0.0, he = mesh.h(e);
     // elements with identical geometry share tables (arith weights depend on
     // counts, which are equal for equal geometry and wall status)
-    auto key = std::make_tuple(L >= 0 ? 1 : 0, R >= 0 ? 1 : 0, hl, he, hr);
+    // learned parameters of the element's left (interface e) and right
+    // (interface e + 1) transitions
+    double sl = 1.0, kl = 5.0, sr = 1.0, kr = 5.0;
+    if (weight == 103 && learned) {
+      const int il = e, ir = mesh.periodic ? (e + 1) % n : e + 1;
+      sl = learned[2 * il];
+      kl = learned[2 * il + 1];
+      sr = learned[2 * ir];
+      kr = learned[2 * ir + 1];
+    }
+    auto key = std::make_tuple(L >= 0 ? 1 : 0, R >= 0 ? 1 : 0, hl, he, hr, sl, kl, sr, kr);
     if (weight != 101) {
       auto it = seen.find(key);
       if (it != seen.end()) { o.tab[e] = it->second; continue; }
@@ -282,6 +300,13 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o) 
         wv = 1.0;
       } else if (weight == 101) {
         wv = 1.0 / cnt[gl[i]];
+      } else if (weight == 103) {
+        double tl = 1.0, tr = -1.0;
+        if (L >= 0) tl = shape_phi_blend(kl, s / (sl * dO * std::min(hl, he) / 2.0));
+        if (R >= 0) tr = shape_phi_blend(kr, (s - he) / (sr * dO * std::min(he, hr) / 2.0));
+        if (k == 0 && L >= 0) tl = 0.0;
+        if (k == p && R >= 0) tr = 0.0;
+        wv = 0.5 * (tl - tr);
       } else {
         double tl = 1.0, tr = -1.0;
         if (L >= 0) tl = shape_phi(weight, s / (dO * std::min(hl, he) / 2.0));

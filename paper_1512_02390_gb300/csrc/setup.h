@@ -41,6 +41,9 @@ bool gen_eig_diag(int n, const std::vector<double>& A, const std::vector<double>
 
 // Shape function phi_kappa of Eq. (shape function) for weight id kappa.
 double shape_phi(int kappa, double x);
+// Shape function of continuous degree kt in [1, 7]: the convex blend of the
+// two neighbouring odd degrees of Table (weighting), sgn outside (-1, 1).
+double shape_phi_blend(double kt, double x);
 
 // Factors of the extended-element subdomains of one direction of one level,
 // padded to the interior window size m = p + 1 + 2 n_o.  Window slot a holds
@@ -63,9 +66,11 @@ struct Dir1D {
   std::vector<SubTable> tables;
 };
 
-// Build one direction of one level.  weight: sem_weight id.  Returns "" or an
-// error message.
-std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& out);
+// Build one direction of one level.  weight: sem_weight id.  learned (weight
+// SEM_W_LEARNED): per interface i = 0..n (between elements i-1 and i) the
+// pair (s, kt): transition half width scale and shape degree.  Returns "" or
+// an error message.
+std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& out, const double* learned = nullptr);
 
 // Coarse (p = 1) factors: generalised eigenpairs of the assembled 1D pair over
 // the unknowns (Dirichlet: nodes 1..n-1; periodic: 0..n-1), and c = S^T 1.

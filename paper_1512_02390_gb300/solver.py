@@ -8,14 +8,14 @@ import numpy as np
 from . import _binding as B
 
 _WEIGHTS = {1: B.SEM_W_LINEAR, 3: B.SEM_W_CUBIC, 5: B.SEM_W_QUINTIC, 7: B.SEM_W_SEPTIC,
-            "t": B.SEM_W_TOPHAT, "a": B.SEM_W_ARITH, "I": B.SEM_W_IDENTITY}
+            "t": B.SEM_W_TOPHAT, "a": B.SEM_W_ARITH, "I": B.SEM_W_IDENTITY, "learned": B.SEM_W_LEARNED}
 _OVERLAP = {"floor8": B.SEM_OVERLAP_FLOOR8, "ceil8": B.SEM_OVERLAP_CEIL8, "ceil2": B.SEM_OVERLAP_CEIL2}
 _PREC = {"fp64": B.SEM_PREC_FP64, "fp32": B.SEM_PREC_FP32, "tf32": B.SEM_PREC_TF32, "bf16": B.SEM_PREC_BF16}
 
 
 def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weight=5, ns1=1, ns2=0,
                 variable_cycle=False, precision="fp64", tol=1e-10, i_max=200, x_edges=None, y_edges=None,
-                nu=None):
+                nu=None, learned_x=None, learned_y=None):
     """nu: None (Poisson), ("contrast", c) or ("paper", amplitude, shift)."""
     cfg = B.sem_default_config()
     cfg.nx, cfg.ny, cfg.p, cfg.periodic = nx, ny, p, int(bool(periodic))
@@ -36,7 +36,7 @@ def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weig
         else:
             raise ValueError(nu)
     keep = []
-    for name, e in (("x_edges", x_edges), ("y_edges", y_edges)):
+    for name, e in (("x_edges", x_edges), ("y_edges", y_edges), ("learned_x", learned_x), ("learned_y", learned_y)):
         if e is not None:
             arr = np.ascontiguousarray(e, dtype=np.float64)
             keep.append(arr)

@@ -1,0 +1,94 @@
+"""The MLP kernels of the learned weights against the FP64 oracle: forward
+to 1e-5 relative (FP32), gradient to 1e-4, training lowers the loss, and the
+trained model's weights beat the fixed quintic weights on a stretched,
+high-contrast problem."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import sem_inputs as SI
+from oracle import mlp_oracle as M
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_1512_02390_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load_library()
+
+
+def _f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _data(seed, n):
+    prm = SI.uniform_nodal(seed, (M.N_PARAMS,), -0.4, 0.4).astype(np.float32)
+    X = SI.uniform_nodal(seed + 1, (n, 4), -1.0, 1.0).astype(np.float32)
+    T = SI.uniform_nodal(seed + 2, (n, 2), -2.0, 2.0).astype(np.float32)
+    return prm, X, T
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 200])
+def test_forward_matches_oracle(n):
+    prm, X, _ = _data(11, n)
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    P.sem_mlp_forward(_f32(prm), _f32(X), Y, transform=False)
+    o, _ = M.forward(prm.astype(np.float64), X.astype(np.float64))
+    got = Y.cpu().numpy()
+    assert np.abs(got - o).max() <= 1e-5 * np.abs(o).max()
+    P.sem_mlp_forward(_f32(prm), _f32(X), Y, transform=True)
+    np.testing.assert_allclose(Y.cpu().numpy(), M.to_weight_params(o), rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("n", [5, 130])
+def test_gradient_matches_backprop(n):
+    prm, X, T = _data(21, n)
+    ws = torch.zeros(P.sem_mlp_workspace_bytes(n) // 4 + 1, dtype=torch.float32, device="cuda")
+    g = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    P.sem_mlp_loss_grad(_f32(prm), _f32(X), _f32(T), g, loss, ws)
+    lo, go = M.loss_grad(prm.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(float(loss.item()) - lo) <= 1e-5 * lo
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-4 * np.abs(go).max()
+
+
+def test_training_lowers_the_loss():
+    n = 256
+    X = SI.uniform_nodal(31, (n, 4), -1.0, 1.0).astype(np.float32)
+    T = np.stack([np.sin(2 * X[:, 0]) + X[:, 1], X[:, 2] * X[:, 3]], axis=1).astype(np.float32)
+    from paper_1512_02390_gb300 import learned as LW
+    prm, hist = LW.train(X, T, steps=400, lr=3e-3)
+    lo, _ = M.loss_grad(LW.init_params(0).astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(hist[0] - lo) <= 1e-4 * lo          # first recorded loss = oracle loss of the start point
+    assert hist[-1] < 0.1 * hist[0]
+    lf, _ = M.loss_grad(prm.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert lf < 0.1 * lo
+
+
+def test_trained_model_beats_quintic_weights_on_stretched_high_contrast_mesh():
+    from paper_1512_02390_gb300 import learned as LW
+    if not os.path.exists(LW.MODEL_PATH):
+        pytest.skip("no trained model in the package")
+    params, meta = LW.load_model()
+    kw = dict(nx=16, ny=16, p=8, overlap=1, x_edges=SI.geometric_edges(16, 1.0 / 16 / 32), nu=("contrast", 100.0),
+              tol=1e-10, i_max=400)
+    px, py = LW.predict(params, **kw)
+    assert np.all((px[..., 0] > 0) & (px[..., 0] <= 1)) and np.all((px[..., 1] >= 1) & (px[..., 1] <= 7))
+    S5 = P.Solver(weight=5, **kw)
+    SL = P.Solver(weight="learned", learned_x=px.ravel(), learned_y=py.ravel(), **kw)
+    fn = torch.from_numpy(SI.uniform_nodal(3, S5.shape).ravel()).cuda()
+    b = torch.empty_like(fn)
+    S5.mass(fn, b)
+    r5, _ = S5.pcg_solve(torch.zeros_like(b), b)
+    rl, _ = SL.pcg_solve(torch.zeros_like(b), b)
+    print("MGCG iterations: w_5 %d (rbar %.3f), learned %d (rbar %.3f)" % (r5.iterations, r5.rbar, rl.iterations,
+                                                                           rl.rbar))
+    assert r5.status == P.SEM_OK and rl.status == P.SEM_OK
+    assert rl.iterations <= r5.iterations

@@ -19,7 +19,7 @@ def _declared_symbols():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(sem_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(sem_\w+)\s*\(", src, re.M))
     return names
 
 
