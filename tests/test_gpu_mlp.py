@@ -73,6 +73,10 @@ def test_training_lowers_the_loss():
 
 
 def test_trained_model_beats_quintic_weights_on_stretched_high_contrast_mesh():
+    """16 x 16 elements, p = 8, x geometrically stretched to 1:32, contrast 100:
+    with the fixed quintic weights MGCG stalls near 1e-2 (the oracle shows the
+    same; stretching alone or contrast alone converge), while the weights the
+    trained network predicts converge to 1e-10."""
     from paper_1512_02390_gb300 import learned as LW
     if not os.path.exists(LW.MODEL_PATH):
         pytest.skip("no trained model in the package")
@@ -90,5 +94,6 @@ def test_trained_model_beats_quintic_weights_on_stretched_high_contrast_mesh():
     rl, _ = SL.pcg_solve(torch.zeros_like(b), b)
     print("MGCG iterations: w_5 %d (rbar %.3f), learned %d (rbar %.3f)" % (r5.iterations, r5.rbar, rl.iterations,
                                                                            rl.rbar))
-    assert r5.status == P.SEM_OK and rl.status == P.SEM_OK
-    assert rl.iterations <= r5.iterations
+    assert rl.status == P.SEM_OK
+    assert rl.rbar > r5.rbar
+    assert r5.status != P.SEM_OK or rl.iterations <= r5.iterations
