@@ -296,6 +296,29 @@ int sem_mlp_loss_grad(const float* params, const float* X, const float* T, int32
 int sem_mlp_train(float* params, float* adam_m, float* adam_v, const float* X, const float* T, int32_t n,
                   int32_t steps, float lr, int32_t step0, float* loss_hist, void* workspace, void* stream);
 
+/* ---- batched solves ----------------------------------------------------------
+ * Not in the paper: many independent problems solved by Alg. 4 at once.
+ * Problems with identical uniform Dirichlet Poisson configurations (same mesh,
+ * p, overlap, weights, precision, tol, i_max) are stacked along y into one
+ * grid separated by wall rows, so every level kernel serves the whole group;
+ * each problem keeps its own MGCG scalars, residual test and iteration count.
+ * Other configurations form groups of one.  From the second sem_batch_solve
+ * on, all groups run as parallel branches of ONE captured CUDA graph (one
+ * launch; a WHILE node per group loops until its last problem converged).
+ * The batch owns all workspace; sem_batch_solve allocates nothing. */
+typedef struct sem_batch sem_batch;
+/* Set up n problems (sync).  Periodic problems are rejected (SEM_BAD_ARG). */
+int sem_batch_create(const sem_config* cfgs, int32_t n, sem_batch** out);
+void sem_batch_destroy(sem_batch* b);
+/* Groups formed and total unknowns (host). */
+int sem_batch_info(const sem_batch* b, int32_t* groups, int64_t* unknowns);
+/* Solve all problems (sync): u[k], f[k] are the DEVICE node grids of problem k
+ * (layout of a single sem_create of cfgs[k]); u in place; res[n] HOST results.
+ * Returns the largest status over the problems. */
+int sem_batch_solve(sem_batch* b, double* const* u, const double* const* f, sem_result* res, void* stream);
+/* Kernel launches of the batch since creation (tracing, host). */
+int sem_batch_launches(const sem_batch* b, int64_t* launches);
+
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);
 

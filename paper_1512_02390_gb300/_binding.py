@@ -31,6 +31,7 @@ EXPORTS = [
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
     "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
     "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
+    "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_status_string", "sem_last_error",
 ]
 SEM_MLP_PARAMS = 4610
@@ -109,6 +110,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_mlp_workspace_bytes": (ctypes.c_int64, [i32]),
         "sem_mlp_loss_grad": (i32, [vp, vp, vp, i32, vp, vp, vp, vp]),
         "sem_mlp_train": (i32, [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, i32, vp, vp, vp]),
+        "sem_batch_create": (i32, [ctypes.POINTER(sem_config), i32, ctypes.POINTER(vp)]),
+        "sem_batch_destroy": (None, [vp]),
+        "sem_batch_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]),
+        "sem_batch_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), vp]),
+        "sem_batch_launches": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -306,3 +312,36 @@ def sem_mlp_train(params, m, v, X, T, steps, lr, step0, loss_hist, workspace, st
     _check(load_library().sem_mlp_train(_fptr(params), _fptr(m), _fptr(v), _fptr(X), _fptr(T), int(X.shape[0]),
                                         int(steps), float(lr), int(step0), _fptr(loss_hist), _fptr(workspace),
                                         _stream(stream)))
+
+
+def sem_batch_create(cfgs):
+    arr = (sem_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    _check(load_library().sem_batch_create(arr, len(cfgs), ctypes.byref(h)))
+    return h
+
+
+def sem_batch_destroy(b) -> None:
+    load_library().sem_batch_destroy(b)
+
+
+def sem_batch_info(b):
+    g, u = ctypes.c_int32(), ctypes.c_int64()
+    _check(load_library().sem_batch_info(b, ctypes.byref(g), ctypes.byref(u)))
+    return g.value, u.value
+
+
+def sem_batch_solve(b, us, fs, stream=None):
+    n = len(us)
+    up = (ctypes.c_void_p * n)(*[_ptr(x) for x in us])
+    fp = (ctypes.c_void_p * n)(*[_ptr(x) for x in fs])
+    res = (sem_result * n)()
+    rc = load_library().sem_batch_solve(b, up, fp, res, _stream(stream))
+    _check(rc, allow=(SEM_OK, SEM_NOT_CONVERGED, SEM_BREAKDOWN))
+    return list(res)
+
+
+def sem_batch_launches(b) -> int:
+    v = ctypes.c_int64()
+    _check(load_library().sem_batch_launches(b, ctypes.byref(v)))
+    return v.value

@@ -14,6 +14,7 @@ struct DirView {
   int N;          // global nodes (periodic: n p; Dirichlet: n p + 1)
   int periodic;   // 1 periodic, 0 Dirichlet walls
   int n_o, m;     // overlap layers, window size p + 1 + 2 n_o
+  int segN;       // > 0: Dirichlet wall every segN nodes (independent problems stacked)
   const T* Le;    // n x (p+1)^2 element stiffness
   const T* Mg;    // N assembled mass diagonal
   const int* tab; // n subdomain table ids
@@ -23,13 +24,21 @@ struct DirView {
 };
 
 // wrap/validate a global node index of a direction; returns -1 if the node
-// does not exist or is a Dirichlet wall node (value 0 there)
-__device__ __forceinline__ int node_or_wall(int g, int N, int periodic) {
+// does not exist or is a Dirichlet wall node (value 0 there).  segN > 0 adds
+// internal walls every segN nodes (problems stacked along the direction).
+__device__ __forceinline__ int node_or_wall(int g, int N, int periodic, int segN = 0) {
   if (periodic) {
     g %= N;
     return g < 0 ? g + N : g;
   }
-  return (g > 0 && g < N - 1) ? g : -1;
+  if (!(g > 0 && g < N - 1)) return -1;
+  return (segN > 0 && g % segN == 0) ? -1 : g;
+}
+
+// is node g of a direction a Dirichlet wall node?
+__device__ __forceinline__ bool wall_node(int g, int N, int periodic, int segN = 0) {
+  if (periodic) return false;
+  return g == 0 || g == N - 1 || (segN > 0 && g % segN == 0);
 }
 
 constexpr int kRedThreads = 256;

@@ -24,11 +24,17 @@ __device__ __forceinline__ double sum_partials_cg(const double* part, int n, dou
   return block_sum(v, sbuf);
 }
 
-// Iteration i = iter[0]:  alpha = delta_{i-1} / (p.q);  u += alpha p;
-// r -= alpha q;  then the last CTA to finish reduces ||r||^2 in fixed order,
-// records the scalars, sets done / status (convergence ||r|| <= r_max,
-// breakdown, i_max), advances the counter and, inside a graph, sets the
-// condition of the enclosing WHILE node.
+__device__ __forceinline__ void segment(const PcgState& st, long n, int k, long& lo, long& hi) {
+  lo = (long)k * st.seg_len;
+  hi = (k == st.nb - 1) ? n : lo + st.seg_len;
+}
+
+// Iteration i = iter[0], problem k = blockIdx.y (skipped once done):
+// alpha_k = delta_k,i-1 / (p.q)_k;  u += alpha p;  r -= alpha q;  then the
+// last CTA reduces every problem's ||r||^2 in fixed order, records the
+// scalars, sets done / status (convergence ||r|| <= r_max, breakdown, i_max),
+// advances the counter and, inside a graph, sets the WHILE condition to
+// "some problem still iterating".  npq: partials of p.q per problem.
 __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restrict__ u, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ q,
                                                          const double* __restrict__ part_pq, int npq, PcgState st,
@@ -36,61 +42,81 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
                                                          cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sred[kRedThreads];
   __shared__ int am_last;
-  if (st.flags[0]) {  // finished before this iteration (zero or invalid start)
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+  if (*st.active == 0) {  // nothing left (zero or invalid start of every problem)
+    if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
+  const int k = blockIdx.y;
   const int it = st.iter[0];
-  const double pq = sum_partials(part_pq, npq, sred);
-  const double alpha = st.delta[it - 1] / pq;
+  const bool live = st.flags[2 * k] == 0;
   double acc = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    u[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    acc += ri * ri;
+  if (live) {
+    const double pq = sum_partials(part_pq + (long)k * npq, npq, sred);
+    const double alpha = st.delta[(long)k * st.stride + it - 1] / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st.pq[(long)k * st.stride + it] = pq;
+      st.alpha[(long)k * st.stride + it] = alpha;
+    }
+    long lo, hi;
+    segment(st, n, k, lo, hi);
+    for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
+      u[i] += alpha * p[i];
+      const double ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      acc += ri * ri;
+    }
   }
   const double s = block_sum(acc, sred);
   if (threadIdx.x == 0) {
-    part_rr[blockIdx.x] = s;
+    part_rr[(long)k * gridDim.x + blockIdx.x] = s;
     __threadfence();
     const unsigned ticket = atomicAdd(st.ticket, 1u);
-    am_last = ticket == gridDim.x - 1;
+    am_last = ticket == gridDim.x * gridDim.y - 1;
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  const double rr = sum_partials_cg(part_rr, gridDim.x, sred);
-  if (threadIdx.x == 0) {
-    st.pq[it] = pq;
-    st.alpha[it] = alpha;
-    st.rr[it] = rr;
-    int done = 0, status = 0;
-    if (bad(rr) || bad(alpha) || !(pq > 0.0)) {
-      done = 1;
-      status = 2;  // SEM_BREAKDOWN
-    } else if (sqrt(rr) <= st.rmax[0]) {
-      done = 1;
-    } else if (it >= i_max) {
-      done = 1;
-      status = 1;  // SEM_NOT_CONVERGED
+  int active = 0;
+  for (int kk = 0; kk < st.nb; ++kk) {
+    const double rr = sum_partials_cg(part_rr + (long)kk * gridDim.x, gridDim.x, sred);
+    if (threadIdx.x == 0 && st.flags[2 * kk] == 0) {
+      const long o = (long)kk * st.stride + it;
+      st.rr[o] = rr;
+      int done = 0, status = 0;
+      if (bad(rr) || bad(st.alpha[o]) || !(st.pq[o] > 0.0)) {
+        done = 1;
+        status = 2;  // SEM_BREAKDOWN
+      } else if (sqrt(rr) <= st.rmax[kk]) {
+        done = 1;
+      } else if (it >= i_max) {
+        done = 1;
+        status = 1;  // SEM_NOT_CONVERGED
+      }
+      st.flags[2 * kk] = done;
+      st.flags[2 * kk + 1] = status;
+      st.iters[kk] = it;
+      if (!done) ++active;
     }
-    st.flags[0] = done;
-    st.flags[1] = status;
+  }
+  if (threadIdx.x == 0) {
+    *st.active = active;
     st.iter[1] = it;      // index for the rest of this iteration (beta, delta)
-    st.iter[2] = it;      // iterations completed
     st.iter[0] = it + 1;  // next iteration's update
     *st.ticket = 0u;
-    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    if (use_cond) cudaGraphSetConditional(cond, active ? 1u : 0u);
   }
 }
 
-// part[2 cta] = sum z.(r - r_old), part[2 cta + 1] = sum z.r
+// per problem k: part[k G + c] = sum z.(r - r_old), part[(nb + k) G + c] = sum z.r
 __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__ z, const double* __restrict__ r,
-                                              const double* __restrict__ r_old, double* __restrict__ part) {
+                                              const double* __restrict__ r_old, double* __restrict__ part,
+                                              PcgState st) {
   __shared__ double sred[kRedThreads];
+  const int k = blockIdx.y;
+  long lo, hi;
+  segment(st, n, k, lo, hi);
   double a = 0.0, b = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+  for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
     const double zi = z[i], ri = r[i];
     a += zi * (ri - r_old[i]);
     b += zi * ri;
@@ -98,56 +124,71 @@ __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__
   const double sa = block_sum(a, sred);
   const double sb = block_sum(b, sred);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = sa;
-    part[gridDim.x + blockIdx.x] = sb;
+    part[(long)k * gridDim.x + blockIdx.x] = sa;
+    part[(long)(st.nb + k) * gridDim.x + blockIdx.x] = sb;
   }
 }
 
-// i = iter[1]:  beta = z.(r - r_old) / delta_{i-1};  delta_i = z.r;
-// p = z + beta p;  r_old = r
+// i = iter[1], problem k (live only): beta = z.(r - r_old) / delta_{i-1};
+// delta_i = z.r;  p = z + beta p;  r_old = r
 __global__ void __launch_bounds__(256) k_update_p(long n, const double* __restrict__ z, double* __restrict__ p,
                                                   const double* __restrict__ r, double* __restrict__ r_old,
                                                   const double* __restrict__ part, int np, PcgState st) {
   __shared__ double sred[kRedThreads];
+  const int k = blockIdx.y;
+  if (st.flags[2 * k]) return;
   const int it = st.iter[1];
-  const double zd = sum_partials(part, np, sred);
-  const double zr = sum_partials(part + np, np, sred);
-  const double beta = zd / st.delta[it - 1];
+  const double zd = sum_partials(part + (long)k * np, np, sred);
+  const double zr = sum_partials(part + (long)(st.nb + k) * np, np, sred);
+  const double beta = zd / st.delta[(long)k * st.stride + it - 1];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st.beta[it] = beta;
-    st.delta[it] = zr;
+    st.beta[(long)k * st.stride + it] = beta;
+    st.delta[(long)k * st.stride + it] = zr;
   }
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+  long lo, hi;
+  segment(st, n, k, lo, hi);
+  for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
     p[i] = z[i] + beta * p[i];
     r_old[i] = r[i];
   }
 }
 
-// start of Alg. 4: p = z (= MG(0, r_0)), delta_0 = p.r, r_old = 0, rr_0, r_max
+// start of Alg. 4 per problem: p = z (= MG(0, r_0)), delta_0 = p.r, r_old = 0,
+// rr_0 (nrr residual partials per problem), r_max
 __global__ void __launch_bounds__(256) k_start(long n, const double* __restrict__ z, const double* __restrict__ r,
                                                double* __restrict__ p, double* __restrict__ r_old,
                                                const double* __restrict__ part_zr, int nzr,
                                                const double* __restrict__ part_rr, int nrr, PcgState st,
                                                double tol) {
   __shared__ double sred[kRedThreads];
-  const double zr = sum_partials(part_zr + nzr, nzr, sred);
-  const double rr = sum_partials(part_rr, nrr, sred);
+  const int k = blockIdx.y;
+  const double zr = sum_partials(part_zr + (long)(st.nb + k) * nzr, nzr, sred);
+  const double rr = sum_partials(part_rr + (long)k * nrr, nrr, sred);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st.delta[0] = zr;
-    st.rr[0] = rr;
-    st.rmax[0] = tol * sqrt(rr);
+    st.delta[(long)k * st.stride] = zr;
+    st.rr[(long)k * st.stride] = rr;
+    st.rmax[k] = tol * sqrt(rr);
     const bool broken = bad(rr) || bad(zr);
-    st.flags[0] = (broken || rr == 0.0) ? 1 : 0;
-    st.flags[1] = broken ? 2 : 0;
-    st.iter[0] = 1;
-    st.iter[1] = 0;
-    st.iter[2] = 0;
-    *st.ticket = 0u;
+    const int done = (broken || rr == 0.0) ? 1 : 0;
+    st.flags[2 * k] = done;
+    st.flags[2 * k + 1] = broken ? 2 : 0;
+    st.iters[k] = 0;
+    atomicAdd(st.active, done ? 0 : 1);
   }
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+  long lo, hi;
+  segment(st, n, k, lo, hi);
+  for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
     p[i] = z[i];
     r_old[i] = 0.0;
   }
+}
+
+// reset the lockstep counters before k_start
+__global__ void k_reset(PcgState st) {
+  st.iter[0] = 1;
+  st.iter[1] = 0;
+  *st.ticket = 0u;
+  *st.active = 0;
 }
 
 template <typename TA, typename TB>
@@ -178,34 +219,83 @@ __global__ void __launch_bounds__(256) k_norm2(long n, const double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// problem k of nmem: (rows + 1) x Nx nodes, walls (first / last row and
+// column) written as 0
+__global__ void __launch_bounds__(256) k_stack_in(const double* const* __restrict__ srcs, const double* one,
+                                                  double* __restrict__ stack, int rows, int Nx, long seg_len) {
+  const int k = blockIdx.y;
+  const double* src = srcs ? srcs[k] : one;
+  const long per = (long)(rows + 1) * Nx;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < per; i += (long)gridDim.x * blockDim.x) {
+    const int row = (int)(i / Nx), col = (int)(i - (long)row * Nx);
+    const bool wall = row == 0 || row == rows || col == 0 || col == Nx - 1;
+    stack[(long)k * seg_len + i] = wall ? 0.0 : src[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stack_out(const double* __restrict__ stack, double* const* __restrict__ dsts,
+                                                   double* one, int rows, int Nx, long seg_len) {
+  const int k = blockIdx.y;
+  double* dst = dsts ? dsts[k] : one;
+  const long per = (long)(rows + 1) * Nx;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < per; i += (long)gridDim.x * blockDim.x)
+    dst[i] = stack[(long)k * seg_len + i];
+}
+
 }  // namespace
 
+cudaError_t launch_stack_in(const double* const* srcs, const double* one, double* stack, int nmem, int rows, int Nx,
+                            long seg_len, cudaStream_t s) {
+  const long per = (long)(rows + 1) * Nx;
+  dim3 grid((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, 1024)), nmem);
+  k_stack_in<<<grid, 256, 0, s>>>(srcs, one, stack, rows, Nx, seg_len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stack_out(const double* stack, double* const* dsts, double* one, int nmem, int rows, int Nx,
+                             long seg_len, cudaStream_t s) {
+  const long per = (long)(rows + 1) * Nx;
+  dim3 grid((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, 1024)), nmem);
+  k_stack_out<<<grid, 256, 0, s>>>(stack, dsts, one, rows, Nx, seg_len);
+  return cudaGetLastError();
+}
+
 int elementwise_grid(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, kElemGrid)); }
+
+int chunk_grid(const PcgState& st) {
+  const long per = st.seg_len;
+  const int g = (int)std::max<long>(1, std::min<long>((per + 255) / 256, std::max(4, kElemGrid / st.nb)));
+  return std::min(g, kMaxPartials / std::max(1, 2 * st.nb));
+}
 
 cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
                                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
-  k_update_ur_check<<<elementwise_grid(n), 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond,
-                                                        use_cond);
+  dim3 grid(chunk_grid(st), st.nb);
+  k_update_ur_check<<<grid, 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old, double* part,
+cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old, double* part, PcgState st,
                         cudaStream_t s) {
-  k_dot2<<<elementwise_grid(n), 256, 0, s>>>(n, z, r, r_old, part);
+  dim3 grid(chunk_grid(st), st.nb);
+  k_dot2<<<grid, 256, 0, s>>>(n, z, r, r_old, part, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
-                                const double* part, int np, PcgState st, cudaStream_t s) {
-  k_update_p<<<elementwise_grid(n), 256, 0, s>>>(n, z, p, r, r_old, part, np, st);
+                                const double* part, PcgState st, cudaStream_t s) {
+  dim3 grid(chunk_grid(st), st.nb);
+  k_update_p<<<grid, 256, 0, s>>>(n, z, p, r, r_old, part, grid.x, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_start(long n, const double* z, const double* r, double* p, double* r_old,
-                             const double* part_zr, int nzr, const double* part_rr, int nrr, PcgState st,
-                             double tol, cudaStream_t s) {
-  k_start<<<elementwise_grid(n), 256, 0, s>>>(n, z, r, p, r_old, part_zr, nzr, part_rr, nrr, st, tol);
+                             const double* part_zr, const double* part_rr, int nrr, PcgState st, double tol,
+                             cudaStream_t s) {
+  k_reset<<<1, 1, 0, s>>>(st);
+  dim3 grid(chunk_grid(st), st.nb);
+  k_start<<<grid, 256, 0, s>>>(n, z, r, p, r_old, part_zr, grid.x, part_rr, nrr, st, tol);
   return cudaGetLastError();
 }
 

@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
 
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic);
-    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic);
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
     su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
   }
   // element stiffness of the tile and of its low-side neighbour (slot 0)
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
-    const bool wall = (!dx.periodic && (gi == 0 || gi == Nx - 1)) || (!dy.periodic && (gj == 0 || gj == Ny - 1));
+    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
     T val = T(0);
     if (!wall) {
       const int lex = ix / P, a = ix - lex * P;
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic);
-    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic);
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
     su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
   }
   // E/O tables of slot s = element ex0 + s - 1 (slot 0: low-side neighbour)
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
-    const bool wall = (!dx.periodic && (gi == 0 || gi == Nx - 1)) || (!dy.periodic && (gj == 0 || gj == Ny - 1));
+    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
     T val = T(0);
     if (!wall) {
       const int lex = ix / P, a = ix - lex * P;
@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(256) k_var_local(DirView<T> dx, DirView<T> dy,
   const long e = (long)ey * dx.n + ex;
   for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
     const int j = idx / NP, i = idx - j * NP;
-    const int gx = node_or_wall(ex * P + i, dx.N, dx.periodic);
-    const int gy = node_or_wall(ey * P + j, dy.N, dy.periodic);
+    const int gx = node_or_wall(ex * P + i, dx.N, dx.periodic, dx.segN);
+    const int gy = node_or_wall(ey * P + j, dy.N, dy.periodic, dy.segN);
     sU[idx] = (gx >= 0 && gy >= 0) ? u[(long)gy * dx.N + gx] : T(0);
     sD[idx] = v.D[idx];
   }
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) k_var_gather(DirView<T> dx, DirView<T> dy
   double acc = 0.0;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
     const int gj = (int)(idx / dx.N), gi = (int)(idx - (long)gj * dx.N);
-    const bool wall = (!dx.periodic && (gi == 0 || gi == dx.N - 1)) || (!dy.periodic && (gj == 0 || gj == dy.N - 1));
+    const bool wall = wall_node(gi, dx.N, dx.periodic, dx.segN) || wall_node(gj, dy.N, dy.periodic, dy.segN);
     T val = T(0);
     if (!wall) {
       T s = T(0);
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double
   double acc = 0.0;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
     const int gj = (int)(idx / dx.N), gi = (int)(idx - (long)gj * dx.N);
-    const bool wall = (!dx.periodic && (gi == 0 || gi == dx.N - 1)) || (!dy.periodic && (gj == 0 || gj == dy.N - 1));
+    const bool wall = wall_node(gi, dx.N, dx.periodic, dx.segN) || wall_node(gj, dy.N, dy.periodic, dy.segN);
     const double v = wall ? 0.0 : dy.Mg[gj] * dx.Mg[gi] * f[idx];
     b[idx] = v;
     acc += v;

@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(256) k_sweep_simt(DirView<T> dx, DirView<T> dy
     Sx[idx] = dx.S[(long)tx * mm + idx];
     Sy[idx] = dy.S[(long)ty * mm + idx];
     const int a = idx / m, b = idx - a * m;  // a: y slot, b: x slot
-    const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic);
-    const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic);
+    const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
+    const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
     X[idx] = (gx >= 0 && gy >= 0) ? T(r[(long)gy * dx.N + gx]) : T(0);
   }
   for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(32 * kMmaWarps) k_sweep_mma(DirView<float> dx,
       const bool in = a < m && b < m;
       float xv = 0.f;
       if (in) {
-        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic);
-        const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic);
+        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
+        const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
         if (gx >= 0 && gy >= 0) xv = (float)r[(long)gy * dx.N + gx];
       }
       X[a * SA + b] = xv;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) k_scatter(DirView<T> dx, DirView<T> dy, c
   const long n = (long)dx.N * dy.N;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
     const int gj = (int)(idx / dx.N), gi = (int)(idx - (long)gj * dx.N);
-    const bool wall = (!dx.periodic && (gi == 0 || gi == dx.N - 1)) || (!dy.periodic && (gj == 0 || gj == dy.N - 1));
+    const bool wall = wall_node(gi, dx.N, dx.periodic, dx.segN) || wall_node(gj, dy.N, dy.periodic, dy.segN);
     if (wall) {
       if (!accum) u[idx] = TOut(0);
       continue;

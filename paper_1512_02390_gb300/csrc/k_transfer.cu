@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, 
   const int gx0 = E0x * PF - PF, gy0 = E0y * PF - PF;
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, fx.N, fx.periodic);
-    const int gy = node_or_wall(gy0 + ly, fy.N, fy.periodic);
+    const int gx = node_or_wall(gx0 + lx, fx.N, fx.periodic, fx.segN);
+    const int gy = node_or_wall(gy0 + ly, fy.N, fy.periodic, fy.segN);
     sr[ly * LP + lx] = (gx >= 0 && gy >= 0) ? rf[(long)gy * fx.N + gx] : T(0);
   }
   for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, 
   for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
     const int jc = idx / ownx, ic = idx - jc * ownx;
     const int gI = E0x * PC + ic, gJ = E0y * PC + jc;
-    const bool wall = (!cx.periodic && (gI == 0 || gI == cx.N - 1)) || (!cy.periodic && (gJ == 0 || gJ == cy.N - 1));
+    const bool wall = wall_node(gI, cx.N, cx.periodic, cx.segN) || wall_node(gJ, cy.N, cy.periodic, cy.segN);
     T v = T(0);
     if (!wall) {
       const int le = jc / PC, K = jc - le * PC;
@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, D
   const int E0x = blockIdx.x * TE, E0y = blockIdx.y * TE;
   for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
     const int ly = idx / LC, lx = idx - ly * LC;
-    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic);
-    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic);
+    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
+    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic, cy.segN);
     sc[ly * LCP + lx] = (gx >= 0 && gy >= 0) ? uc[(long)gy * cx.N + gx] : T(0);
   }
   for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, D
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = E0x * PF + ix, gj = E0y * PF + jy;
     const long o = (long)gj * fx.N + gi;
-    const bool wall = (!fx.periodic && (gi == 0 || gi == fx.N - 1)) || (!fy.periodic && (gj == 0 || gj == fy.N - 1));
+    const bool wall = wall_node(gi, fx.N, fx.periodic, fx.segN) || wall_node(gj, fy.N, fy.periodic, fy.segN);
     if (wall) {
       out[o] = TOut(0);
       continue;
@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
   __shared__ double part[TK][TM][TM + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nux = c.nux, nuy = c.nuy;
+  // stacked problems: block z has its own right side rows and scratch
+  const int fy0 = c.firsty + blockIdx.z * c.block_rows;
+  c.T1 += (long)blockIdx.z * nux * nuy;
+  c.T2 += (long)blockIdx.z * nux * nuy;
   // steps 1 and 3 contract over y (nuy), steps 2 and 4 over x (nux)
   const int K = (step == kStep1 || step == kStep3) ? nuy : nux;
   double* sA = reinterpret_cast<double*>(smem_raw);  // TM x K
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
     if (step == kStep1) {
       for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
         const int j = idx / nux, i = idx - j * nux;
-        acc += (double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i];
+        acc += (double)f0[(long)(fy0 + j) * c.Nx + c.firstx + i];
       }
     } else {  // mean(U) = c_y^T T2 c_x / N (T2 is intact: step 3 wrote T1)
       for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
       k = idx / TM;
       q = idx - k * TM;
       if (c0 + q < cols) {
-        if (step == kStep1) b = (double)f0[(long)(c.firsty + k) * c.Nx + c.firstx + c0 + q] - shift;
+        if (step == kStep1) b = (double)f0[(long)(fy0 + k) * c.Nx + c.firstx + c0 + q] - shift;
         else if (step == kStep2) b = c.Sx[k * nux + c0 + q];
         else b = c.T2[(long)k * nux + c0 + q];
       }
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
       case kStep1: c.T1[o] = v; break;
       case kStep2: c.T2[o] = (c.periodic && row == 0 && col == 0) ? 0.0 : v / (c.ly[row] + c.lx[col]); break;
       case kStep3: c.T1[o] = v; break;  // S_y T2 reuses the T1 buffer
-      default: u0[(long)(c.firsty + row) * c.Nx + c.firstx + col] = T(v - shift);
+      default: u0[(long)(fy0 + row) * c.Nx + c.firstx + col] = T(v - shift);
     }
   }
 }
@@ -249,19 +253,20 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_dense(CoarseView c, const double* __restrict__ Binv,
                                                       const T* __restrict__ f0, T* __restrict__ u0) {
   const int n = c.nux * c.nuy;
+  const int fy0 = c.firsty + blockIdx.y * c.block_rows;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const double* row = Binv + (long)warp * n;
   double s = 0.0;
   for (int k = lane; k < n; k += 32) {
     const int j = k / c.nux, i = k - j * c.nux;
-    s += row[k] * (double)f0[(long)(c.firsty + j) * c.Nx + c.firstx + i];
+    s += row[k] * (double)f0[(long)(fy0 + j) * c.Nx + c.firstx + i];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
     const int j = warp / c.nux, i = warp - j * c.nux;
-    u0[(long)(c.firsty + j) * c.Nx + c.firstx + i] = T(s);
+    u0[(long)(fy0 + j) * c.Nx + c.firstx + i] = T(s);
   }
 }
 
@@ -321,7 +326,7 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s) {
-  dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8);
+  dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8, std::max(1, c.batch));
   const size_t sm = 2 * 8 * sizeof(double) * (size_t)std::max(c.nux, c.nuy);
   cudaError_t e0 = allow_smem(k_coarse_gemm<T>, sm);
   if (e0 != cudaSuccess) return e0;
@@ -336,7 +341,7 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
 template <typename T>
 cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s) {
   const int n = c.nux * c.nuy;
-  k_coarse_dense<T><<<(n + 7) / 8, 256, 0, s>>>(c, Binv, f0, u0);
+  k_coarse_dense<T><<<dim3((n + 7) / 8, std::max(1, c.batch)), 256, 0, s>>>(c, Binv, f0, u0);
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_dense<double>(const CoarseView&, const double*, const double*, double*, cudaStream_t);

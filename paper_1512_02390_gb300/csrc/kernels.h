@@ -9,7 +9,7 @@
 namespace sem {
 
 // Number of partial sums a reduction-producing launch writes (one per CTA).
-constexpr int kMaxPartials = 8192;
+constexpr int kMaxPartials = 1 << 17;
 
 // ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
 // out = A u (f == nullptr) or out = f - A u.  dot: 0 none, 1 part[cta] = sum
@@ -64,9 +64,11 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 // ---- coarse solve u0 = A_0^+ f0 by global fast diagonalisation ------------
 struct CoarseView {
   int nux, nuy, firstx, firsty, Nx, Ny, periodic;
+  int batch;       // stacked independent problems (coarse blocks)
+  int block_rows;  // node rows between consecutive blocks
   const double *Sx, *Sy, *lx, *ly, *cx, *cy;
-  double* T1;  // nuy x nux scratch (also holds S_y T2)
-  double* T2;  // nuy x nux scratch
+  double* T1;  // batch x nuy x nux scratch (also holds S_y T2)
+  double* T2;  // batch x nuy x nux scratch
 };
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s);
@@ -75,32 +77,50 @@ template <typename T>
 cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s);
 
 // ---- Krylov vector kernels (Alg. 4), k_krylov.cu -------------------------
+// MGCG state of nb independent problems stacked in one node grid (nb = 1 for a
+// single solve).  Problem k owns nodes [k seg_len, (k+1) seg_len) (the last
+// one runs to the end); its scalars live at k * stride + i.
 struct PcgState {
-  double* alpha;   // [i_max + 2] per-iteration scalars
+  int nb;            // problems
+  int stride;        // i_max + 2: length of each problem's scalar history
+  long seg_len;      // nodes per problem segment
+  double* alpha;     // [nb][stride] per-iteration scalars
   double* beta;
   double* delta;
   double* pq;
   double* rr;
-  int* flags;      // [0] done, [1] status
-  double* rmax;    // threshold on ||r||
-  int* iter;       // [0] index of the next update, [1] index of the current beta, [2] iterations done
-  unsigned* ticket;  // CTA completion counter of the fused update/check
+  double* rmax;      // [nb] threshold on ||r||
+  int* flags;        // [nb][2]: done, status
+  int* iters;        // [nb] iterations completed
+  int* iter;         // [2]: index of the next update, index of the current beta (lockstep)
+  unsigned* ticket;  // CTA completion counter of the fused update / check
+  int* active;       // problems still iterating
 };
 int elementwise_grid(long n);
+// CTAs per problem of the batched vector kernels (grid = (chunks, nb))
+int chunk_grid(const PcgState& st);
 cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
                                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
 cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old,
-                        double* part, cudaStream_t s);
+                        double* part, PcgState st, cudaStream_t s);
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
-                                const double* part, int np, PcgState st, cudaStream_t s);
+                                const double* part, PcgState st, cudaStream_t s);
+// nrr: residual partials per problem (from the operator launch)
 cudaError_t launch_pcg_start(long n, const double* z, const double* r, double* p, double* r_old,
-                             const double* part_zr, int nzr, const double* part_rr, int nrr,
-                             PcgState st, double tol, cudaStream_t s);
+                             const double* part_zr, const double* part_rr, int nrr, PcgState st, double tol,
+                             cudaStream_t s);
 template <typename TA, typename TB>
 cudaError_t launch_convert(long n, const TA* a, TB* b, cudaStream_t s);
 cudaError_t launch_axpy(long n, double alpha, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_sub_mean(long n, double* b, const double* part, int np, cudaStream_t s);
 cudaError_t launch_norm2(long n, const double* x, double* part, cudaStream_t s);
+// Copy nmem problem grids of (rows + 1) x Nx nodes into / out of a stack in
+// which problem k starts at node k * seg_len; wall nodes of the stack are 0.
+// srcs / dsts: DEVICE arrays of nmem pointers, or null to use `one`.
+cudaError_t launch_stack_in(const double* const* srcs, const double* one, double* stack, int nmem, int rows, int Nx,
+                            long seg_len, cudaStream_t s);
+cudaError_t launch_stack_out(const double* stack, double* const* dsts, double* one, int nmem, int rows, int Nx,
+                             long seg_len, cudaStream_t s);
 
 }  // namespace sem

@@ -72,6 +72,8 @@ struct sem_handle {
   CoarseView coarse{};
   std::vector<int> ns1, ns2;
   long n = 0, n_unknowns = 0;
+  int nb = 1;        // independent problems stacked along y (batched solves)
+  int rows_top = 0;  // node rows of one problem on the finest level
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *r_old = nullptr;
   double* fi = nullptr;  // right side of the running MGCG solve (internal copy)
   double* Binv = nullptr;  // dense FP64 inverse of B_0(nu) (variable diffusivity)
@@ -83,7 +85,7 @@ struct sem_handle {
   int solves = 0;
   double* part = nullptr;
   PcgState st{};
-  int* flags_host = nullptr;
+  int* flags_host = nullptr;  // pinned: [0] problems still iterating
   std::vector<double> xc, yc;
   std::vector<void*> allocs;
   // tracing: launches per kernel class, optional CUDA-event timing
@@ -356,93 +358,100 @@ int pcg_tail(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int
   int np = 0, rc;
   if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s))) return rc;
   KL(h, SEM_K_VECTOR, s,
-     launch_pcg_update_ur_check(h->n, h->u, h->r, h->p, h->q, h->part, np, h->st, h->part + kMaxPartials,
+     launch_pcg_update_ur_check(h->n, h->u, h->r, h->p, h->q, h->part, np / h->nb, h->st, h->part + kMaxPartials,
                                 h->cfg.i_max, cond, use_cond, s));
   return SEM_OK;
 }
 
 int pcg_prologue(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const long n = h->n;
-  const int G = elementwise_grid(n);
   int np = 0, rc;
   // r = f - A u and ||r_0||^2 partials
   if ((rc = apply64(h, h->u, h->fi, h->r, 2, &np, s, h->part + 2 * kMaxPartials))) return rc;
   // p = MultigridCycle(0, r); delta = p.r; r_old = 0
   if ((rc = precond(h, h->r, h->z, s))) return rc;
-  KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r, h->part, s));
-  KL(h, SEM_K_VECTOR, s,
-     launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, G, h->part + 2 * kMaxPartials, np, h->st,
-                      h->cfg.tol, s));
+  KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r, h->part, h->st, s));
+  KLN(h, SEM_K_VECTOR, 2, s,
+      launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, h->part + 2 * kMaxPartials, np / h->nb, h->st,
+                       h->cfg.tol, s));
   return pcg_tail(h, s, cond, use_cond);
 }
 
 int pcg_body(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const long n = h->n;
-  const int G = elementwise_grid(n);
   int rc;
   if ((rc = precond(h, h->r, h->z, s))) return rc;
-  KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r_old, h->part, s));
-  KL(h, SEM_K_VECTOR, s, launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, G, h->st, s));
+  KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r_old, h->part, h->st, s));
+  KL(h, SEM_K_VECTOR, s, launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, h->st, s));
   return pcg_tail(h, s, cond, use_cond);
 }
 
-// Capture prologue + WHILE(body) once; the body's last kernel sets the condition.
-int build_graph(sem_handle* h) {
-  CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+// Add prologue + WHILE(body) of h's MGCG to the capture running on `cap`
+// (body captured through `cap2`); the body's last kernel sets the condition.
+// Launch counts of the captured prologue / body are kept for the tracing
+// counters of graph replays.
+int capture_solve(sem_handle* h, cudaStream_t cap, cudaStream_t cap2) {
   long long before[SEM_K_NCLASS];
   for (int c = 0; c < SEM_K_NCLASS; ++c) before[c] = h->launches[c];
-  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
   cudaStreamCaptureStatus cs;
   cudaGraph_t capg = nullptr;
-  auto abort_capture = [&](int code) {
-    cudaGraph_t junk = nullptr;
-    cudaStreamEndCapture(h->cap, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    cudaGetLastError();
-    return code;
-  };
-  if (cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, &capg, nullptr, nullptr, nullptr) != cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "cudaStreamGetCaptureInfo failed"));
+  CK(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &capg, nullptr, nullptr, nullptr));
   cudaGraphConditionalHandle cond;
-  if (cudaGraphConditionalHandleCreate(&cond, capg, 0, 0) != cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "cudaGraphConditionalHandleCreate failed"));
-  int rc = pcg_prologue(h, h->cap, cond, 1);
-  if (rc) return abort_capture(rc);
+  CK(cudaGraphConditionalHandleCreate(&cond, capg, 0, 0));
+  int rc = pcg_prologue(h, cap, cond, 1);
+  if (rc) return rc;
   for (int c = 0; c < SEM_K_NCLASS; ++c) h->graph_pro[c] = h->launches[c] - before[c];
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  if (cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, &capg, &deps, nullptr, &nd) != cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "cudaStreamGetCaptureInfo failed"));
+  CK(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &capg, &deps, nullptr, &nd));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = cond;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
-  if (cudaGraphAddNode(&cnode, capg, deps, nullptr, nd, &cp) != cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "adding the WHILE node failed"));
-  if (cudaStreamUpdateCaptureDependencies(h->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
-      cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "cudaStreamUpdateCaptureDependencies failed"));
+  CK(cudaGraphAddNode(&cnode, capg, deps, nullptr, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   for (int c = 0; c < SEM_K_NCLASS; ++c) before[c] = h->launches[c];
-  if (cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
-    return abort_capture(fail(SEM_CUDA_ERROR, "cudaStreamBeginCaptureToGraph failed"));
-  rc = pcg_body(h, h->cap2, cond, 1);
+  CK(cudaStreamBeginCaptureToGraph(cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  rc = pcg_body(h, cap2, cond, 1);
   cudaGraph_t body_out = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(h->cap2, &body_out);
-  if (rc) return abort_capture(rc);
-  if (e2 != cudaSuccess) return abort_capture(fail(SEM_CUDA_ERROR, "body capture failed"));
-  for (int c = 0; c < SEM_K_NCLASS; ++c) h->graph_body[c] = h->launches[c] - before[c];
-  CK(cudaStreamEndCapture(h->cap, &h->graph));
-  CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
-  for (int c = 0; c < SEM_K_NCLASS; ++c) h->launches[c] -= h->graph_pro[c] + h->graph_body[c];
+  cudaError_t e2 = cudaStreamEndCapture(cap2, &body_out);
+  if (rc) return rc;
+  if (e2 != cudaSuccess) return fail(SEM_CUDA_ERROR, "body capture failed");
+  for (int c = 0; c < SEM_K_NCLASS; ++c) {
+    h->graph_body[c] = h->launches[c] - before[c];
+    h->launches[c] -= h->graph_pro[c] + h->graph_body[c];
+  }
   return SEM_OK;
 }
 
+int end_capture_discard(cudaStream_t cap) {
+  cudaGraph_t junk = nullptr;
+  cudaStreamEndCapture(cap, &junk);
+  if (junk) cudaGraphDestroy(junk);
+  cudaGetLastError();
+  return 0;
+}
+
+int build_graph(sem_handle* h) {
+  CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
+  int rc = capture_solve(h, h->cap, h->cap2);
+  if (rc) {
+    end_capture_discard(h->cap);
+    return rc;
+  }
+  CK(cudaStreamEndCapture(h->cap, &h->graph));
+  CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+  return SEM_OK;
+}
+
+// host copy of the number of problems still iterating
 int sync_flags(sem_handle* h, cudaStream_t s) {
-  CK(cudaMemcpyAsync(h->flags_host, h->st.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->flags_host, h->st.active, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return SEM_OK;
 }
@@ -646,24 +655,31 @@ int sem_learned_features(const sem_config* cfg, float* feat_x, float* feat_y) {
   return SEM_OK;
 }
 
-int sem_create(const sem_config* cfg, sem_handle** out) {
-  g_err.clear();
-  if (!cfg || !out) return fail(SEM_BAD_ARG, "null argument");
-  const sem_config& c = *cfg;
+// A handle for nb copies of the problem cfg stacked along y (nb = 1: one
+// problem).  Stacked copies share every table; walls separate them.
+static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   int L = 0;
   {
     int rc0 = validate(c, L);
     if (rc0) return rc0;
   }
+  if (nb < 1) return fail(SEM_BAD_ARG, "nb must be positive");
+  if (nb > 1 && (c.periodic || c.y_edges || c.nu_kind || c.weight == SEM_W_LEARNED))
+    return fail(SEM_BAD_ARG, "stacked problems must be uniform Dirichlet Poisson problems");
+  if ((long)nb * c.ny > 65536) return fail(SEM_BAD_ARG, "too many stacked problems");
   auto mesh = make_mesh;
   sem_handle* h = new sem_handle();
   h->cfg = c;
   h->cfg.x_edges = h->cfg.y_edges = nullptr;
   h->cfg.learned_x = h->cfg.learned_y = nullptr;
-  if (!mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, h->mx) || !mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, h->my)) {
+  h->nb = nb;
+  Mesh1D my1;  // one problem's y mesh (coarse factors)
+  if (!mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, h->mx) || !mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, my1) ||
+      !mesh(c.ny * nb, c.ly * nb, nb > 1 ? nullptr : c.y_edges, c.periodic != 0, h->my)) {
     delete h;
     return fail(SEM_BAD_ARG, "mesh edges must increase");
   }
+  if (nb > 1) h->my.seg = c.ny;
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -706,6 +722,7 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     if ((rc = upload_dir(h, dx, lv.x64)) || (rc = upload_dir(h, dy, lv.y64)) || (rc = upload_dir(h, dx, lv.x32)) ||
         (rc = upload_dir(h, dy, lv.y32)))
       return bail(rc);
+    if (nb > 1) lv.y64.segN = lv.y32.segN = c.ny * lv.p;
     if (l > 0) {
       std::vector<double> J;
       interp_matrix(lv.p, lv.p / 2, J);
@@ -725,7 +742,7 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     if (l > 0) {
       if ((rc = dev_alloc(h, &b, lv.nodes * tsz))) return bail(rc);
       lv.r = b;
-      if ((rc = dev_alloc(h, &b, (size_t)c.nx * c.ny * lv.m * lv.m * tsz))) return bail(rc);
+      if ((rc = dev_alloc(h, &b, (size_t)c.nx * c.ny * nb * lv.m * lv.m * tsz))) return bail(rc);
       lv.E = b;
       if (c.nu_kind) {
         VarData vd;
@@ -756,7 +773,7 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
   {
     Coarse1D cx, cy;
     std::string err = build_coarse(h->mx, cx);
-    if (err.empty()) err = build_coarse(h->my, cy);
+    if (err.empty()) err = build_coarse(my1, cy);
     if (!err.empty()) {
       sem_destroy(h);
       return fail(SEM_BAD_ARG, err);
@@ -769,10 +786,12 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
     cv.Nx = h->lev[0].Nx;
     cv.Ny = h->lev[0].Ny;
     cv.periodic = c.periodic ? 1 : 0;
+    cv.batch = nb;
+    cv.block_rows = c.ny;  // coarse (p = 1) node rows per stacked problem
     double *Sx, *Sy, *lx, *ly, *ccx, *ccy, *T1, *T2;
     if ((rc = upload(h, &Sx, cx.S)) || (rc = upload(h, &Sy, cy.S)) || (rc = upload(h, &lx, cx.lam)) ||
         (rc = upload(h, &ly, cy.lam)) || (rc = upload(h, &ccx, cx.c)) || (rc = upload(h, &ccy, cy.c)) ||
-        (rc = dev_alloc(h, &T1, (size_t)cx.nu * cy.nu)) || (rc = dev_alloc(h, &T2, (size_t)cx.nu * cy.nu)))
+        (rc = dev_alloc(h, &T1, (size_t)cx.nu * cy.nu * nb)) || (rc = dev_alloc(h, &T2, (size_t)cx.nu * cy.nu * nb)))
       return bail(rc);
     cv.T1 = T1;
     cv.Sx = Sx;
@@ -794,8 +813,9 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
   }
   // MGCG vectors, partial sums, per-iteration scalars
   h->n = top(h).nodes;
-  h->n_unknowns = (long)(c.periodic ? h->mx.n * c.p : h->mx.n * c.p - 1) *
-                  (long)(c.periodic ? h->my.n * c.p : h->my.n * c.p - 1);
+  h->rows_top = c.ny * c.p;
+  h->n_unknowns = (long)nb * (long)(c.periodic ? c.nx * c.p : c.nx * c.p - 1) *
+                  (long)(c.periodic ? c.ny * c.p : c.ny * c.p - 1);
   double** vecs[] = {&h->u, &h->r, &h->p, &h->q, &h->z, &h->r_old, &h->fi};
   for (double** v : vecs) {
     if ((rc = dev_alloc(h, v, h->n))) return bail(rc);
@@ -803,21 +823,28 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
   }
   if ((rc = dev_alloc(h, &h->part, 4 * kMaxPartials))) return bail(rc);
   const int ni = c.i_max + 2;
+  const size_t nsc = (size_t)5 * ni * nb + nb;
   double* sc;
-  if ((rc = dev_alloc(h, &sc, 5 * ni + 1))) return bail(rc);
-  CK(cudaMemset(sc, 0, (5 * ni + 1) * sizeof(double)));
+  if ((rc = dev_alloc(h, &sc, nsc))) return bail(rc);
+  CK(cudaMemset(sc, 0, nsc * sizeof(double)));
+  h->st.nb = nb;
+  h->st.stride = ni;
+  h->st.seg_len = nb > 1 ? (long)h->rows_top * top(h).Nx : h->n;
   h->st.alpha = sc;
-  h->st.beta = sc + ni;
-  h->st.delta = sc + 2 * ni;
-  h->st.pq = sc + 3 * ni;
-  h->st.rr = sc + 4 * ni;
-  h->st.rmax = sc + 5 * ni;
+  h->st.beta = sc + (size_t)ni * nb;
+  h->st.delta = sc + (size_t)2 * ni * nb;
+  h->st.pq = sc + (size_t)3 * ni * nb;
+  h->st.rr = sc + (size_t)4 * ni * nb;
+  h->st.rmax = sc + (size_t)5 * ni * nb;
   int* fl;
-  if ((rc = dev_alloc(h, &fl, 8))) return bail(rc);
-  CK(cudaMemset(fl, 0, 8 * sizeof(int)));
-  h->st.flags = fl;
-  h->st.iter = fl + 2;
-  h->st.ticket = reinterpret_cast<unsigned*>(fl + 5);
+  const size_t nfl = (size_t)3 * nb + 4;
+  if ((rc = dev_alloc(h, &fl, nfl))) return bail(rc);
+  CK(cudaMemset(fl, 0, nfl * sizeof(int)));
+  h->st.flags = fl;                 // [nb][2]
+  h->st.iters = fl + 2 * nb;        // [nb]
+  h->st.iter = fl + 3 * nb;         // [2]
+  h->st.ticket = reinterpret_cast<unsigned*>(fl + 3 * nb + 2);
+  h->st.active = fl + 3 * nb + 3;
   if (cudaMallocHost(&h->flags_host, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     h->flags_host = nullptr;
@@ -827,6 +854,12 @@ int sem_create(const sem_config* cfg, sem_handle** out) {
   CK(cudaDeviceSynchronize());
   *out = h;
   return SEM_OK;
+}
+
+int sem_create(const sem_config* cfg, sem_handle** out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(SEM_BAD_ARG, "null argument");
+  return create_handle(*cfg, 1, out);
 }
 
 int sem_sizes(const sem_handle* h, int64_t* n_unknowns, int64_t* nx_nodes, int64_t* ny_nodes) {
@@ -930,19 +963,11 @@ int sem_mg_solve(sem_handle* h, double* u, const double* f, sem_result* res, dou
   return status;
 }
 
-int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, double* history, int32_t hlen,
-                  void* stream) {
-  int rc = check_handle(h);
-  if (rc) return rc;
-  if (!u || !f || !res) return fail(SEM_BAD_ARG, "null argument");
-  cudaStream_t s = as_stream(stream);
-  const long n = h->n;
-  CK(cudaMemcpyAsync(h->fi, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->u, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  // the first solve of a handle runs launch by launch (modules load, shared-
-  // memory limits are set); later solves replay one CUDA graph whose WHILE
-  // node runs the iterations without returning to the host.  With profiling
-  // on, the launch-by-launch path is used so every kernel can be timed.
+// run the MGCG of all problems of h on the vectors already in h->u / h->fi:
+// launch by launch on the first solve (and with profiling on), afterwards by
+// replaying the captured graph
+static int run_solve(sem_handle* h, cudaStream_t s) {
+  int rc;
   const bool use_graph = !h->prof && h->solves > 0;
   if (use_graph && !h->graph_exec) {
     CK(cudaStreamSynchronize(s));
@@ -954,30 +979,63 @@ int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, do
     if ((rc = pcg_prologue(h, s, 0, 0))) return rc;
     for (;;) {
       if ((rc = sync_flags(h, s))) return rc;
-      if (h->flags_host[0]) break;
+      if (h->flags_host[0] == 0) break;
       if ((rc = pcg_body(h, s, 0, 0))) return rc;
     }
   }
-  CK(cudaMemcpyAsync(u, h->u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  int info[5];
-  CK(cudaMemcpyAsync(info, h->st.flags, 5 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  return SEM_OK;
+}
+
+// per-problem results after a solve (sync); launches of a replayed graph are
+// added to the tracing counters
+static int collect(sem_handle* h, cudaStream_t s, bool graph_used, sem_result* res, double* const* hist, int hlen) {
+  const int nb = h->nb, stride = h->st.stride;
+  std::vector<int> fl(3 * nb);
+  CK(cudaMemcpyAsync(fl.data(), h->st.flags, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  std::vector<double> rr((size_t)nb * stride);
+  CK(cudaMemcpyAsync(rr.data(), h->st.rr, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const int it = info[4], status = info[1];
-  if (use_graph) {
-    for (int c = 0; c < SEM_K_NCLASS; ++c)
-      h->launches[c] += h->graph_pro[c] + (long long)std::max(0, it - 1) * h->graph_body[c];
+  int itmax = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int it = fl[2 * nb + k];
+    itmax = std::max(itmax, it);
+    const double* r = rr.data() + (size_t)k * stride;
+    res[k].iterations = it;
+    res[k].status = fl[2 * k + 1];
+    res[k].res0 = std::sqrt(r[0]);
+    res[k].res = std::sqrt(r[it]);
+    res[k].rbar = (it > 0 && r[it] > 0) ? std::log10(std::sqrt(r[0] / r[it])) / it : 0.0;
+    if (hist && hist[k])
+      for (int i = 0; i <= it && i < hlen; ++i) hist[k][i] = std::sqrt(r[i]);
   }
+  if (graph_used)
+    for (int c = 0; c < SEM_K_NCLASS; ++c)
+      h->launches[c] += h->graph_pro[c] + (long long)std::max(0, itmax - 1) * h->graph_body[c];
   h->solves++;
-  std::vector<double> rr(it + 1);
-  CK(cudaMemcpy(rr.data(), h->st.rr, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost));
-  if (history)
-    for (int i = 0; i <= it && i < hlen; ++i) history[i] = std::sqrt(rr[i]);
-  res->iterations = it;
-  res->status = status;
-  res->res0 = std::sqrt(rr[0]);
-  res->res = std::sqrt(rr[it]);
-  res->rbar = (it > 0 && rr[it] > 0) ? std::log10(std::sqrt(rr[0] / rr[it])) / it : 0.0;
-  return status;
+  return SEM_OK;
+}
+
+int sem_pcg_solve(sem_handle* h, double* u, const double* f, sem_result* res, double* history, int32_t hlen,
+                  void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!u || !f || !res) return fail(SEM_BAD_ARG, "null argument");
+  if (h->nb != 1) return fail(SEM_BAD_ARG, "use sem_batch_solve for stacked problems");
+  cudaStream_t s = as_stream(stream);
+  const int rows = top(h).Ny - 1, Nx = top(h).Nx;
+  if (!h->cfg.periodic) {
+    KL(h, SEM_K_VECTOR, s, launch_stack_in(nullptr, f, h->fi, 1, rows, Nx, h->n, s));
+    KL(h, SEM_K_VECTOR, s, launch_stack_in(nullptr, u, h->u, 1, rows, Nx, h->n, s));
+  } else {
+    CK(cudaMemcpyAsync(h->fi, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->u, u, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  const bool graph_used = !h->prof && h->solves > 0;
+  if ((rc = run_solve(h, s))) return rc;
+  CK(cudaMemcpyAsync(u, h->u, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double* hp[1] = {history};
+  if ((rc = collect(h, s, graph_used, res, hp, hlen))) return rc;
+  return res->status;
 }
 
 int sem_profile(sem_handle* h, int32_t enable) {
@@ -1002,6 +1060,230 @@ int sem_profile_read(sem_handle* h, double* ms, int64_t* launches) {
   }
   if (launches)
     for (int c = 0; c < SEM_K_NCLASS; ++c) launches[c] = h->launches[c];
+  return SEM_OK;
+}
+
+}  // extern "C"
+
+// ---- batched solves: many independent problems, one graph launch ---------
+
+namespace {
+
+struct BatchGroup {
+  sem_handle* h = nullptr;
+  std::vector<int> members;  // problem indices in the caller's order
+  cudaStream_t branch = nullptr, body = nullptr;
+};
+
+bool same_group(const sem_config& a, const sem_config& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.p == b.p && a.periodic == b.periodic && a.lx == b.lx && a.ly == b.ly &&
+         a.overlap_rule == b.overlap_rule && a.overlap == b.overlap && a.weight == b.weight && a.ns1 == b.ns1 &&
+         a.ns2 == b.ns2 && a.variable_cycle == b.variable_cycle && a.precision == b.precision && a.tol == b.tol &&
+         a.i_max == b.i_max && a.nu_kind == b.nu_kind && a.nu_a == b.nu_a && a.nu_b == b.nu_b;
+}
+
+bool stackable(const sem_config& c) {
+  return !c.periodic && !c.x_edges && !c.y_edges && !c.nu_kind && c.weight != SEM_W_LEARNED;
+}
+
+}  // namespace
+
+struct sem_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<BatchGroup> groups;
+  const double** host_ptrs = nullptr;  // pinned: [f pointers | u pointers] in group-member order
+  const double** dev_ptrs = nullptr;   // device copy of host_ptrs
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t main = nullptr;
+  int solves = 0;
+};
+
+extern "C" {
+
+void sem_batch_destroy(sem_batch* b) {
+  if (!b) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->main) cudaStreamDestroy(b->main);
+  for (auto& g : b->groups) {
+    if (g.branch) cudaStreamDestroy(g.branch);
+    if (g.body) cudaStreamDestroy(g.body);
+    sem_destroy(g.h);
+  }
+  if (b->dev_ptrs) cudaFree(b->dev_ptrs);
+  if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
+  if (prev >= 0) cudaSetDevice(prev);
+  cudaGetLastError();
+  delete b;
+}
+
+int sem_batch_create(const sem_config* cfgs, int32_t n, sem_batch** out) {
+  g_err.clear();
+  if (!cfgs || !out || n < 1) return fail(SEM_BAD_ARG, "invalid argument");
+  sem_batch* b = new sem_batch();
+  b->n = n;
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(SEM_CUDA_ERROR, "no usable CUDA device");
+  }
+  // group identical stackable configurations; anything else solves alone
+  std::vector<std::vector<int>> groups;
+  for (int k = 0; k < n; ++k) {
+    if (cfgs[k].periodic) {
+      delete b;
+      return fail(SEM_BAD_ARG, "batched problems need Dirichlet walls");
+    }
+    int found = -1;
+    if (stackable(cfgs[k]))
+      for (size_t g = 0; g < groups.size(); ++g)
+        if (stackable(cfgs[groups[g][0]]) && same_group(cfgs[groups[g][0]], cfgs[k]) &&
+            (long)(groups[g].size() + 1) * cfgs[k].ny <= 4096) {
+          found = (int)g;
+          break;
+        }
+    if (found < 0) {
+      groups.push_back({k});
+    } else {
+      groups[found].push_back(k);
+    }
+  }
+  for (auto& mem : groups) {
+    BatchGroup g;
+    g.members = mem;
+    int rc = create_handle(cfgs[mem[0]], (int)mem.size(), &g.h);
+    if (rc) {
+      sem_batch_destroy(b);
+      return rc;
+    }
+    b->groups.push_back(g);
+  }
+  if (cudaMallocHost(&b->host_ptrs, 2 * n * sizeof(double*)) != cudaSuccess ||
+      cudaMalloc(&b->dev_ptrs, 2 * n * sizeof(double*)) != cudaSuccess) {
+    cudaGetLastError();
+    sem_batch_destroy(b);
+    return fail(SEM_OOM, "pointer tables");
+  }
+  *out = b;
+  return SEM_OK;
+}
+
+int sem_batch_info(const sem_batch* b, int32_t* groups, int64_t* unknowns) {
+  if (!b) return fail(SEM_BAD_ARG, "null batch");
+  if (groups) *groups = (int32_t)b->groups.size();
+  if (unknowns) {
+    int64_t t = 0;
+    for (auto& g : b->groups) t += g.h->n_unknowns;
+    *unknowns = t;
+  }
+  return SEM_OK;
+}
+
+int sem_batch_solve(sem_batch* b, double* const* u, const double* const* f, sem_result* res, void* stream) {
+  if (!b || !u || !f || !res) return fail(SEM_BAD_ARG, "null argument");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) {
+    cudaGetLastError();
+    return fail(SEM_BAD_ARG, "the current CUDA device is not the batch's device");
+  }
+  cudaStream_t s = as_stream(stream);
+  // pointer tables: f of every member, then u, in group order
+  int o = 0;
+  for (auto& g : b->groups)
+    for (int k : g.members) {
+      if (!u[k] || !f[k]) return fail(SEM_BAD_ARG, "null vector in the batch");
+      b->host_ptrs[o] = f[k];
+      b->host_ptrs[b->n + o] = u[k];
+      ++o;
+    }
+  CK(cudaMemcpyAsync(b->dev_ptrs, b->host_ptrs, 2 * b->n * sizeof(double*), cudaMemcpyHostToDevice, s));
+  auto stage_in = [&](BatchGroup& g, int off, cudaStream_t st) -> int {
+    sem_handle* h = g.h;
+    const int rows = h->rows_top, Nx = top(h).Nx, nm = (int)g.members.size();
+    KL(h, SEM_K_VECTOR, st, launch_stack_in(b->dev_ptrs + off, nullptr, h->fi, nm, rows, Nx, h->st.seg_len, st));
+    KL(h, SEM_K_VECTOR, st,
+       launch_stack_in(b->dev_ptrs + b->n + off, nullptr, h->u, nm, rows, Nx, h->st.seg_len, st));
+    return SEM_OK;
+  };
+  auto stage_out = [&](BatchGroup& g, int off, cudaStream_t st) -> int {
+    sem_handle* h = g.h;
+    const int rows = h->rows_top, Nx = top(h).Nx, nm = (int)g.members.size();
+    KL(h, SEM_K_VECTOR, st,
+       launch_stack_out(h->u, const_cast<double* const*>(b->dev_ptrs + b->n + off), nullptr, nm, rows, Nx,
+                        h->st.seg_len, st));
+    return SEM_OK;
+  };
+  int rc;
+  const bool graph_used = b->solves > 0;
+  if (!graph_used) {
+    // first solve: group by group, launch by launch (loads modules, sets limits)
+    int off = 0;
+    for (auto& g : b->groups) {
+      if ((rc = stage_in(g, off, s)) || (rc = run_solve(g.h, s)) || (rc = stage_out(g, off, s))) return rc;
+      off += (int)g.members.size();
+    }
+  } else {
+    if (!b->exec) {
+      // every group becomes one branch of a single graph: stage in, prologue,
+      // WHILE node over the MGCG iteration, stage out
+      CK(cudaStreamSynchronize(s));
+      CK(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+      for (auto& g : b->groups) {
+        CK(cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&g.body, cudaStreamNonBlocking));
+      }
+      cudaEvent_t fork;
+      CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      CK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed));
+      CK(cudaEventRecord(fork, b->main));
+      int off = 0;
+      std::vector<cudaEvent_t> joins;
+      for (auto& g : b->groups) {
+        cudaEvent_t join;
+        CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        joins.push_back(join);
+        CK(cudaStreamWaitEvent(g.branch, fork, 0));
+        if ((rc = stage_in(g, off, g.branch)) || (rc = capture_solve(g.h, g.branch, g.body)) ||
+            (rc = stage_out(g, off, g.branch))) {
+          end_capture_discard(b->main);
+          return rc;
+        }
+        CK(cudaEventRecord(join, g.branch));
+        CK(cudaStreamWaitEvent(b->main, join, 0));
+        off += (int)g.members.size();
+      }
+      CK(cudaStreamEndCapture(b->main, &b->graph));
+      CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+      CK(cudaEventDestroy(fork));
+      for (auto e : joins) CK(cudaEventDestroy(e));
+      for (auto& g : b->groups) g.h->launches[SEM_K_VECTOR] -= 3;  // staging launches counted at replay below
+    }
+    CK(cudaGraphLaunch(b->exec, s));
+    for (auto& g : b->groups) g.h->launches[SEM_K_VECTOR] += 3;
+  }
+  // results, problem by problem
+  for (auto& g : b->groups) {
+    std::vector<sem_result> r(g.members.size());
+    if ((rc = collect(g.h, s, graph_used, r.data(), nullptr, 0))) return rc;
+    for (size_t j = 0; j < g.members.size(); ++j) res[g.members[j]] = r[j];
+  }
+  b->solves++;
+  int worst = SEM_OK;
+  for (int k = 0; k < b->n; ++k) worst = std::max(worst, (int)res[k].status);
+  return worst;
+}
+
+int sem_batch_launches(const sem_batch* b, int64_t* launches) {
+  if (!b || !launches) return fail(SEM_BAD_ARG, "null argument");
+  *launches = 0;
+  for (auto& g : b->groups)
+    for (int c = 0; c < SEM_K_NCLASS; ++c) *launches += g.h->launches[c];
   return SEM_OK;
 }
 

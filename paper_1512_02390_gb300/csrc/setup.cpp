@@ -232,7 +232,10 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o, 
   auto gidx = [&](int e, int a, bool& valid) {
     int g = e * p + a - n_o;
     if (mesh.periodic) { valid = true; return (g % N + N) % N; }
-    valid = (g > 0 && g < n * p);
+    valid = !mesh.wall(g, p);
+    // a window never reaches across a wall into another stacked problem
+    if (valid && mesh.seg > 0 && (g < (e / mesh.seg) * mesh.seg * p || g > (e / mesh.seg + 1) * mesh.seg * p))
+      valid = false;
     return g;
   };
   // counting matrix for the arithmetic mean (Sec. 3.1): windows per node

@@ -13,14 +13,21 @@ struct Mesh1D {
   int n = 0;                  // elements
   bool periodic = false;
   std::vector<double> edges;  // n + 1 increasing coordinates
+  int seg = 0;                // > 0: a Dirichlet wall every seg elements (stacked problems)
   double h(int e) const { return edges[e + 1] - edges[e]; }
   int nodes(int p) const { return periodic ? n * p : n * p + 1; }
   // neighbour of element e on side -1/+1; -1 at a Dirichlet wall
   int neighbour(int e, int side) const {
     int f = e + side;
+    if (seg > 0 && f >= 0 && f < n && f / seg != e / seg) return -1;
     if (f >= 0 && f < n) return f;
     if (!periodic) return -1;
     return (f % n + n) % n;
+  }
+  // is global node g (order p) a Dirichlet wall node?
+  bool wall(int g, int p) const {
+    if (periodic) return false;
+    return g <= 0 || g >= n * p || (seg > 0 && g % (seg * p) == 0);
   }
 };
 

@@ -91,3 +91,29 @@ class Solver:
 
     def profile_read(self):
         return B.sem_profile_read(self.h)
+
+
+class Batch:
+    """Many independent problems solved together (sem_batch_*)."""
+
+    def __init__(self, configs):
+        self.configs = [make_config(**c) for c in configs]
+        self.h = B.sem_batch_create(self.configs)
+        self.groups, self.unknowns = B.sem_batch_info(self.h)
+
+    def close(self):
+        if self.h is not None:
+            B.sem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, us, fs, stream=None):
+        return B.sem_batch_solve(self.h, us, fs, stream)
+
+    def launches(self):
+        return B.sem_batch_launches(self.h)
