@@ -72,8 +72,9 @@ def test_batch_matches_individual_solves(prec):
 
 
 def test_batch_reports_each_problems_status():
-    cfgs = [dict(nx=4, ny=4, p=4, i_max=2), dict(nx=4, ny=4, p=4, i_max=2)]
+    cfgs = [dict(nx=8, ny=8, p=4, i_max=2), dict(nx=8, ny=8, p=4, i_max=2)]
     batch = P.Batch(cfgs)
+    assert batch.groups == 1
     S = P.Solver(**cfgs[0])
     b1 = _rhs(S, 1)
     b0 = torch.zeros_like(b1)  # zero right side: converged at the start
