@@ -140,6 +140,113 @@ def _level_work(p, n_o_fixed, ne):
     return {"sweep_flops_per_cycle": sweep_flops, "sweep_launches_per_cycle": L}
 
 
+def c5_configs(seed=7, count=512, prec="tf32"):
+    """512 problems: n x n elements, n in {8,16,32,64}; p in {4,8,16,32};
+    n_o in {1,2}, drawn uniformly and independently with SplitMix64."""
+    import sem_inputs as SI
+    d = (SI.uniform01(seed, 3 * count).reshape(count, 3) * np.array([4, 4, 2])).astype(int)
+    return [dict(nx=8 << int(a), ny=8 << int(a), p=4 << int(b), overlap=1 + int(c), weight=5, precision=prec,
+                 tol=TOL, i_max=200) for a, b, c in d]
+
+
+def run_batched(args, flush, stream):
+    """C5: one batch solve (all 512 problems, one graph launch) per step."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    cfgs = c5_configs()
+    t0 = time.perf_counter()
+    batch = P.Batch(cfgs)
+    setup_s = time.perf_counter() - t0
+    bs, us = [], []
+    for k, c in enumerate(cfgs):
+        nx, ny = c["nx"] * c["p"] + 1, c["ny"] * c["p"] + 1
+        fn = torch.from_numpy(SI.uniform_nodal(1000 + k, (ny, nx)).ravel()).cuda()
+        # b = M f through one single-problem handle per shape would allocate
+        # 512 handles; the mass matrix of the batch member is applied by a
+        # solver of the same shape, created once per shape
+        bs.append(fn)
+        us.append(torch.zeros_like(fn))
+    shapes = {}
+    for k, c in enumerate(cfgs):
+        key = (c["nx"], c["p"], c["overlap"])
+        if key not in shapes:
+            shapes[key] = P.Solver(**c)
+        b = torch.empty_like(bs[k])
+        shapes[key].mass(bs[k], b)
+        bs[k] = b
+    for S in shapes.values():
+        S.close()
+    for _ in range(max(2, args.warmup)):
+        for u in us:
+            u.zero_()
+        res = batch.solve(us, bs)
+    l0 = batch.launches()
+    times = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = batch.solve(us, bs)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = (batch.launches() - l0) / len(times)
+    ms = float(np.mean(times))
+    its = [r.iterations for r in res]
+    ok = sum(1 for r in res if r.status == P.SEM_OK)
+    return {"problems": len(cfgs), "groups": batch.groups, "unknowns": batch.unknowns, "ms_per_batch_solve": ms,
+            "dof_per_s": batch.unknowns / (ms * 1e-3), "converged": ok, "iterations_min_max": [min(its), max(its)],
+            "kernel_launches_per_solve": launches, "graph_launches_per_solve": 1, "setup_s": round(setup_s, 2),
+            "precision": "tf32", "workload": "512 problems, seed 7: n^2 elements n in {8,16,32,64}, p in "
+                                           "{4,8,16,32}, n_o in {1,2}, U[-1,1] nodal RHS, MGCG(1,0) w_5 to 1e-10"}
+
+
+def run_learned(args, stream):
+    """C4: 64x64, p=16, x stretched to 1:32, nu contrast 100: learned weights vs w_5."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    from paper_1512_02390_gb300 import learned as LW
+    import sem_inputs as SI
+
+    out = {}
+    params, _ = LW.load_model()
+    for c in (10.0, 100.0):
+        kw = dict(nx=64, ny=64, p=16, overlap=2, x_edges=SI.geometric_edges(64, 1.0 / 64 / 32), nu=("contrast", c),
+                  tol=TOL, i_max=400, precision=HEADLINE)
+        px, py = LW.predict(params, **kw)
+        row = {}
+        for name, extra in (("w5", dict(weight=5)),
+                            ("learned", dict(weight="learned", learned_x=px.ravel(), learned_y=py.ravel()))):
+            S = P.Solver(**kw, **extra)
+            fn = torch.from_numpy(SI.uniform_nodal(SEED, S.shape).ravel()).cuda()
+            b = torch.empty_like(fn)
+            S.mass(fn, b)
+            u = torch.zeros_like(b)
+            for _ in range(2):
+                u.zero_()
+                res, _ = S.pcg_solve(u, b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u.zero_()
+            e0.record(stream)
+            res, _ = S.pcg_solve(u, b)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[name] = {"iterations": res.iterations, "status": res.status, "rbar": res.rbar, "ms": ms,
+                         "dof_per_s": (S.n_unknowns / (ms * 1e-3)) if res.status == 0 else 0.0}
+            S.close()
+        out["contrast_%d" % int(c)] = row
+    out["workload"] = ("64x64 elements, p=16, n_o=2, x geometric 1:32 (first width = h_y/32), nu = 1 + (c-1)(1/2 + "
+                       "1/2 sin 2 pi x cos 2 pi y), TF32 V-cycle, MGCG to 1e-10")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -304,6 +411,9 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
     }
+    if args.variants == "all" and rank == 0:
+        line["batched"] = run_batched(args, flush, stream)
+        line["learned"] = run_learned(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
         line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",
