@@ -82,3 +82,33 @@ inline cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 }  // namespace sem
+
+namespace sem {
+
+// Sum of the weighted Schwarz corrections at node (gj, gi): the R_s^T sum of
+// Eq. (correction:global) over the (at most 3 x 3) windows that hold the node,
+// in a fixed order.  E: element-blocked m x m corrections.
+template <typename T>
+__device__ __forceinline__ T window_sum(const DirView<T>& dx, const DirView<T>& dy, const T* __restrict__ E, int gj,
+                                        int gi) {
+  const int p = dx.p, no = dx.n_o, m = dx.m, mm = m * m;
+  const int ey_lo = floordiv(gj - no - 1, p), ey_hi = floordiv(gj + no, p);
+  const int ex_lo = floordiv(gi - no - 1, p), ex_hi = floordiv(gi + no, p);
+  T s = T(0);
+  for (int eyu = ey_lo; eyu <= ey_hi; ++eyu) {
+    int ey = eyu;
+    if (dy.periodic) ey = ((ey % dy.n) + dy.n) % dy.n;
+    else if (ey < 0 || ey >= dy.n) continue;
+    const int a = gj - eyu * p + no;
+    for (int exu = ex_lo; exu <= ex_hi; ++exu) {
+      int ex = exu;
+      if (dx.periodic) ex = ((ex % dx.n) + dx.n) % dx.n;
+      else if (ex < 0 || ex >= dx.n) continue;
+      const int b = gi - exu * p + no;
+      s += E[(long)(ey * dx.n + ex) * mm + a * m + b];
+    }
+  }
+  return s;
+}
+
+}  // namespace sem

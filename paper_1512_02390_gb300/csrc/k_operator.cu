@@ -32,10 +32,11 @@ size_t apply_smem() {
          sizeof(double) * kRedThreads;
 }
 
-template <typename T, int P>
+template <typename T, typename TF, int P>
 __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
-                                               const T* __restrict__ f, T* __restrict__ out, int dot,
-                                               double* __restrict__ part) {
+                                               const TF* __restrict__ f, T* __restrict__ out, int dot,
+                                               double* __restrict__ part, const T* __restrict__ E,
+                                               T* __restrict__ uout) {
   using Tl = Tile<P>;
   constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -54,7 +55,9 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
     const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
+    T v = T(0);
+    if (gx >= 0 && gy >= 0) v = E ? window_sum(dx, dy, E, gy, gx) : u[(long)gy * Nx + gx];
+    su[ly * LP + lx] = v;
   }
   // element stiffness of the tile and of its low-side neighbour (slot 0)
   for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
@@ -225,7 +228,8 @@ __device__ __forceinline__ void eo_products(const T* eo, const T* ev, T* dst_bas
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
                                                   const T* __restrict__ f, T* __restrict__ out, int dot,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, const T* __restrict__ E,
+                                                  T* __restrict__ uout) {
   using Q = EOTile<P>;
   constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE,
                 NV = Q::NV;
@@ -247,7 +251,9 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
     const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    su[ly * LP + lx] = (gx >= 0 && gy >= 0) ? u[(long)gy * Nx + gx] : T(0);
+    T v = T(0);
+    if (gx >= 0 && gy >= 0) v = E ? window_sum(dx, dy, E, gy, gx) : u[(long)gy * Nx + gx];
+    su[ly * LP + lx] = v;
   }
   // E/O tables of slot s = element ex0 + s - 1 (slot 0: low-side neighbour)
   for (int idx = threadIdx.x; idx < 2 * (TE + 1) * EO; idx += blockDim.x) {
@@ -424,39 +430,39 @@ __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-template <typename T, int P>
-cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f, T* out, int dot,
-                    double* part, int* nparts, cudaStream_t s) {
+template <typename T, typename TF, int P>
+cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
+                    double* part, int* nparts, cudaStream_t s, const T* E, T* uout) {
   using Tl = Tile<P>;
   dim3 grid((dx.n + Tl::TE - 1) / Tl::TE, (dy.n + Tl::TE - 1) / Tl::TE);
   if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
   if (nparts) *nparts = grid.x * grid.y;
-  if constexpr (std::is_same<T, double>::value && P >= 4) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<TF, double>::value && P >= 4) {
     const size_t sm = apply_eo_smem<T, P>();
     cudaError_t e = allow_smem(k_apply_eo<T, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout);
   } else {
     const size_t sm = apply_smem<T, P>();
-    cudaError_t e = allow_smem(k_apply<T, P>, sm);
+    cudaError_t e = allow_smem(k_apply<T, TF, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part);
+    k_apply<T, TF, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f, T* out, int dot,
-                         double* part, int* nparts, cudaStream_t s) {
+template <typename T, typename TF>
+cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
+                         double* part, int* nparts, cudaStream_t s, const T* E, T* uout) {
   switch (dx.p) {
-    case 1: return apply_p<T, 1>(dx, dy, u, f, out, dot, part, nparts, s);
-    case 2: return apply_p<T, 2>(dx, dy, u, f, out, dot, part, nparts, s);
-    case 4: return apply_p<T, 4>(dx, dy, u, f, out, dot, part, nparts, s);
-    case 8: return apply_p<T, 8>(dx, dy, u, f, out, dot, part, nparts, s);
-    case 16: return apply_p<T, 16>(dx, dy, u, f, out, dot, part, nparts, s);
-    case 32: return apply_p<T, 32>(dx, dy, u, f, out, dot, part, nparts, s);
+    case 1: return apply_p<T, TF, 1>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 2: return apply_p<T, TF, 2>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 4: return apply_p<T, TF, 4>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 8: return apply_p<T, TF, 8>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 16: return apply_p<T, TF, 16>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 32: return apply_p<T, TF, 32>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -487,10 +493,15 @@ template cudaError_t launch_apply_var<double>(const DirView<double>&, const DirV
 template cudaError_t launch_apply_var<float>(const DirView<float>&, const DirView<float>&, const VarView<float>&,
                                              const float*, const float*, float*, int, double*, int*, cudaStream_t);
 
-template cudaError_t launch_apply<double>(const DirView<double>&, const DirView<double>&, const double*,
-                                          const double*, double*, int, double*, int*, cudaStream_t);
-template cudaError_t launch_apply<float>(const DirView<float>&, const DirView<float>&, const float*,
-                                         const float*, float*, int, double*, int*, cudaStream_t);
+template cudaError_t launch_apply<double, double>(const DirView<double>&, const DirView<double>&, const double*,
+                                                  const double*, double*, int, double*, int*, cudaStream_t,
+                                                  const double*, double*);
+template cudaError_t launch_apply<float, float>(const DirView<float>&, const DirView<float>&, const float*,
+                                                const float*, float*, int, double*, int*, cudaStream_t, const float*,
+                                                float*);
+template cudaError_t launch_apply<float, double>(const DirView<float>&, const DirView<float>&, const float*,
+                                                 const double*, float*, int, double*, int*, cudaStream_t,
+                                                 const float*, float*);
 
 cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f, double* b,
                         double* part, int* nparts, cudaStream_t s) {

@@ -215,30 +215,57 @@ __global__ void __launch_bounds__(32 * kMmaWarps) k_sweep_mma(DirView<float> dx,
   float* wx = ly + MP;
   float* wy = wx + MP;
   const int m = dx.m, mm = m * m, p = dx.p, no = dx.n_o;
+  int cur_tx = -1, cur_ty = -1;  // tables currently in this warp's shared memory
   for (int sidx = blockIdx.x * kMmaWarps + warp; sidx < nsub; sidx += gridDim.x * kMmaWarps) {
     const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
     const int tx = dx.tab[ex], ty = dy.tab[ey];
-    const float* gSx = dx.S + (long)tx * mm;
-    const float* gSy = dy.S + (long)ty * mm;
-    for (int idx = lane; idx < MP * MP; idx += 32) {
+    // window gather: every lane issues all its loads before the first store
+    constexpr int PER = (MP * MP + 31) / 32;
+    float xv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane + 32 * q;
       const int a = idx / MP, b = idx - a * MP;
-      const bool in = a < m && b < m;
-      float xv = 0.f;
-      if (in) {
+      float v = 0.f;
+      if (idx < MP * MP && a < m && b < m) {
         const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
         const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
-        if (gx >= 0 && gy >= 0) xv = (float)r[(long)gy * dx.N + gx];
+        if (gx >= 0 && gy >= 0) v = (float)r[(long)gy * dx.N + gx];
       }
-      X[a * SA + b] = xv;
-      Sx[a * SA + b] = in ? gSx[a * m + b] : 0.f;
-      Sy[a * SA + b] = in ? gSy[a * m + b] : 0.f;
+      xv[q] = v;
     }
-    for (int idx = lane; idx < MP; idx += 32) {
-      const bool in = idx < m;
-      lx[idx] = in ? dx.lam[tx * m + idx] : 1.f;
-      ly[idx] = in ? dy.lam[ty * m + idx] : 1.f;
-      wx[idx] = in ? dx.w[tx * m + idx] : 0.f;
-      wy[idx] = in ? dy.w[ty * m + idx] : 0.f;
+    // tables: reloaded only when this subdomain's type differs from the last
+    if (tx != cur_tx) {
+      const float* gSx = dx.S + (long)tx * mm;
+      for (int idx = lane; idx < MP * MP; idx += 32) {
+        const int a = idx / MP, b = idx - a * MP;
+        Sx[a * SA + b] = (a < m && b < m) ? gSx[a * m + b] : 0.f;
+      }
+      for (int idx = lane; idx < MP; idx += 32) {
+        lx[idx] = idx < m ? dx.lam[tx * m + idx] : 1.f;
+        wx[idx] = idx < m ? dx.w[tx * m + idx] : 0.f;
+      }
+      cur_tx = tx;
+    }
+    if (ty != cur_ty) {
+      const float* gSy = dy.S + (long)ty * mm;
+      for (int idx = lane; idx < MP * MP; idx += 32) {
+        const int a = idx / MP, b = idx - a * MP;
+        Sy[a * SA + b] = (a < m && b < m) ? gSy[a * m + b] : 0.f;
+      }
+      for (int idx = lane; idx < MP; idx += 32) {
+        ly[idx] = idx < m ? dy.lam[ty * m + idx] : 1.f;
+        wy[idx] = idx < m ? dy.w[ty * m + idx] : 0.f;
+      }
+      cur_ty = ty;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx < MP * MP) {
+        const int a = idx / MP, b = idx - a * MP;
+        X[a * SA + b] = xv[q];
+      }
     }
     __syncwarp();
     // P1: Y = S_y^T X
@@ -275,7 +302,8 @@ cudaError_t sweep_mma_launch(const DirView<float>& dx, const DirView<float>& dy,
   cudaError_t e = allow_smem(k_sweep_mma<TIn, MODE, MP>, sm);
   if (e != cudaSuccess) return e;
   const int nsub = dx.n * dy.n;
-  const int grid = std::min((nsub + kMmaWarps - 1) / kMmaWarps, 152 * 8);
+  // about two subdomains per warp: tables are reused between them
+  const int grid = std::max(1, std::min((nsub + 2 * kMmaWarps - 1) / (2 * kMmaWarps), 152 * 4));
   k_sweep_mma<TIn, MODE, MP><<<grid, 32 * kMmaWarps, sm, s>>>(dx, dy, r, E, nu_inv, nsub);
   return cudaGetLastError();
 }

@@ -14,10 +14,13 @@ constexpr int kMaxPartials = 1 << 17;
 // ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
 // out = A u (f == nullptr) or out = f - A u.  dot: 0 none, 1 part[cta] = sum
 // u.out, 2 part[cta] = sum out.out over the CTA's nodes.  *nparts receives
-// the number of partials written.
-template <typename T>
-cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const T* f,
-                         T* out, int dot, double* part, int* nparts, cudaStream_t s);
+// the number of partials written.  With E != nullptr the input u is not read:
+// it is assembled on the fly as the Schwarz correction sum_s R_s^T E[s] (the
+// scatter of Alg. 2 fused into the residual) and written to uout.
+template <typename T, typename TF>
+cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f,
+                         T* out, int dot, double* part, int* nparts, cudaStream_t s, const T* E = nullptr,
+                         T* uout = nullptr);
 
 // Variable-diffusivity operator B(nu) (Sec. 4.3): element data of one level.
 template <typename T>

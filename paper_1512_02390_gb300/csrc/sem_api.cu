@@ -236,15 +236,22 @@ const T* NUI(const Level& l) {
   if constexpr (std::is_same<T, double>::value) return l.nu_inv64; else return l.nu_inv32;
 }
 
-// out = A_l u (f null) or f - A_l u on level l; B_l(nu) when nu varies
-template <typename T>
-int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const T* f, T* out, int dot, double* part,
-                int* np, cudaStream_t s) {
+// out = A_l u (f null) or f - A_l u on level l; B_l(nu) when nu varies.
+// With E, u is assembled from the Schwarz corrections (fused scatter) and
+// written to uout (Poisson operator only).
+template <typename T, typename TF = T>
+int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f, T* out, int dot, double* part,
+                int* np, cudaStream_t s, const T* E = nullptr, T* uout = nullptr) {
   if (l.var) {
-    KLN(h, cls, 2, s, launch_apply_var<T>(DX<T>(l), DY<T>(l), VV<T>(l), u, f, out, dot, part, np, s));
-  } else {
-    KL(h, cls, s, launch_apply<T>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s));
+    if constexpr (std::is_same<T, TF>::value) {
+      if (E) return fail(SEM_BAD_ARG, "fused scatter needs the Poisson operator");
+      KLN(h, cls, 2, s, launch_apply_var<T>(DX<T>(l), DY<T>(l), VV<T>(l), u, f, out, dot, part, np, s));
+      return SEM_OK;
+    } else {
+      return fail(SEM_BAD_ARG, "variable operator needs a right side of its own type");
+    }
   }
+  KL(h, cls, s, (launch_apply<T, TF>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s, E, uout)));
   return SEM_OK;
 }
 
@@ -274,11 +281,11 @@ int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cud
   return SEM_OK;
 }
 
-template <typename T>
-int smooth(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
+template <typename T, typename TF = T>
+int smooth(sem_handle* h, const Level& l, const TF* f, T* u, int n, cudaStream_t s) {
   T* r = static_cast<T*>(l.r);
   for (int k = 0; k < n; ++k) {
-    int rc = level_apply<T>(h, l, SEM_K_APPLY_MG, u, f, r, 0, nullptr, nullptr, s);
+    int rc = level_apply<T, TF>(h, l, SEM_K_APPLY_MG, u, f, r, 0, nullptr, nullptr, s);
     if (rc) return rc;
     rc = sweep<T, T, T>(h, l, r, u, true, s);
     if (rc) return rc;
@@ -286,29 +293,64 @@ int smooth(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t 
   return SEM_OK;
 }
 
-// z = MultigridCycle(0, rtop), Alg. 3, with the level vectors in type T
+// One level of the down-sweep from u_l = 0 with one smoothing step: the
+// sweep writes the corrections E; the residual kernel assembles u_l from E
+// (scatter fused) and writes r_l = f_l - A_l u_l.
+template <typename T, typename TF>
+int level_down_fused(sem_handle* h, const Level& l, const TF* f, T* u, cudaStream_t s) {
+  T* E = static_cast<T*>(l.E);
+  T* r = static_cast<T*>(l.r);
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TF>(DX<T>(l), DY<T>(l), f, E, h->sweep_mode, NUI<T>(l), s)));
+  return level_apply<T, TF>(h, l, SEM_K_APPLY_MG, nullptr, f, r, 0, nullptr, nullptr, s, E, u);
+}
+
+// z = MultigridCycle(0, rtop), Alg. 3, with the level vectors in type T.  In
+// the mixed mode the finest level reads the FP64 residual directly.
 template <typename T>
 int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
   const int L = h->L;
   auto& lv = h->lev;
-  const T* fL;
-  T* uL;
-  if constexpr (std::is_same<T, double>::value) {
-    fL = rtop;
-    uL = zout;
-  } else {
+  constexpr bool dbl = std::is_same<T, double>::value;
+  // the finest right side: FP64 in both modes, except the variable operator in
+  // the mixed mode (converted once)
+  const bool convert_top = !dbl && lv[L].var;
+  if (convert_top)
     KL(h, SEM_K_VECTOR, s, (launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
-    fL = static_cast<const T*>(lv[L].f);
-    uL = static_cast<T*>(lv[L].u);
-  }
+  T* uL = dbl ? reinterpret_cast<T*>(zout) : static_cast<T*>(lv[L].u);
   int rc;
   for (int l = L; l >= 1; --l) {
-    const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
-    if ((rc = smooth_from_zero<T>(h, lv[l], fl, ul, h->ns1[l], s))) return rc;
     T* rl = static_cast<T*>(lv[l].r);
-    if ((rc = level_apply<T>(h, lv[l], SEM_K_APPLY_MG, ul, fl, rl, 0, nullptr, nullptr, s))) return rc;
-    KL(h, SEM_K_RESTRICT, s, launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
+    const bool fuse = h->ns1[l] == 1 && !lv[l].var;
+    if (l == L && !convert_top) {  // right side rtop (FP64)
+      if (fuse) {
+        if ((rc = level_down_fused<T, double>(h, lv[l], rtop, ul, s))) return rc;
+      } else {
+        if constexpr (dbl) {
+          if ((rc = smooth_from_zero<T>(h, lv[l], rtop, ul, h->ns1[l], s))) return rc;
+        } else {
+          // several pre-smoothing steps from an FP64 right side: first sweep on
+          // rtop itself, then residual sweeps
+          if (h->ns1[l] <= 0) {
+            CK(cudaMemsetAsync(ul, 0, lv[l].nodes * sizeof(T), s));
+          } else {
+            if ((rc = sweep<T, double, T>(h, lv[l], rtop, ul, false, s))) return rc;
+            if ((rc = smooth<T, double>(h, lv[l], rtop, ul, h->ns1[l] - 1, s))) return rc;
+          }
+        }
+        if ((rc = level_apply<T, double>(h, lv[l], SEM_K_APPLY_MG, ul, rtop, rl, 0, nullptr, nullptr, s))) return rc;
+      }
+    } else {
+      const T* fl = static_cast<const T*>(lv[l].f);
+      if (fuse) {
+        if ((rc = level_down_fused<T, T>(h, lv[l], fl, ul, s))) return rc;
+      } else {
+        if ((rc = smooth_from_zero<T>(h, lv[l], fl, ul, h->ns1[l], s))) return rc;
+        if ((rc = level_apply<T>(h, lv[l], SEM_K_APPLY_MG, ul, fl, rl, 0, nullptr, nullptr, s))) return rc;
+      }
+    }
+    KL(h, SEM_K_RESTRICT, s,
+       launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
                           static_cast<T*>(lv[l - 1].f), s));
   }
   if (h->Binv)
@@ -317,20 +359,27 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
   else
     KLN(h, SEM_K_COARSE, 4, s,
         launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
-  bool z_written = std::is_same<T, double>::value;
+  bool z_written = dbl;
   for (int l = 1; l <= L; ++l) {
-    const T* fl = (l == L) ? fL : static_cast<const T*>(lv[l].f);
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
     if (l == L && !z_written && h->ns2[l] == 0) {
-      KL(h, SEM_K_PROLONG, s, (launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
-                                     uc, ul, zout, s)));
+      KL(h, SEM_K_PROLONG, s,
+         (launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
+                                    uc, ul, zout, s)));
       z_written = true;
       continue;
     }
-    KL(h, SEM_K_PROLONG, s, (launch_prolong<T, T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc, ul,
-                              ul, s)));
-    if ((rc = smooth<T>(h, lv[l], fl, ul, h->ns2[l], s))) return rc;
+    KL(h, SEM_K_PROLONG, s,
+       (launch_prolong<T, T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc, ul,
+                             ul, s)));
+    if (h->ns2[l] > 0) {
+      if (l == L && !convert_top) {
+        if ((rc = smooth<T, double>(h, lv[l], rtop, ul, h->ns2[l], s))) return rc;
+      } else {
+        if ((rc = smooth<T>(h, lv[l], static_cast<const T*>(lv[l].f), ul, h->ns2[l], s))) return rc;
+      }
+    }
   }
   if (!z_written) KL(h, SEM_K_VECTOR, s, (launch_convert<float, double>(lv[L].nodes, static_cast<const float*>(lv[L].u), zout, s)));
   return SEM_OK;
