@@ -116,9 +116,10 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
         }
       }
       val = sMy[jy] * xs + sMx[ix] * ys;
-      if (f) val = f[o] - val;
+      if (f) val = T(f[o]) - val;
     }
     out[o] = val;
+    if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
     if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
     else if (dot == 2) acc += (double)val * (double)val;
   }
@@ -311,9 +312,10 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
       T ys = yc[b * TN];
       if (b == 0) ys += yc[(P - NP) * TN];
       val = sMy[jy] * xs + sMx[ix] * ys;
-      if (f) val = f[o] - val;
+      if (f) val = T(f[o]) - val;
     }
     out[o] = val;
+    if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
     if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
     else if (dot == 2) acc += (double)val * (double)val;
   }
