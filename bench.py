@@ -159,6 +159,9 @@ def run_batched(args, flush, stream):
     t0 = time.perf_counter()
     batch = P.Batch(cfgs)
     setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch.autotune()
+    tune_s = time.perf_counter() - t0
     bs, us = [], []
     for k, c in enumerate(cfgs):
         nx, ny = c["nx"] * c["p"] + 1, c["ny"] * c["p"] + 1
@@ -202,6 +205,7 @@ def run_batched(args, flush, stream):
     return {"problems": len(cfgs), "groups": batch.groups, "unknowns": batch.unknowns, "ms_per_batch_solve": ms,
             "dof_per_s": batch.unknowns / (ms * 1e-3), "converged": ok, "iterations_min_max": [min(its), max(its)],
             "kernel_launches_per_solve": launches, "graph_launches_per_solve": 1, "setup_s": round(setup_s, 2),
+            "autotune_s": round(tune_s, 2),
             "precision": "tf32", "workload": "512 problems, seed 7: n^2 elements n in {8,16,32,64}, p in "
                                            "{4,8,16,32}, n_o in {1,2}, U[-1,1] nodal RHS, MGCG(1,0) w_5 to 1e-10"}
 
@@ -266,6 +270,7 @@ def run_ours(args):
 
     def make(prec, n_o):
         S = P.Solver(nx=NX, ny=NY, p=P_ORDER, overlap=n_o, weight=5, precision=prec, tol=TOL, i_max=100)
+        S.tune = S.autotune()  # launch shapes per level, timed on this GPU (results unchanged)
         fn = SI.uniform_nodal(SEED + rank, S.shape)  # each replica solves its own problem
         b = torch.empty(S.nx_nodes * S.ny_nodes, dtype=torch.float64, device="cuda")
         S.mass(torch.from_numpy(fn.ravel()).cuda(), b)
@@ -325,7 +330,9 @@ def run_ours(args):
             ms = float(t.item())
         variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
                          "iterations": res.iterations, "status": res.status,
-                         "final_rel_residual": res.res / res.res0 if res.res0 else 0.0}
+                         "final_rel_residual": res.res / res.res0 if res.res0 else 0.0,
+                         "launch_shapes": {"p%d" % (1 << l): {"fuse": t[0], "spw": t[1], "us": round(t[2], 2)}
+                                           for l, t in S.tune.items()}}
         if not is_head:
             variants[key]["class_ms_per_solve"] = {k: round(v[0] / 2, 4) for k, v in vprof.items()}
         if is_head:

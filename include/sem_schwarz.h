@@ -225,6 +225,34 @@ typedef enum sem_kernel_class {
 int sem_profile(sem_handle* h, int32_t enable);
 int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
 
+/* ---- launch-shape autotuning --------------------------------------------------
+ * Not in the paper: two launch choices per level l = 1..log2(p) that change the
+ * speed of Alg. 3 but not its arithmetic (the results are bitwise the same):
+ *   fuse  with one pre-smoothing step, the down-sweep of the V-cycle writes the
+ *         Schwarz corrections E_s, and ONE residual kernel assembles
+ *         u_l = sum_s R_s^T E_s itself (Eq. (correction:global), same order of
+ *         summation as the scatter kernel), writes u_l and r_l = f_l - A_l u_l.
+ *         Saves a launch and a pass over u_l; costs re-assembly of u_l at the
+ *         halos of the residual's tiles (worth it at small p_l only).
+ *   spw   reduced-precision tensor-core sweep: subdomains per warp (sets the
+ *         grid size; a warp that loops reuses its factor tables).
+ * Defaults (no tuning): fuse 0, spw 1.  sem_autotune (sync) times every
+ * candidate on the handle's own level vectors (best of 3 x 10 steps, CUDA
+ * events) and keeps the fastest; with cache_path != NULL it first looks each
+ * level up in that JSON-lines file (key: device name, p_l, n_o, precision,
+ * operator kind, element grid) and stores what it measured.  Tuning or setting
+ * a level discards the captured solve graph; the next solve captures a new one.
+ * It overwrites the level work vectors and the MGCG residual (no solve may be
+ * in flight on the handle). */
+typedef struct sem_level_tune {
+  int32_t fuse; /* 0 or 1 */
+  int32_t spw;  /* 1..64 */
+  double us;    /* measured time of the level's down-sweep step (microseconds; 0 if not timed) */
+} sem_level_tune;
+int sem_autotune(sem_handle* h, const char* cache_path, void* stream);
+int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t);
+int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t);
+
 /* Allocation-free Schwarz correction.  The paper has no counterpart: this is a
  * deployment variant of the correction step of Alg. 2,
  *     u += sum_s R_s^T W A_ss^{-1} R_s r      (Eq. (correction:global)),
@@ -318,6 +346,9 @@ int sem_batch_info(const sem_batch* b, int32_t* groups, int64_t* unknowns);
 int sem_batch_solve(sem_batch* b, double* const* u, const double* const* f, sem_result* res, void* stream);
 /* Kernel launches of the batch since creation (tracing, host). */
 int sem_batch_launches(const sem_batch* b, int64_t* launches);
+/* sem_autotune for every group of the batch (sync); the next sem_batch_solve
+ * captures a new batch graph. */
+int sem_batch_autotune(sem_batch* b, const char* cache_path, void* stream);
 
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);

@@ -32,6 +32,7 @@ EXPORTS = [
     "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
     "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
+    "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune",
     "sem_status_string", "sem_last_error",
 ]
 SEM_MLP_PARAMS = 4610
@@ -60,6 +61,10 @@ class sem_result(ctypes.Structure):
 class sem_level_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("n_o", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("n_tables_x", ctypes.c_int32), ("nx_nodes", ctypes.c_int32)]
+
+
+class sem_level_tune(ctypes.Structure):
+    _fields_ = [("fuse", ctypes.c_int32), ("spw", ctypes.c_int32), ("us", ctypes.c_double)]
 
 
 class sem_sweep_tables(ctypes.Structure):
@@ -115,6 +120,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_batch_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]),
         "sem_batch_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), vp]),
         "sem_batch_launches": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "sem_autotune": (i32, [vp, ctypes.c_char_p, vp]),
+        "sem_get_tune": (i32, [vp, i32, ctypes.POINTER(sem_level_tune)]),
+        "sem_set_tune": (i32, [vp, i32, ctypes.POINTER(sem_level_tune)]),
+        "sem_batch_autotune": (i32, [vp, ctypes.c_char_p, vp]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -345,3 +354,28 @@ def sem_batch_launches(b) -> int:
     v = ctypes.c_int64()
     _check(load_library().sem_batch_launches(b, ctypes.byref(v)))
     return v.value
+
+
+def _path_arg(path):
+    return None if path is None else os.fsencode(path)
+
+
+def sem_autotune(h, cache_path=None, stream=None) -> None:
+    """Time the launch-shape candidates of every level (or read them from the cache file)."""
+    _check(load_library().sem_autotune(h, _path_arg(cache_path), _stream(stream)))
+
+
+def sem_get_tune(h, level: int):
+    """(fuse, spw, us) of level `level` (1..log2 p)."""
+    t = sem_level_tune()
+    _check(load_library().sem_get_tune(h, int(level), ctypes.byref(t)))
+    return t.fuse, t.spw, t.us
+
+
+def sem_set_tune(h, level: int, fuse: int, spw: int = 1) -> None:
+    t = sem_level_tune(int(fuse), int(spw), 0.0)
+    _check(load_library().sem_set_tune(h, int(level), ctypes.byref(t)))
+
+
+def sem_batch_autotune(b, cache_path=None, stream=None) -> None:
+    _check(load_library().sem_batch_autotune(b, _path_arg(cache_path), _stream(stream)))

@@ -297,23 +297,25 @@ __global__ void __launch_bounds__(32 * kMmaWarps) k_sweep_mma(DirView<float> dx,
 
 template <typename TIn, int MODE, int MP>
 cudaError_t sweep_mma_launch(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E,
-                             const float* nu_inv, cudaStream_t s) {
+                             const float* nu_inv, cudaStream_t s, int spw) {
   const size_t sm = sizeof(float) * MmaSmem<MP>::PER_WARP * kMmaWarps;
   cudaError_t e = allow_smem(k_sweep_mma<TIn, MODE, MP>, sm);
   if (e != cudaSuccess) return e;
   const int nsub = dx.n * dy.n;
-  // about two subdomains per warp: tables are reused between them
-  const int grid = std::max(1, std::min((nsub + 2 * kMmaWarps - 1) / (2 * kMmaWarps), 152 * 4));
+  // about spw subdomains per warp; a warp that loops reuses its tables when
+  // the next subdomain has the same type
+  const int per = kMmaWarps * std::max(1, spw);
+  const int grid = std::max(1, std::min((nsub + per - 1) / per, 152 * 16));
   k_sweep_mma<TIn, MODE, MP><<<grid, 32 * kMmaWarps, sm, s>>>(dx, dy, r, E, nu_inv, nsub);
   return cudaGetLastError();
 }
 
 template <typename TIn, int MODE>
 cudaError_t sweep_mma(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E,
-                      const float* nu_inv, cudaStream_t s) {
-  if (dx.m <= 16) return sweep_mma_launch<TIn, MODE, 16>(dx, dy, r, E, nu_inv, s);
-  if (dx.m <= 32) return sweep_mma_launch<TIn, MODE, 32>(dx, dy, r, E, nu_inv, s);
-  if (dx.m <= 48) return sweep_mma_launch<TIn, MODE, 48>(dx, dy, r, E, nu_inv, s);
+                      const float* nu_inv, cudaStream_t s, int spw) {
+  if (dx.m <= 16) return sweep_mma_launch<TIn, MODE, 16>(dx, dy, r, E, nu_inv, s, spw);
+  if (dx.m <= 32) return sweep_mma_launch<TIn, MODE, 32>(dx, dy, r, E, nu_inv, s, spw);
+  if (dx.m <= 48) return sweep_mma_launch<TIn, MODE, 48>(dx, dy, r, E, nu_inv, s, spw);
   return cudaErrorInvalidValue;
 }
 
@@ -354,10 +356,10 @@ __global__ void __launch_bounds__(256) k_scatter(DirView<T> dx, DirView<T> dy, c
 
 template <typename T, typename TIn>
 cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
-                         const T* nu_inv, cudaStream_t s) {
+                         const T* nu_inv, cudaStream_t s, int spw) {
   if constexpr (std::is_same<T, float>::value) {
-    if (mode == 1) return sweep_mma<TIn, 1>(dx, dy, r, E, nu_inv, s);
-    if (mode == 2) return sweep_mma<TIn, 2>(dx, dy, r, E, nu_inv, s);
+    if (mode == 1) return sweep_mma<TIn, 1>(dx, dy, r, E, nu_inv, s, spw);
+    if (mode == 2) return sweep_mma<TIn, 2>(dx, dy, r, E, nu_inv, s, spw);
   }
   const int m = dx.m;
   const size_t sm = sizeof(T) * (4 * m * m + 4 * m);
@@ -378,11 +380,11 @@ cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* 
 }
 
 template cudaError_t launch_sweep<double, double>(const DirView<double>&, const DirView<double>&, const double*,
-                                                  double*, int, const double*, cudaStream_t);
+                                                  double*, int, const double*, cudaStream_t, int);
 template cudaError_t launch_sweep<float, float>(const DirView<float>&, const DirView<float>&, const float*, float*,
-                                                int, const float*, cudaStream_t);
+                                                int, const float*, cudaStream_t, int);
 template cudaError_t launch_sweep<float, double>(const DirView<float>&, const DirView<float>&, const double*,
-                                                 float*, int, const float*, cudaStream_t);
+                                                 float*, int, const float*, cudaStream_t, int);
 template cudaError_t launch_scatter<double, double>(const DirView<double>&, const DirView<double>&, const double*,
                                                     double*, bool, cudaStream_t);
 template cudaError_t launch_scatter<float, float>(const DirView<float>&, const DirView<float>&, const float*,

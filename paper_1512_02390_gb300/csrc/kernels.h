@@ -45,9 +45,10 @@ cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, co
 // E[s] = W_s A_ss^{-1} R_s r for every subdomain s (element-blocked m x m).
 // mode: 0 SIMT in T, 1 tensor cores TF32, 2 tensor cores BF16 (T = float).
 // nu_inv (may be null): 1 / nu_bar_s per subdomain (Eq. (subproblem:solution)).
+// spw: tensor-core modes, about spw subdomains per warp (grid size).
 template <typename T, typename TIn>
 cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
-                         const T* nu_inv, cudaStream_t s);
+                         const T* nu_inv, cudaStream_t s, int spw = 1);
 // u = (accum ? u : 0) + sum_s R_s^T E[s]  (deterministic node-centric sum).
 template <typename T, typename TOut>
 cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* E, TOut* u,

@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "sem_schwarz.h"
 #include "setup.h"
+#include "tune_cache.h"
 
 using namespace sem;
 
@@ -52,6 +53,7 @@ struct Level {
   void* f = nullptr;
   void* r = nullptr;
   void* E = nullptr;      // element-blocked Schwarz corrections
+  TuneVal tune{};         // launch shapes (autotuner): fused scatter, MMA sweep grid
 };
 
 }  // namespace
@@ -259,7 +261,7 @@ int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f,
 template <typename T, typename TIn, typename TU>
 int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
-  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, NUI<T>(l), s)));
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, NUI<T>(l), s, l.tune.spw)));
   KL(h, SEM_K_SCATTER, s, (launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
   return SEM_OK;
 }
@@ -300,7 +302,7 @@ template <typename T, typename TF>
 int level_down_fused(sem_handle* h, const Level& l, const TF* f, T* u, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
   T* r = static_cast<T*>(l.r);
-  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TF>(DX<T>(l), DY<T>(l), f, E, h->sweep_mode, NUI<T>(l), s)));
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TF>(DX<T>(l), DY<T>(l), f, E, h->sweep_mode, NUI<T>(l), s, l.tune.spw)));
   return level_apply<T, TF>(h, l, SEM_K_APPLY_MG, nullptr, f, r, 0, nullptr, nullptr, s, E, u);
 }
 
@@ -321,7 +323,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
   for (int l = L; l >= 1; --l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     T* rl = static_cast<T*>(lv[l].r);
-    const bool fuse = h->ns1[l] == 1 && !lv[l].var;
+    const bool fuse = lv[l].tune.fuse && h->ns1[l] == 1 && !lv[l].var;
     if (l == L && !convert_top) {  // right side rtop (FP64)
       if (fuse) {
         if ((rc = level_down_fused<T, double>(h, lv[l], rtop, ul, s))) return rc;
@@ -513,6 +515,117 @@ int check_handle(const sem_handle* h) {
     return fail(SEM_BAD_ARG, "the current CUDA device is not the handle's device");
   }
   return SEM_OK;
+}
+
+// drop the captured solve graph (launch shapes changed): the next solve
+// captures a new one
+void drop_graph(sem_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap2) cudaStreamDestroy(h->cap2);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+  h->cap = h->cap2 = nullptr;
+}
+
+// one down-sweep step of level l from u_l = 0 (one pre-smoothing sweep, then
+// the level residual) with the level's current launch shapes
+template <typename T, typename TF>
+int down_step(sem_handle* h, Level& l, const TF* f, T* u, cudaStream_t s) {
+  if (l.tune.fuse) return level_down_fused<T, TF>(h, l, f, u, s);
+  int rc = sweep<T, TF, T>(h, l, f, u, false, s);
+  if (rc) return rc;
+  return level_apply<T, TF>(h, l, SEM_K_APPLY_MG, u, f, static_cast<T*>(l.r), 0, nullptr, nullptr, s);
+}
+
+// Time every launch-shape candidate of level l on the level's own vectors
+// (best of three batches of ten steps each) and keep the fastest.
+template <typename T, typename TF>
+int tune_level(sem_handle* h, Level& l, const TF* f, bool allow_fuse, cudaStream_t s, cudaEvent_t e0,
+               cudaEvent_t e1) {
+  T* u = static_cast<T*>(l.u);
+  const bool mma = std::is_same<T, float>::value && h->sweep_mode != 0;
+  const int spws[3] = {1, 2, 4};
+  const int nspw = mma ? 3 : 1;
+  TuneVal best;
+  best.us = -1.0;
+  constexpr int kReps = 10;
+  for (int fuse = 0; fuse <= (allow_fuse ? 1 : 0); ++fuse)
+    for (int k = 0; k < nspw; ++k) {
+      l.tune.fuse = fuse;
+      l.tune.spw = spws[k];
+      int rc;
+      for (int w = 0; w < 2; ++w)
+        if ((rc = down_step<T, TF>(h, l, f, u, s))) return rc;
+      double us = -1.0;
+      for (int batch = 0; batch < 3; ++batch) {
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < kReps; ++r)
+          if ((rc = down_step<T, TF>(h, l, f, u, s))) return rc;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double t = 1000.0 * ms / kReps;
+        if (us < 0 || t < us) us = t;
+      }
+      if (best.us < 0 || us < best.us) {
+        best.fuse = fuse;
+        best.spw = spws[k];
+        best.us = us;
+      }
+    }
+  l.tune = best;
+  return SEM_OK;
+}
+
+// tune (or read from the cache) every level l = 1..L of h on stream s
+int autotune(sem_handle* h, const std::string& path, cudaStream_t s) {
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, h->device));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(SEM_CUDA_ERROR, "cudaEventCreate failed");
+  }
+  long long saved[SEM_K_NCLASS];
+  std::memcpy(saved, h->launches, sizeof(saved));
+  const bool prof = h->prof;
+  h->prof = false;
+  int rc = SEM_OK;
+  for (int l = 1; l <= h->L && rc == SEM_OK; ++l) {
+    Level& lv = h->lev[l];
+    const std::string key = tune_key(prop.name, lv.p, lv.n_o, h->cfg.precision, lv.var ? 1 : 0, lv.x64.n, lv.y64.n);
+    TuneVal v;
+    if (!path.empty() && tune_cache_find(path, key, v)) {
+      lv.tune = v;
+      continue;
+    }
+    const bool allow_fuse = h->ns1[l] == 1 && !lv.var;
+    if (!allow_fuse && !(h->mixed && h->sweep_mode != 0)) {
+      lv.tune = TuneVal{};  // a single candidate: nothing to time
+    } else if (!h->mixed) {
+      rc = tune_level<double, double>(h, lv, static_cast<const double*>(lv.f), allow_fuse, s, e0, e1);
+    } else if (l == h->L && !lv.var) {  // the mixed V-cycle reads the FP64 residual here
+      if (cudaMemsetAsync(h->r, 0, h->n * sizeof(double), s) != cudaSuccess) rc = fail(SEM_CUDA_ERROR, "memset");
+      if (!rc) rc = tune_level<float, double>(h, lv, h->r, allow_fuse, s, e0, e1);
+    } else {
+      rc = tune_level<float, float>(h, lv, static_cast<const float*>(lv.f), allow_fuse, s, e0, e1);
+    }
+    if (!rc && !path.empty()) {
+      const std::string err = tune_cache_store(path, key, lv.tune);
+      if (!err.empty()) rc = fail(SEM_BAD_ARG, err);
+    }
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = fail(SEM_CUDA_ERROR, "autotune stream failed");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::memcpy(h->launches, saved, sizeof(saved));
+  h->prof = prof;
+  drop_graph(h);
+  return rc;
 }
 
 }  // namespace
@@ -1098,6 +1211,39 @@ int sem_profile(sem_handle* h, int32_t enable) {
   return SEM_OK;
 }
 
+int sem_autotune(sem_handle* h, const char* cache_path, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  return autotune(h, cache_path ? std::string(cache_path) : std::string(), as_stream(stream));
+}
+
+int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!t) return fail(SEM_BAD_ARG, "null argument");
+  if (level < 1 || level > h->L) return fail(SEM_BAD_ARG, "level must be in 1..log2(p)");
+  const TuneVal& v = h->lev[level].tune;
+  t->fuse = v.fuse;
+  t->spw = v.spw;
+  t->us = v.us;
+  return SEM_OK;
+}
+
+int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!t) return fail(SEM_BAD_ARG, "null argument");
+  if (level < 1 || level > h->L) return fail(SEM_BAD_ARG, "level must be in 1..log2(p)");
+  if (t->fuse < 0 || t->fuse > 1 || t->spw < 1 || t->spw > 64) return fail(SEM_BAD_ARG, "need fuse in {0, 1}, 1 <= spw <= 64");
+  CK(cudaDeviceSynchronize());
+  TuneVal& v = h->lev[level].tune;
+  v.fuse = t->fuse;
+  v.spw = t->spw;
+  v.us = t->us;
+  drop_graph(h);
+  return SEM_OK;
+}
+
 int sem_profile_read(sem_handle* h, double* ms, int64_t* launches) {
   int rc = check_handle(h);
   if (rc) return rc;
@@ -1332,6 +1478,28 @@ int sem_batch_solve(sem_batch* b, double* const* u, const double* const* f, sem_
   int worst = SEM_OK;
   for (int k = 0; k < b->n; ++k) worst = std::max(worst, (int)res[k].status);
   return worst;
+}
+
+int sem_batch_autotune(sem_batch* b, const char* cache_path, void* stream) {
+  if (!b) return fail(SEM_BAD_ARG, "null batch");
+  for (auto& g : b->groups) {
+    int rc = sem_autotune(g.h, cache_path, stream);
+    if (rc) return rc;
+  }
+  // the batch graph holds the old launch shapes: capture a new one next solve
+  CK(cudaDeviceSynchronize());
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->main) cudaStreamDestroy(b->main);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->main = nullptr;
+  for (auto& g : b->groups) {
+    if (g.branch) cudaStreamDestroy(g.branch);
+    if (g.body) cudaStreamDestroy(g.body);
+    g.branch = g.body = nullptr;
+  }
+  return SEM_OK;
 }
 
 int sem_batch_launches(const sem_batch* b, int64_t* launches) {

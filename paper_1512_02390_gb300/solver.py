@@ -53,6 +53,7 @@ class Solver:
         self.h = B.sem_create(self.cfg)
         self.n_unknowns, self.nx_nodes, self.ny_nodes = B.sem_sizes(self.h)
         self.shape = (self.ny_nodes, self.nx_nodes)
+        self.levels = int(self.cfg.p).bit_length() - 1  # L = log2(p)
 
     def close(self):
         if self.h is not None:
@@ -92,6 +93,14 @@ class Solver:
     def profile_read(self):
         return B.sem_profile_read(self.h)
 
+    def autotune(self, cache_path=None, stream=None):
+        """Pick the launch shapes of every level by timing (results unchanged)."""
+        B.sem_autotune(self.h, cache_path, stream)
+        return {l: B.sem_get_tune(self.h, l) for l in range(1, self.levels + 1)}
+
+    def set_tune(self, level, fuse, spw=1):
+        B.sem_set_tune(self.h, level, fuse, spw)
+
 
 class Batch:
     """Many independent problems solved together (sem_batch_*)."""
@@ -117,3 +126,6 @@ class Batch:
 
     def launches(self):
         return B.sem_batch_launches(self.h)
+
+    def autotune(self, cache_path=None, stream=None):
+        B.sem_batch_autotune(self.h, cache_path, stream)
