@@ -4,9 +4,10 @@
 //   (A u)_{ji} = Mg_y[j] * sum_k Lg_x[i, k] u_{jk} + Mg_x[i] * sum_k Lg_y[j, k] u_{ki}
 // where the assembled 1D stiffness row Lg[i, .] is the element row of the
 // element holding i, plus the last row of the left neighbour when i sits on an
-// element interface.  A CTA owns a tile of TE x TE elements (32 x 32 nodes),
-// stages the tile plus one element of halo on the low side in shared memory,
-// and writes every owned node exactly once: no atomics, deterministic.
+// element interface.  A CTA owns a tile of TE x TE elements (32 x 32 nodes,
+// 16 x 16 at P <= 4), stages the tile plus one element of halo on the low side
+// in shared memory, and writes every owned node exactly once: no atomics,
+// deterministic.
 #include <algorithm>
 #include <type_traits>
 
@@ -18,7 +19,7 @@ namespace {
 
 template <int P>
 struct Tile {
-  static constexpr int TE = (P >= 32) ? 1 : 32 / P;  // elements per direction
+  static constexpr int TE = tile_elems(P);           // elements per direction
   static constexpr int TN = TE * P;                  // owned nodes per direction
   static constexpr int LN = TN + P + 1;              // staged nodes per direction
   static constexpr int LP = LN + 1;                  // padded row pitch

@@ -25,7 +25,7 @@ namespace {
 template <int PF>
 struct TT {
   static constexpr int PC = PF / 2;
-  static constexpr int TE = (PF >= 32) ? 1 : 32 / PF;  // elements per tile per direction
+  static constexpr int TE = tile_elems(PF);            // elements per tile per direction
   static constexpr int TNF = TE * PF;
   static constexpr int TNC = TE * PC;
   static constexpr int NPF = PF + 1, NPC = PC + 1;

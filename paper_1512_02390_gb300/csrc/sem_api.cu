@@ -828,8 +828,8 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   if (nb < 1) return fail(SEM_BAD_ARG, "nb must be positive");
   if (nb > 1 && (c.periodic || c.y_edges || c.nu_kind || c.weight == SEM_W_LEARNED))
     return fail(SEM_BAD_ARG, "stacked problems must be uniform Dirichlet Poisson problems");
-  if (nb > 1 && !(c.p >= 32 || c.ny % (32 / c.p) == 0))
-    return fail(SEM_BAD_ARG, "stacked problems need ny divisible by 32/p");
+  if (nb > 1 && c.ny % tile_elems(c.p) != 0)
+    return fail(SEM_BAD_ARG, "stacked problems need ny divisible by the operator tile height");
   if ((long)nb * c.ny > 65536) return fail(SEM_BAD_ARG, "too many stacked problems");
   auto mesh = make_mesh;
   sem_handle* h = new sem_handle();
@@ -1279,9 +1279,9 @@ bool same_group(const sem_config& a, const sem_config& b) {
          a.i_max == b.i_max && a.nu_kind == b.nu_kind && a.nu_a == b.nu_a && a.nu_b == b.nu_b;
 }
 
-// the finest-level operator tiles (32/p elements high) must not straddle two
+// the finest-level operator tiles (tile_elems(p) elements high) must not straddle two
 // stacked problems: their partial sums are per problem
-bool tiles_fit(const sem_config& c) { return c.p >= 32 || c.ny % (32 / c.p) == 0; }
+bool tiles_fit(const sem_config& c) { return c.ny % tile_elems(c.p) == 0; }
 
 bool stackable(const sem_config& c) {
   return !c.periodic && !c.x_edges && !c.y_edges && !c.nu_kind && c.weight != SEM_W_LEARNED && tiles_fit(c);
