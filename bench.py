@@ -331,7 +331,8 @@ def run_ours(args):
         variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
                          "iterations": res.iterations, "status": res.status,
                          "final_rel_residual": res.res / res.res0 if res.res0 else 0.0,
-                         "launch_shapes": {"p%d" % (1 << l): {"fuse": t[0], "spw": t[1], "us": round(t[2], 2)}
+                         "launch_shapes": {"p%d" % (1 << l): {"fuse": t["fuse"], "tc": t["tc"], "spw": t["spw"],
+                                                              "us": round(t["us"], 2)}
                                            for l, t in S.tune.items()}}
         if not is_head:
             variants[key]["class_ms_per_solve"] = {k: round(v[0] / 2, 4) for k, v in vprof.items()}

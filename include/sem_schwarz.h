@@ -226,17 +226,23 @@ int sem_profile(sem_handle* h, int32_t enable);
 int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
 
 /* ---- launch-shape autotuning --------------------------------------------------
- * Not in the paper: two launch choices per level l = 1..log2(p) that change the
- * speed of Alg. 3 but not its arithmetic (the results are bitwise the same):
+ * Not in the paper: launch choices per level l = 1..log2(p) that change the
+ * speed of Alg. 3 (fuse and spw leave the results bitwise the same; tc changes
+ * only the rounding order of the reduced-precision local solves):
  *   fuse  with one pre-smoothing step, the down-sweep of the V-cycle writes the
  *         Schwarz corrections E_s, and ONE residual kernel assembles
  *         u_l = sum_s R_s^T E_s itself (Eq. (correction:global), same order of
  *         summation as the scatter kernel), writes u_l and r_l = f_l - A_l u_l.
  *         Saves a launch and a pass over u_l; costs re-assembly of u_l at the
  *         halos of the residual's tiles (worth it at small p_l only).
- *   spw   reduced-precision tensor-core sweep: subdomains per warp (sets the
- *         grid size; a warp that loops reuses its factor tables).
- * Defaults (no tuning): fuse 0, spw 1.  sem_autotune (sync) times every
+ *   tc    reduced-precision sweep (TF32 / BF16): 1 = on the tcgen05 tensor
+ *         cores, floor(128 / m) subdomains that share their factor tables
+ *         stacked per MMA (available where the stacks are at least half
+ *         full: uniform or one-direction-stretched meshes); 0 = mma.sync with
+ *         one subdomain per warp at a time.
+ *   spw   mma.sync sweep: subdomains per warp (sets the grid size; a warp
+ *         that loops reuses its factor tables).
+ * Defaults (no tuning): fuse 0, tc 1 where available, spw 1.  sem_autotune (sync) times every
  * candidate on the handle's own level vectors (best of 3 x 10 steps, CUDA
  * events) and keeps the fastest; with cache_path != NULL it first looks each
  * level up in that JSON-lines file (key: device name, p_l, n_o, precision,
@@ -245,9 +251,11 @@ int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
  * It overwrites the level work vectors and the MGCG residual (no solve may be
  * in flight on the handle). */
 typedef struct sem_level_tune {
-  int32_t fuse; /* 0 or 1 */
-  int32_t spw;  /* 1..64 */
-  double us;    /* measured time of the level's down-sweep step (microseconds; 0 if not timed) */
+  int32_t fuse;         /* 0 or 1 */
+  int32_t spw;          /* 1..64 */
+  int32_t tc;           /* 0 or 1 */
+  int32_t tc_available; /* sem_get_tune: 1 if the level has tcgen05 stacks (ignored by sem_set_tune) */
+  double us;            /* measured time of the level's down-sweep step (microseconds; 0 if not timed) */
 } sem_level_tune;
 int sem_autotune(sem_handle* h, const char* cache_path, void* stream);
 int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t);

@@ -1,0 +1,404 @@
+// Weighted additive Schwarz sweep on the fifth-generation tensor cores
+// (tcgen05, sm_103a): the fast-diagonalisation local solve of Sec. 3.1,
+// Eq. (FDM), E_s = W_s (S_y (x) S_x) Lambda^{-1} (S_y^T (x) S_x^T) R_s r, for a
+// STACK of subdomains per MMA.
+//
+// Subdomains with the same factor tables (S_x, S_y, Lambda, w; all interior
+// elements of a uniform mesh share them) are grouped G = floor(128 / m) at a
+// time; their m x m windows are stacked into the 128 rows of one accumulator
+// (one TMEM lane per row, one CTA thread per lane).  Every product of the FDM
+// is then a right multiplication of the stack by a shared m x m table:
+//
+//   G1  C1[(s,a)][bh] = sum_b  X_s[a][b]     S_x[b][bh]       (x transform)
+//   G2  C2[(s,bh)][ah] = sum_a C1[(s,a)][bh]  S_y[a][ah]      (y transform; A = per-subdomain transpose of C1)
+//       C2 /= lambda_y[ah] + lambda_x[bh]
+//   G3  C3[(s,bh)][a] = sum_ah C2[(s,bh)][ah] S_y[a][ah]      (inverse y transform; A = C2)
+//   G4  E_s[a][b]     = sum_bh C3[(s,bh)][a]  S_x[b][bh]      (inverse x transform; A = transpose of C3)
+//       E_s[a][b]    *= w_y[a] w_x[b] / nu_bar_s
+//
+// A (the stack) and B (a table) sit in shared memory in the K-major,
+// no-swizzle canonical layout (8-row x 16-byte core matrices; LBO = stride of
+// core matrices along K, SBO = stride of 8-row groups); one elected thread
+// issues tcgen05.mma, tcgen05.commit arrives on an mbarrier, and the 128
+// threads read the accumulator back with tcgen05.ld and write the next A
+// operand.  TF32 (kind::tf32) or BF16 (kind::f16) operands, FP32 accumulation.
+//
+// Every wait on the tensor cores is bounded: a CTA whose wait runs out sets
+// *err, stops issuing, waits (bounded) for what it issued, frees its TMEM and
+// returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace sem {
+
+namespace {
+
+constexpr int kTcThreads = 128;          // one thread per accumulator row / TMEM lane
+constexpr long long kTcWaitCycles = 1LL << 31;  // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
+  return d;
+}
+
+// instruction descriptor: D FP32, A/B TF32 (MODE 1) or BF16 (MODE 2), both
+// K-major, M = 128, N = n
+template <int MODE>
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  const uint32_t fmt = MODE == 1 ? 2u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcThreads >> 4) << 24);
+}
+
+template <int MODE>
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  if (MODE == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// bounded wait for phase `parity` of the mbarrier
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kTcWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Operand geometry of one level (host-computed): N padded to NP (multiple of
+// 16: M = 128 needs N % 16 == 0), K padded to KP (multiple of the K step:
+// 8 for TF32, 16 for BF16), `chunks` 16-byte core-matrix columns along K.
+struct TcLay {
+  int m, G, NP, KP, cols;      // cols: TMEM columns allocated (power of two >= 32)
+  uint32_t lbo, sbo;           // bytes
+  uint32_t a_bytes, b_bytes;   // the stack operand; one table operand
+};
+
+template <int MODE>
+__device__ __forceinline__ uint32_t op_off(int row, int k, const TcLay& L) {
+  constexpr int ES = MODE == 1 ? 4 : 2;
+  return (row & 7) * 16 + (row >> 3) * L.sbo + ((k * ES) & 15) + ((k * ES) >> 4) * L.lbo;
+}
+
+__device__ __forceinline__ uint32_t round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void op_put(unsigned char* base, uint32_t off, float v) {
+  if (MODE == 1) *reinterpret_cast<uint32_t*>(base + off) = round_tf32(v);
+  else *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// this thread's accumulator row, NPC x 16 columns
+template <int NPC>
+__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[NPC * 16]) {
+  float t[16];
+#pragma unroll
+  for (int c = 0; c < NPC; ++c) {
+    tmem_ld16(taddr + c * 16, t);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[c * 16 + i] = t[i];
+  }
+  tmem_wait_ld();
+}
+
+// One block-wide step between operand writes and the next MMA: make the
+// generic-proxy shared-memory writes visible to the tensor cores, order the
+// TMEM reads before the next MMA, and agree on `ok`.
+__device__ __forceinline__ bool tc_sync(bool ok) {
+  fence_async_smem();
+  fence_before();
+  const bool all = __syncthreads_and(ok ? 1 : 0) != 0;
+  fence_after();
+  return all;
+}
+
+// D (TMEM) = A (stack) * B^T (table), K = KP; issued by thread 0
+template <int MODE>
+__device__ __forceinline__ void tc_gemm(uint32_t tmem, uint32_t a, uint32_t b, const TcLay& L, uint32_t bar) {
+  constexpr int KS = MODE == 1 ? 8 : 16;  // 32 bytes of K per instruction = 2 core matrices
+  const uint32_t idesc = tc_idesc<MODE>(L.NP);
+  for (int kb = 0; kb < L.KP / KS; ++kb) {
+    const uint32_t step = (uint32_t)kb * 2u * L.lbo;
+    tc_mma<MODE>(tmem, tc_desc(a + step, L.lbo, L.sbo), tc_desc(b + step, L.lbo, L.sbo), idesc, kb > 0 ? 1u : 0u);
+  }
+  tc_commit(bar);
+}
+
+// NPC = NP / 16: the accumulator row is held in registers (constant indices)
+template <typename TIn, int MODE, int NPC>
+__global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirView<float> dy,
+                                                         const TIn* __restrict__ r, float* __restrict__ E,
+                                                         const float* __restrict__ nu_inv, TcWork wk, TcLay L) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + L.a_bytes;  // tables B1 = S_x^T, B2 = S_y^T, B3 = S_y, B4 = S_x (N x K rows)
+  float* lxs = reinterpret_cast<float*>(sB + 4 * L.b_bytes);
+  float* lys = lxs + 64;
+  float* wxs = lys + 64;
+  float* wys = wxs + 64;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t bar = smem_addr(&mbar);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tbase)),
+                 "r"(L.cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // zero the stack once: padded rows and K columns stay zero for every stage
+  for (int i = t; i < (int)(L.a_bytes / 4); i += kTcThreads) reinterpret_cast<uint32_t*>(sA)[i] = 0u;
+  bool ok = tc_sync(true);
+  const uint32_t tmem = tbase;
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t a_s = smem_addr(sA);
+  const int m = L.m, mm = m * m, G = L.G, NP = NPC * 16, KP = L.KP;
+  const int p = dx.p, no = dx.n_o, Nx = dx.N;
+  const int rows = G * m;
+  // this thread's stack row: subdomain slot s, local index j (a or bh)
+  const int s_me = t / m, j_me = t - s_me * m;
+  const int per = (wk.ngroups + gridDim.x - 1) / gridDim.x;
+  const int g0 = blockIdx.x * per, g1 = min(wk.ngroups, g0 + per);
+  int cur_tx = -1, cur_ty = -1;
+  uint32_t phase = 0;
+  constexpr int NPR = NPC * 16;
+  float v[NPR];
+  for (int g = g0; g < g1 && ok; ++g) {
+    const int* sub = wk.sub + (long)g * G;
+    const int first = sub[0];
+    const int tx = dx.tab[first % dx.n], ty = dy.tab[first / dx.n];
+    if (tx != cur_tx || ty != cur_ty) {
+      // the previous MMAs have completed: the tables may be overwritten
+      const float* Sx = dx.S + (long)tx * mm;
+      const float* Sy = dy.S + (long)ty * mm;
+      for (int idx = t; idx < NP * KP; idx += kTcThreads) {
+        const int n = idx / KP, k = idx - n * KP;
+        const bool in = n < m && k < m;
+        const uint32_t o = op_off<MODE>(n, k, L);
+        op_put<MODE>(sB, o, in ? Sx[k * m + n] : 0.f);
+        op_put<MODE>(sB + L.b_bytes, o, in ? Sy[k * m + n] : 0.f);
+        op_put<MODE>(sB + 2 * L.b_bytes, o, in ? Sy[n * m + k] : 0.f);
+        op_put<MODE>(sB + 3 * L.b_bytes, o, in ? Sx[n * m + k] : 0.f);
+      }
+      for (int i = t; i < 64; i += kTcThreads) {
+        lxs[i] = i < m ? dx.lam[tx * m + i] : 1.f;
+        lys[i] = i < m ? dy.lam[ty * m + i] : 1.f;
+        wxs[i] = i < m ? dx.w[tx * m + i] : 0.f;
+        wys[i] = i < m ? dy.w[ty * m + i] : 0.f;
+      }
+      cur_tx = tx;
+      cur_ty = ty;
+    }
+    // gather R_s r into the stack: row (s, a), column b; consecutive threads
+    // read consecutive nodes of a window row
+    for (int idx = t; idx < rows * m; idx += kTcThreads) {
+      const int row = idx / m, b = idx - row * m;
+      const int s = row / m, a = row - s * m;
+      const int sidx = sub[s];
+      float x = 0.f;
+      if (sidx >= 0) {
+        const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
+        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
+        const int gx = node_or_wall(ex * p + b - no, Nx, dx.periodic, dx.segN);
+        if (gx >= 0 && gy >= 0) x = (float)r[(long)gy * Nx + gx];
+      }
+      op_put<MODE>(sA, op_off<MODE>(row, b, L), x);
+    }
+    ok = tc_sync(ok);
+    if (!ok) break;
+    // G1: C1 = X S_x
+    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB), L, bar);
+    ok = tc_wait(bar, phase);
+    phase ^= 1u;
+    fence_after();
+    if (ok) {
+      tmem_row<NPC>(taddr, v);
+      // A2[(s, bh)][a] = C1[(s, a)][bh]
+      if (t < rows) {
+#pragma unroll
+        for (int bh = 0; bh < NPR; ++bh)
+          if (bh < m) op_put<MODE>(sA, op_off<MODE>(s_me * m + bh, j_me, L), v[bh]);
+      }
+    }
+    ok = tc_sync(ok);
+    if (!ok) break;
+    // G2: C2 = A2 S_y, then / (lambda_y + lambda_x)
+    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + L.b_bytes), L, bar);
+    ok = tc_wait(bar, phase);
+    phase ^= 1u;
+    fence_after();
+    if (ok) {
+      tmem_row<NPC>(taddr, v);
+      if (t < rows) {
+        const float lx = lxs[j_me];
+#pragma unroll
+        for (int ah = 0; ah < NPR; ++ah)
+          if (ah < m) op_put<MODE>(sA, op_off<MODE>(t, ah, L), v[ah] / (lys[ah] + lx));
+      }
+    }
+    ok = tc_sync(ok);
+    if (!ok) break;
+    // G3: C3 = C2 S_y^T
+    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + 2 * L.b_bytes), L, bar);
+    ok = tc_wait(bar, phase);
+    phase ^= 1u;
+    fence_after();
+    if (ok) {
+      tmem_row<NPC>(taddr, v);
+      // A4[(s, a)][bh] = C3[(s, bh)][a]
+      if (t < rows) {
+#pragma unroll
+        for (int a = 0; a < NPR; ++a)
+          if (a < m) op_put<MODE>(sA, op_off<MODE>(s_me * m + a, j_me, L), v[a]);
+      }
+    }
+    ok = tc_sync(ok);
+    if (!ok) break;
+    // G4: E = A4 S_x^T, weighted
+    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + 3 * L.b_bytes), L, bar);
+    ok = tc_wait(bar, phase);
+    phase ^= 1u;
+    fence_after();
+    if (ok) {
+      tmem_row<NPC>(taddr, v);
+      const int sidx = t < rows ? sub[s_me] : -1;
+      if (sidx >= 0) {
+        const float sc = nu_inv ? nu_inv[sidx] : 1.f;
+        const float wy = wys[j_me];
+        float* Es = E + (long)sidx * mm + j_me * m;
+#pragma unroll
+        for (int b = 0; b < NPR; ++b)
+          if (b < m) Es[b] = wy * wxs[b] * v[b] * sc;
+      }
+    }
+    ok = tc_sync(ok);
+  }
+  if (!ok) {
+    if (t == 0) atomicExch(wk.err, 1);
+    // let a commit still in flight land before the accumulator is freed
+    tc_wait(bar, phase);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.cols));
+  }
+}
+
+template <int MODE>
+TcLay tc_layout(int m) {
+  TcLay L{};
+  constexpr int ES = MODE == 1 ? 4 : 2, KS = MODE == 1 ? 8 : 16;
+  L.m = m;
+  L.G = kTcThreads / m;
+  L.NP = (m + 15) / 16 * 16;
+  L.KP = (m + KS - 1) / KS * KS;
+  L.cols = L.NP <= 32 ? 32 : 64;
+  const int chunks = L.KP * ES / 16;
+  // core matrices 144 bytes apart along K (a 16-byte gap): the transposing
+  // writes of consecutive K then fall in distinct banks
+  L.lbo = 144;
+  L.sbo = (uint32_t)chunks * L.lbo;
+  L.a_bytes = (kTcThreads / 8) * L.sbo;
+  L.b_bytes = (uint32_t)(L.NP / 8) * L.sbo;
+  return L;
+}
+
+template <typename TIn, int MODE, int NPC>
+cudaError_t sweep_tc_launch(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E,
+                            const float* nu_inv, const TcWork& wk, const TcLay& L, cudaStream_t s) {
+  const size_t sm = L.a_bytes + 4 * (size_t)L.b_bytes + 4 * 64 * sizeof(float);
+  // TMEM: at most 512 / cols CTAs of this kernel may be resident on one SM
+  const size_t sm_min = (size_t)(228 * 1024) / (512 / L.cols) + 1;
+  const size_t smem = std::max(sm, L.cols > 32 ? sm_min : sm);
+  cudaError_t e = allow_smem(k_sweep_tc<TIn, MODE, NPC>, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(wk.ngroups, 152 * 8);
+  k_sweep_tc<TIn, MODE, NPC><<<grid, kTcThreads, smem, s>>>(dx, dy, r, E, nu_inv, wk, L);
+  return cudaGetLastError();
+}
+
+template <typename TIn, int MODE>
+cudaError_t sweep_tc_mode(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E,
+                          const float* nu_inv, const TcWork& wk, cudaStream_t s) {
+  if (dx.m != dy.m || dx.m > 64 || dx.m < 2 || wk.G != kTcThreads / dx.m || wk.ngroups <= 0 || !wk.sub || !wk.err)
+    return cudaErrorInvalidValue;
+  const TcLay L = tc_layout<MODE>(dx.m);
+  switch (L.NP / 16) {
+    case 1: return sweep_tc_launch<TIn, MODE, 1>(dx, dy, r, E, nu_inv, wk, L, s);
+    case 2: return sweep_tc_launch<TIn, MODE, 2>(dx, dy, r, E, nu_inv, wk, L, s);
+    case 3: return sweep_tc_launch<TIn, MODE, 3>(dx, dy, r, E, nu_inv, wk, L, s);
+    default: return sweep_tc_launch<TIn, MODE, 4>(dx, dy, r, E, nu_inv, wk, L, s);
+  }
+}
+
+}  // namespace
+
+template <typename TIn>
+cudaError_t launch_sweep_tc(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E, int mode,
+                            const float* nu_inv, const TcWork& wk, cudaStream_t s) {
+  if (mode == 1) return sweep_tc_mode<TIn, 1>(dx, dy, r, E, nu_inv, wk, s);
+  if (mode == 2) return sweep_tc_mode<TIn, 2>(dx, dy, r, E, nu_inv, wk, s);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_sweep_tc<float>(const DirView<float>&, const DirView<float>&, const float*, float*, int,
+                                            const float*, const TcWork&, cudaStream_t);
+template cudaError_t launch_sweep_tc<double>(const DirView<float>&, const DirView<float>&, const double*, float*,
+                                             int, const float*, const TcWork&, cudaStream_t);
+
+}  // namespace sem

@@ -53,6 +53,19 @@ cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, co
 template <typename T, typename TIn>
 cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* r, T* E, int mode,
                          const T* nu_inv, cudaStream_t s, int spw = 1);
+// Work list of the tensor-core (tcgen05) sweep of one level: groups of up to
+// G = floor(128 / m) subdomains sharing their factor tables (same table id in
+// x and in y); every group's first slot is used.
+struct TcWork {
+  const int* sub = nullptr;  // ngroups x G subdomain indices ey * n_x + ex (-1: empty slot)
+  int ngroups = 0, G = 0;
+  int* err = nullptr;        // set to 1 by a CTA whose wait on the tensor cores ran out
+};
+// The sweep of launch_sweep (mode 1 TF32, 2 BF16) with stacks of G subdomains
+// per tcgen05 MMA (k_sweep_tc.cu).
+template <typename TIn>
+cudaError_t launch_sweep_tc(const DirView<float>& dx, const DirView<float>& dy, const TIn* r, float* E, int mode,
+                            const float* nu_inv, const TcWork& wk, cudaStream_t s);
 // u = (accum ? u : 0) + sum_s R_s^T E[s]  (deterministic node-centric sum).
 template <typename T, typename TOut>
 cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* E, TOut* u,

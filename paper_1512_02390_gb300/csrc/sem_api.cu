@@ -9,6 +9,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <map>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -53,7 +54,8 @@ struct Level {
   void* f = nullptr;
   void* r = nullptr;
   void* E = nullptr;      // element-blocked Schwarz corrections
-  TuneVal tune{};         // launch shapes (autotuner): fused scatter, MMA sweep grid
+  TuneVal tune{};         // launch shapes (autotuner): fused scatter, sweep kernel and grid
+  TcWork tc{};            // stacks of the tcgen05 sweep (ngroups == 0: not available)
 };
 
 }  // namespace
@@ -79,6 +81,7 @@ struct sem_handle {
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *r_old = nullptr;
   double* fi = nullptr;  // right side of the running MGCG solve (internal copy)
   double* Binv = nullptr;  // dense FP64 inverse of B_0(nu) (variable diffusivity)
+  int* tc_err = nullptr;   // device flag: a tcgen05 sweep gave up waiting
   // the whole MGCG solve as one CUDA graph: prologue + WHILE node over one iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -257,11 +260,27 @@ int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f,
   return SEM_OK;
 }
 
+// E_s = W_s A_ss^{-1} R_s r for every subdomain of level l: tcgen05 stacks or
+// one subdomain per warp / CTA, as the level is tuned
+template <typename T, typename TIn>
+int level_sweep(sem_handle* h, const Level& l, const TIn* r, T* E, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (l.tune.tc && l.tc.ngroups > 0 && h->sweep_mode != 0) {
+      KL(h, SEM_K_SWEEP, s,
+         (launch_sweep_tc<TIn>(DX<float>(l), DY<float>(l), r, E, h->sweep_mode, NUI<float>(l), l.tc, s)));
+      return SEM_OK;
+    }
+  }
+  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, NUI<T>(l), s, l.tune.spw)));
+  return SEM_OK;
+}
+
 // u = (accum ? u : 0) + sum_s R_s^T W A_ss^{-1} R_s r  (one additive sweep on r)
 template <typename T, typename TIn, typename TU>
 int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
-  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TIn>(DX<T>(l), DY<T>(l), r, E, h->sweep_mode, NUI<T>(l), s, l.tune.spw)));
+  int rc = level_sweep<T, TIn>(h, l, r, E, s);
+  if (rc) return rc;
   KL(h, SEM_K_SCATTER, s, (launch_scatter<T, TU>(DX<T>(l), DY<T>(l), E, u, accum, s)));
   return SEM_OK;
 }
@@ -302,7 +321,8 @@ template <typename T, typename TF>
 int level_down_fused(sem_handle* h, const Level& l, const TF* f, T* u, cudaStream_t s) {
   T* E = static_cast<T*>(l.E);
   T* r = static_cast<T*>(l.r);
-  KL(h, SEM_K_SWEEP, s, (launch_sweep<T, TF>(DX<T>(l), DY<T>(l), f, E, h->sweep_mode, NUI<T>(l), s, l.tune.spw)));
+  int rc = level_sweep<T, TF>(h, l, f, E, s);
+  if (rc) return rc;
   return level_apply<T, TF>(h, l, SEM_K_APPLY_MG, nullptr, f, r, 0, nullptr, nullptr, s, E, u);
 }
 
@@ -500,6 +520,16 @@ int build_graph(sem_handle* h) {
   return SEM_OK;
 }
 
+// read and clear the tcgen05 give-up flag (sync)
+int take_tc_err(sem_handle* h, cudaStream_t s, bool& hit) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  hit = e != 0;
+  if (hit) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+  return SEM_OK;
+}
+
 // host copy of the number of problems still iterating
 int sync_flags(sem_handle* h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h->flags_host, h->st.active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -546,15 +576,21 @@ int tune_level(sem_handle* h, Level& l, const TF* f, bool allow_fuse, cudaStream
                cudaEvent_t e1) {
   T* u = static_cast<T*>(l.u);
   const bool mma = std::is_same<T, float>::value && h->sweep_mode != 0;
-  const int spws[3] = {1, 2, 4};
-  const int nspw = mma ? 3 : 1;
+  // sweep kernels: (tc, spw) = tcgen05 stacks, or mma.sync with 1, 2, 4 subdomains per warp
+  std::vector<std::pair<int, int>> kern = {{0, 1}};
+  if (mma) {
+    kern.push_back({0, 2});
+    kern.push_back({0, 4});
+    if (l.tc.ngroups > 0) kern.push_back({1, 1});
+  }
   TuneVal best;
   best.us = -1.0;
   constexpr int kReps = 10;
   for (int fuse = 0; fuse <= (allow_fuse ? 1 : 0); ++fuse)
-    for (int k = 0; k < nspw; ++k) {
+    for (const auto& kc : kern) {
       l.tune.fuse = fuse;
-      l.tune.spw = spws[k];
+      l.tune.tc = kc.first;
+      l.tune.spw = kc.second;
       int rc;
       for (int w = 0; w < 2; ++w)
         if ((rc = down_step<T, TF>(h, l, f, u, s))) return rc;
@@ -570,11 +606,7 @@ int tune_level(sem_handle* h, Level& l, const TF* f, bool allow_fuse, cudaStream
         const double t = 1000.0 * ms / kReps;
         if (us < 0 || t < us) us = t;
       }
-      if (best.us < 0 || us < best.us) {
-        best.fuse = fuse;
-        best.spw = spws[k];
-        best.us = us;
-      }
+      if (best.us < 0 || us < best.us) best = l.tune, best.us = us;
     }
   l.tune = best;
   return SEM_OK;
@@ -599,7 +631,7 @@ int autotune(sem_handle* h, const std::string& path, cudaStream_t s) {
     Level& lv = h->lev[l];
     const std::string key = tune_key(prop.name, lv.p, lv.n_o, h->cfg.precision, lv.var ? 1 : 0, lv.x64.n, lv.y64.n);
     TuneVal v;
-    if (!path.empty() && tune_cache_find(path, key, v)) {
+    if (!path.empty() && tune_cache_find(path, key, v) && !(v.tc && lv.tc.ngroups == 0)) {
       lv.tune = v;
       continue;
     }
@@ -819,6 +851,34 @@ int sem_learned_features(const sem_config* cfg, float* feat_x, float* feat_y) {
 
 // A handle for nb copies of the problem cfg stacked along y (nb = 1: one
 // problem).  Stacked copies share every table; walls separate them.
+// Stacks of the tcgen05 sweep of one level: subdomains grouped by their pair of
+// table ids, G = floor(128 / m) per stack, in row-major order within a pair.
+// Left unbuilt (the level keeps the per-subdomain kernels) when the stacks
+// would be less than half full, e.g. on meshes stretched in both directions.
+static int build_tc_work(sem_handle* h, const Dir1D& dx, const Dir1D& dy, Level& lv) {
+  if (lv.m < 2 || lv.m > 64) return SEM_OK;
+  const int G = 128 / lv.m;
+  std::map<std::pair<int, int>, std::vector<int>> cls;
+  for (int ey = 0; ey < dy.n; ++ey)
+    for (int ex = 0; ex < dx.n; ++ex) cls[{dx.tab[ex], dy.tab[ey]}].push_back(ey * dx.n + ex);
+  std::vector<int> sub;
+  long members = 0;
+  int ng = 0;
+  for (const auto& kv : cls) {
+    const auto& v = kv.second;
+    for (size_t i = 0; i < v.size(); i += G, ++ng)
+      for (int k = 0; k < G; ++k) sub.push_back(i + k < v.size() ? v[i + k] : -1);
+    members += (long)v.size();
+  }
+  if (2 * members < (long)ng * G) return SEM_OK;
+  int* d = nullptr;
+  int rc = upload(h, &d, sub);
+  if (rc) return rc;
+  lv.tc = TcWork{d, ng, G, h->tc_err};
+  lv.tune.tc = 1;
+  return SEM_OK;
+}
+
 static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   int L = 0;
   {
@@ -865,6 +925,8 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     return code;
   };
   const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
+  if ((rc = dev_alloc(h, &h->tc_err, 1))) return bail(rc);
+  CK(cudaMemset(h->tc_err, 0, sizeof(int)));
   h->lev.resize(L + 1);
   for (int l = 0; l <= L; ++l) {
     Level& lv = h->lev[l];
@@ -887,6 +949,7 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
         (rc = upload_dir(h, dy, lv.y32)))
       return bail(rc);
     if (nb > 1) lv.y64.segN = lv.y32.segN = c.ny * lv.p;
+    if (l > 0 && h->sweep_mode != 0 && (rc = build_tc_work(h, dx, dy, lv))) return bail(rc);
     if (l > 0) {
       std::vector<double> J;
       interp_matrix(lv.p, lv.p / 2, J);
@@ -1119,6 +1182,9 @@ int sem_mg_solve(sem_handle* h, double* u, const double* f, sem_result* res, dou
     if (!std::isfinite(rn)) status = SEM_BREAKDOWN;
     else if (rn <= h->cfg.tol * r0) status = SEM_OK;
   }
+  bool timeout = false;
+  if ((rc = take_tc_err(h, s, timeout))) return rc;
+  if (timeout) status = SEM_TIMEOUT;
   res->iterations = it;
   res->status = status;
   res->res0 = r0;
@@ -1159,6 +1225,9 @@ static int collect(sem_handle* h, cudaStream_t s, bool graph_used, sem_result* r
   std::vector<double> rr((size_t)nb * stride);
   CK(cudaMemcpyAsync(rr.data(), h->st.rr, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  bool timeout = false;
+  int rc0 = take_tc_err(h, s, timeout);
+  if (rc0) return rc0;
   int itmax = 0;
   for (int k = 0; k < nb; ++k) {
     const int it = fl[2 * nb + k];
@@ -1169,6 +1238,7 @@ static int collect(sem_handle* h, cudaStream_t s, bool graph_used, sem_result* r
     res[k].res0 = std::sqrt(r[0]);
     res[k].res = std::sqrt(r[it]);
     res[k].rbar = (it > 0 && r[it] > 0) ? std::log10(std::sqrt(r[0] / r[it])) / it : 0.0;
+    if (timeout) res[k].status = SEM_TIMEOUT;
     if (hist && hist[k])
       for (int i = 0; i <= it && i < hlen; ++i) hist[k][i] = std::sqrt(r[i]);
   }
@@ -1225,6 +1295,8 @@ int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t) {
   const TuneVal& v = h->lev[level].tune;
   t->fuse = v.fuse;
   t->spw = v.spw;
+  t->tc = v.tc;
+  t->tc_available = h->lev[level].tc.ngroups > 0;
   t->us = v.us;
   return SEM_OK;
 }
@@ -1234,11 +1306,14 @@ int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t) {
   if (rc) return rc;
   if (!t) return fail(SEM_BAD_ARG, "null argument");
   if (level < 1 || level > h->L) return fail(SEM_BAD_ARG, "level must be in 1..log2(p)");
-  if (t->fuse < 0 || t->fuse > 1 || t->spw < 1 || t->spw > 64) return fail(SEM_BAD_ARG, "need fuse in {0, 1}, 1 <= spw <= 64");
+  if (t->fuse < 0 || t->fuse > 1 || t->spw < 1 || t->spw > 64 || t->tc < 0 || t->tc > 1)
+    return fail(SEM_BAD_ARG, "need fuse, tc in {0, 1}, 1 <= spw <= 64");
+  if (t->tc && h->lev[level].tc.ngroups == 0) return fail(SEM_BAD_ARG, "no tcgen05 sweep on this level");
   CK(cudaDeviceSynchronize());
   TuneVal& v = h->lev[level].tune;
   v.fuse = t->fuse;
   v.spw = t->spw;
+  v.tc = t->tc;
   v.us = t->us;
   drop_graph(h);
   return SEM_OK;

@@ -250,6 +250,14 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o, 
   std::map<std::tuple<int, int, double, double, double, double, double, double, double>, int> seen;
   o.tab.assign(n, 0);
   o.tables.clear();
+  // widths equal up to rounding (edges e * l / n) count as equal geometry
+  std::vector<double> widths;
+  auto canon = [&widths](double h) {
+    for (double c : widths)
+      if (std::fabs(h - c) <= 1e-12 * c) return c;
+    widths.push_back(h);
+    return h;
+  };
   for (int e = 0; e < n; ++e) {
     int L = mesh.neighbour(e, -1), R = mesh.neighbour(e, +1);
     double hl = L >= 0 ? mesh.h(L) : 0.0, hr = R >= 0 ? mesh.h(R) : 0.0, he = mesh.h(e);
@@ -265,7 +273,8 @@ std::string build_dir(const Mesh1D& mesh, int p, int n_o, int weight, Dir1D& o, 
       sr = learned[2 * ir];
       kr = learned[2 * ir + 1];
     }
-    auto key = std::make_tuple(L >= 0 ? 1 : 0, R >= 0 ? 1 : 0, hl, he, hr, sl, kl, sr, kr);
+    auto key = std::make_tuple(L >= 0 ? 1 : 0, R >= 0 ? 1 : 0, L >= 0 ? canon(hl) : 0.0, canon(he),
+                               R >= 0 ? canon(hr) : 0.0, sl, kl, sr, kr);
     if (weight != 101) {
       auto it = seen.find(key);
       if (it != seen.end()) { o.tab[e] = it->second; continue; }

@@ -98,8 +98,11 @@ class Solver:
         B.sem_autotune(self.h, cache_path, stream)
         return {l: B.sem_get_tune(self.h, l) for l in range(1, self.levels + 1)}
 
-    def set_tune(self, level, fuse, spw=1):
-        B.sem_set_tune(self.h, level, fuse, spw)
+    def set_tune(self, level, fuse, spw=1, tc=0):
+        B.sem_set_tune(self.h, level, fuse, spw, tc)
+
+    def get_tune(self, level):
+        return B.sem_get_tune(self.h, level)
 
 
 class Batch:

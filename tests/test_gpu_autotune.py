@@ -1,9 +1,10 @@
-"""Launch-shape tuning changes how the V-cycle is launched, never what it
+"""Launch-shape tuning changes how the V-cycle is launched, not what it
 computes: with the scatter fused into the level residual and any number of
-subdomains per warp in the tensor-core sweep, MGCG must take the same
-iterations and return the bitwise-identical solution, on the first solve
-(launch by launch) and on the replayed graph; the autotuner's JSON-lines cache
-must round-trip."""
+subdomains per warp in the mma.sync sweep, MGCG must take the same iterations
+and return the bitwise-identical solution, on the first solve (launch by
+launch) and on the replayed graph.  The tcgen05 sweep rounds its products in
+another order: the same solve to 1e-8 and +-1 iteration.  The autotuner's
+JSON-lines cache must round-trip."""
 import json
 
 import numpy as np
@@ -50,16 +51,27 @@ CASES = [dict(nx=16, ny=16, p=16, overlap=2, precision="tf32"),
 def test_tuned_shapes_give_identical_solves(cfg):
     S = P.Solver(**cfg)
     b = _rhs(S, 71)
-    ref = _solves(S, b)
-    assert ref[0][1] == P.SEM_OK
-    assert np.array_equal(ref[0][2], ref[1][2])
-    for fuse, spw in [(1, 1), (1, 2), (0, 4)]:
+    avail = [l for l in range(1, S.levels + 1) if S.get_tune(l)["tc_available"]]
+    for tc in (0, 1):
+        if tc and not avail:
+            continue
         for l in range(1, S.levels + 1):
-            S.set_tune(l, fuse, spw)
-        got = _solves(S, b)
-        for it, st, u in got:
-            assert (it, st) == ref[0][:2], (fuse, spw)
-            assert np.array_equal(u, ref[0][2]), (fuse, spw, np.max(np.abs(u - ref[0][2])))
+            S.set_tune(l, 0, 1, tc if l in avail else 0)
+        ref = _solves(S, b)
+        assert ref[0][1] == P.SEM_OK
+        assert np.array_equal(ref[0][2], ref[1][2])
+        for fuse, spw in [(1, 1), (1, 2), (0, 4)]:
+            for l in range(1, S.levels + 1):
+                S.set_tune(l, fuse, spw, tc if l in avail else 0)
+            for it, st, u in _solves(S, b):
+                assert (it, st) == ref[0][:2], (tc, fuse, spw)
+                assert np.array_equal(u, ref[0][2]), (tc, fuse, spw, np.max(np.abs(u - ref[0][2])))
+        if tc == 0:
+            ref0 = ref
+    if avail:  # tcgen05 and mma.sync sweeps round in another order: same solve to the tolerance
+        it0, it1 = ref0[0][0], ref[0][0]
+        assert abs(it0 - it1) <= 1
+        assert np.abs(ref[0][2] - ref0[0][2]).max() <= 1e-8 * np.abs(ref0[0][2]).max()
 
 
 def test_autotune_cache_roundtrip(tmp_path):
@@ -67,25 +79,30 @@ def test_autotune_cache_roundtrip(tmp_path):
     path = str(tmp_path / "tune.jsonl")
     S = P.Solver(**cfg)
     b = _rhs(S, 72)
-    ref = _solves(S, b)
     tuned = S.autotune(path)
     assert set(tuned) == set(range(1, S.levels + 1))
-    for fuse, spw, us in tuned.values():
-        assert fuse in (0, 1) and spw in (1, 2, 4) and us > 0
+    for t in tuned.values():
+        assert t["fuse"] in (0, 1) and t["spw"] in (1, 2, 4) and t["tc"] in (0, 1) and t["us"] > 0
+        assert t["tc"] <= t["tc_available"]
     lines = [json.loads(l) for l in open(path).read().splitlines()]
     assert len(lines) == S.levels
     assert len({d["key"] for d in lines}) == S.levels
-    got = _solves(S, b)
-    for it, st, u in got:
-        assert (it, st) == ref[0][:2]
+    ref = _solves(S, b)
+    for it, st, u in ref:
+        assert st == P.SEM_OK
         assert np.array_equal(u, ref[0][2])
-    # a second handle of the same shape reads the cache instead of timing
+    # a second handle of the same shape reads the cache instead of timing, and
+    # solves bitwise the same with the same launch shapes
     S2 = P.Solver(**cfg)
     again = S2.autotune(path)
     for l in tuned:
-        assert again[l][:2] == tuned[l][:2]
-        assert abs(again[l][2] - round(tuned[l][2], 3)) < 1e-9
+        for k in ("fuse", "spw", "tc"):
+            assert again[l][k] == tuned[l][k]
+        assert abs(again[l]["us"] - round(tuned[l]["us"], 3)) < 1e-9
     assert len(open(path).read().splitlines()) == S.levels
+    for it, st, u in _solves(S2, b):
+        assert (it, st) == ref[0][:2]
+        assert np.array_equal(u, ref[0][2])
 
 
 def test_set_tune_rejects_bad_values():
@@ -98,6 +115,8 @@ def test_set_tune_rejects_bad_values():
         S.set_tune(1, 2, 1)
     with pytest.raises(P.SemError):
         S.set_tune(1, 0, 0)
+    with pytest.raises(P.SemError):  # FP64: no tensor-core sweep
+        S.set_tune(1, 0, 1, tc=1)
 
 
 def test_batch_autotune_keeps_results(tmp_path):
@@ -112,10 +131,16 @@ def test_batch_autotune_keeps_results(tmp_path):
         res = batch.solve(us, bs)
         first.append(([r.iterations for r in res], [u.cpu().numpy() for u in us]))
     batch.autotune(str(tmp_path / "tune.jsonl"))
+    got = []
     for rep in range(2):  # the first replays a newly captured graph
         us = [torch.zeros_like(b) for b in bs]
         res = batch.solve(us, bs)
         assert [r.status for r in res] == [P.SEM_OK] * len(cfgs)
-        assert [r.iterations for r in res] == first[1][0]
-        for k, u in enumerate(us):
-            assert np.array_equal(u.cpu().numpy(), first[1][1][k]), k
+        got.append(([r.iterations for r in res], [u.cpu().numpy() for u in us]))
+        for k, u in enumerate(got[-1][1]):
+            want = first[1][1][k]
+            assert abs(got[-1][0][k] - first[1][0][k]) <= 1, k
+            assert np.abs(u - want).max() <= 1e-8 * np.abs(want).max(), k
+    assert got[0][0] == got[1][0]
+    for a, b in zip(got[0][1], got[1][1]):
+        assert np.array_equal(a, b)
