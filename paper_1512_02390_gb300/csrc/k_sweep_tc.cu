@@ -120,10 +120,20 @@ struct TcLay {
   uint32_t a_bytes, b_bytes;   // the stack operand; one table operand
 };
 
+// core matrices 144 bytes apart along K (a 16-byte gap): writes of
+// consecutive K by consecutive threads then fall in distinct banks
+constexpr uint32_t kLbo = 144;
+
+// byte offset of stack / table row `row` and of column k within a row
+__device__ __forceinline__ uint32_t row_off(int row, uint32_t sbo) { return (row & 7) * 16 + (row >> 3) * sbo; }
+template <int MODE>
+__device__ __forceinline__ uint32_t k_off(int k) {
+  constexpr int ES = MODE == 1 ? 4 : 2;
+  return ((k * ES) & 15) + ((k * ES) >> 4) * kLbo;
+}
 template <int MODE>
 __device__ __forceinline__ uint32_t op_off(int row, int k, const TcLay& L) {
-  constexpr int ES = MODE == 1 ? 4 : 2;
-  return (row & 7) * 16 + (row >> 3) * L.sbo + ((k * ES) & 15) + ((k * ES) >> 4) * L.lbo;
+  return row_off(row, L.sbo) + k_off<MODE>(k);
 }
 
 __device__ __forceinline__ uint32_t round_tf32(float x) {
@@ -136,19 +146,6 @@ template <int MODE>
 __device__ __forceinline__ void op_put(unsigned char* base, uint32_t off, float v) {
   if (MODE == 1) *reinterpret_cast<uint32_t*>(base + off) = round_tf32(v);
   else *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
-}
-
-// this thread's accumulator row, NPC x 16 columns
-template <int NPC>
-__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[NPC * 16]) {
-  float t[16];
-#pragma unroll
-  for (int c = 0; c < NPC; ++c) {
-    tmem_ld16(taddr + c * 16, t);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[c * 16 + i] = t[i];
-  }
-  tmem_wait_ld();
 }
 
 // One block-wide step between operand writes and the next MMA: make the
@@ -188,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
   float* wys = wxs + 64;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t bar = smem_addr(&mbar);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
@@ -214,8 +211,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
   const int g0 = blockIdx.x * per, g1 = min(wk.ngroups, g0 + per);
   int cur_tx = -1, cur_ty = -1;
   uint32_t phase = 0;
-  constexpr int NPR = NPC * 16;
-  float v[NPR];
+  float v[16];  // accumulator columns are read 16 at a time
   for (int g = g0; g < g1 && ok; ++g) {
     const int* sub = wk.sub + (long)g * G;
     const int first = sub[0];
@@ -242,20 +238,26 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
       cur_tx = tx;
       cur_ty = ty;
     }
-    // gather R_s r into the stack: row (s, a), column b; consecutive threads
-    // read consecutive nodes of a window row
-    for (int idx = t; idx < rows * m; idx += kTcThreads) {
-      const int row = idx / m, b = idx - row * m;
+    // gather R_s r into the stack: warp w takes window rows w, w + 4, ...;
+    // lane b reads node b of the row (consecutive lanes, consecutive nodes)
+    for (int row = warp; row < rows; row += kTcThreads / 32) {
       const int s = row / m, a = row - s * m;
       const int sidx = sub[s];
-      float x = 0.f;
+      const uint32_t ro = row_off(row, L.sbo);
+      int ey = 0, ex = 0, gy = -1;
       if (sidx >= 0) {
-        const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
-        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
-        const int gx = node_or_wall(ex * p + b - no, Nx, dx.periodic, dx.segN);
-        if (gx >= 0 && gy >= 0) x = (float)r[(long)gy * Nx + gx];
+        ey = sidx / dx.n;
+        ex = sidx - ey * dx.n;
+        gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
       }
-      op_put<MODE>(sA, op_off<MODE>(row, b, L), x);
+      for (int b = lane; b < m; b += 32) {
+        float x = 0.f;
+        if (gy >= 0) {
+          const int gx = node_or_wall(ex * p + b - no, Nx, dx.periodic, dx.segN);
+          if (gx >= 0) x = (float)r[(long)gy * Nx + gx];
+        }
+        op_put<MODE>(sA, ro + k_off<MODE>(b), x);
+      }
     }
     ok = tc_sync(ok);
     if (!ok) break;
@@ -265,12 +267,17 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     phase ^= 1u;
     fence_after();
     if (ok) {
-      tmem_row<NPC>(taddr, v);
       // A2[(s, bh)][a] = C1[(s, a)][bh]
-      if (t < rows) {
+      const uint32_t ko = k_off<MODE>(j_me);
 #pragma unroll
-        for (int bh = 0; bh < NPR; ++bh)
-          if (bh < m) op_put<MODE>(sA, op_off<MODE>(s_me * m + bh, j_me, L), v[bh]);
+      for (int c = 0; c < NPC; ++c) {
+        tmem_ld16(taddr + c * 16, v);
+        tmem_wait_ld();
+        if (t < rows) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c * 16 + i < m) op_put<MODE>(sA, row_off(s_me * m + c * 16 + i, L.sbo) + ko, v[i]);
+        }
       }
     }
     ok = tc_sync(ok);
@@ -281,12 +288,19 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     phase ^= 1u;
     fence_after();
     if (ok) {
-      tmem_row<NPC>(taddr, v);
-      if (t < rows) {
-        const float lx = lxs[j_me];
+      const float lx = lxs[j_me];
+      unsigned char* ro = sA + row_off(t, L.sbo);
 #pragma unroll
-        for (int ah = 0; ah < NPR; ++ah)
-          if (ah < m) op_put<MODE>(sA, op_off<MODE>(t, ah, L), v[ah] / (lys[ah] + lx));
+      for (int c = 0; c < NPC; ++c) {
+        tmem_ld16(taddr + c * 16, v);
+        tmem_wait_ld();
+        if (t < rows) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int ah = c * 16 + i;
+            if (ah < m) op_put<MODE>(ro, k_off<MODE>(ah), __fdividef(v[i], lys[ah] + lx));
+          }
+        }
       }
     }
     ok = tc_sync(ok);
@@ -297,12 +311,17 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     phase ^= 1u;
     fence_after();
     if (ok) {
-      tmem_row<NPC>(taddr, v);
       // A4[(s, a)][bh] = C3[(s, bh)][a]
-      if (t < rows) {
+      const uint32_t ko = k_off<MODE>(j_me);
 #pragma unroll
-        for (int a = 0; a < NPR; ++a)
-          if (a < m) op_put<MODE>(sA, op_off<MODE>(s_me * m + a, j_me, L), v[a]);
+      for (int c = 0; c < NPC; ++c) {
+        tmem_ld16(taddr + c * 16, v);
+        tmem_wait_ld();
+        if (t < rows) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c * 16 + i < m) op_put<MODE>(sA, row_off(s_me * m + c * 16 + i, L.sbo) + ko, v[i]);
+        }
       }
     }
     ok = tc_sync(ok);
@@ -313,15 +332,21 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     phase ^= 1u;
     fence_after();
     if (ok) {
-      tmem_row<NPC>(taddr, v);
       const int sidx = t < rows ? sub[s_me] : -1;
-      if (sidx >= 0) {
-        const float sc = nu_inv ? nu_inv[sidx] : 1.f;
-        const float wy = wys[j_me];
-        float* Es = E + (long)sidx * mm + j_me * m;
+      const float sc = (sidx >= 0 && nu_inv) ? nu_inv[sidx] : 1.f;
+      const float wy = wys[j_me];
+      float* Es = E + (long)max(sidx, 0) * mm + j_me * m;
 #pragma unroll
-        for (int b = 0; b < NPR; ++b)
-          if (b < m) Es[b] = wy * wxs[b] * v[b] * sc;
+      for (int c = 0; c < NPC; ++c) {
+        tmem_ld16(taddr + c * 16, v);
+        tmem_wait_ld();
+        if (sidx >= 0) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int b = c * 16 + i;
+            if (b < m) Es[b] = wy * wxs[b] * v[i] * sc;
+          }
+        }
       }
     }
     ok = tc_sync(ok);
@@ -349,9 +374,7 @@ TcLay tc_layout(int m) {
   L.KP = (m + KS - 1) / KS * KS;
   L.cols = L.NP <= 32 ? 32 : 64;
   const int chunks = L.KP * ES / 16;
-  // core matrices 144 bytes apart along K (a 16-byte gap): the transposing
-  // writes of consecutive K then fall in distinct banks
-  L.lbo = 144;
+  L.lbo = kLbo;
   L.sbo = (uint32_t)chunks * L.lbo;
   L.a_bytes = (kTcThreads / 8) * L.sbo;
   L.b_bytes = (uint32_t)(L.NP / 8) * L.sbo;

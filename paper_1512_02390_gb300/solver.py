@@ -132,3 +132,62 @@ class Batch:
 
     def autotune(self, cache_path=None, stream=None):
         B.sem_batch_autotune(self.h, cache_path, stream)
+
+
+def main(argv=None):
+    """Solve one seeded random-RHS problem (b = M f, f ~ U[-1, 1] at the GLL
+    nodes, u0 = 0) a few times and print one JSON line per solve:
+
+        python -m paper_1512_02390_gb300.solver --nx 64 --ny 64 --p 16 --overlap 2 --precision tf32
+
+    --trace runs every solve launch by launch with CUDA-event tracing (no
+    graph replay; what a kernel profiler can attribute), --tune autotunes the
+    launch shapes first, --set-tune L:FUSE:SPW:TC fixes level L's shapes."""
+    import argparse
+    import json
+
+    import torch
+
+    import sem_inputs as SI
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=64)
+    ap.add_argument("--ny", type=int, default=64)
+    ap.add_argument("--p", type=int, default=16)
+    ap.add_argument("--overlap", type=int, default=2)
+    ap.add_argument("--precision", default="tf32", choices=sorted(_PREC))
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--solves", type=int, default=3)
+    ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--set-tune", action="append", default=[])
+    a = ap.parse_args(argv)
+    S = Solver(nx=a.nx, ny=a.ny, p=a.p, overlap=a.overlap, precision=a.precision, tol=a.tol, i_max=500)
+    if a.tune:
+        S.autotune()
+    for spec in a.set_tune:
+        lvl, fuse, spw, tc = (int(x) for x in spec.split(":"))
+        S.set_tune(lvl, fuse, spw, tc)
+    fn = torch.from_numpy(SI.uniform_nodal(a.seed, S.shape).ravel()).cuda()
+    b = torch.empty_like(fn)
+    S.mass(fn, b)
+    S.profile(a.trace)
+    for k in range(a.solves):
+        u = torch.zeros_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res, _ = S.pcg_solve(u, b)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"solve": k, "iterations": res.iterations, "status": B.status_name(res.status),
+                          "rel_res": res.res / res.res0 if res.res0 else 0.0, "ms": round(ms, 4),
+                          "dof_per_s": S.n_unknowns / (ms * 1e-3)}))
+    if a.trace:
+        print(json.dumps({"class_ms_total": {k: round(v[0], 4) for k, v in S.profile_read().items()}}))
+    S.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -71,7 +71,10 @@ def test_tuned_shapes_give_identical_solves(cfg):
     if avail:  # tcgen05 and mma.sync sweeps round in another order: same solve to the tolerance
         it0, it1 = ref0[0][0], ref[0][0]
         assert abs(it0 - it1) <= 1
-        assert np.abs(ref[0][2] - ref0[0][2]).max() <= 1e-8 * np.abs(ref0[0][2]).max()
+        u1, u0 = ref[0][2], ref0[0][2]
+        if cfg.get("periodic"):  # solutions are unique up to a constant
+            u1, u0 = u1 - u1.mean(), u0 - u0.mean()
+        assert np.abs(u1 - u0).max() <= 1e-8 * np.abs(u0).max()
 
 
 def test_autotune_cache_roundtrip(tmp_path):

@@ -33,7 +33,7 @@ CASES = [
     dict(nx=12, ny=10, p=16, overlap=2),                    # m = 21, the bench's window
     dict(nx=12, ny=9, p=16, overlap=1),                     # m = 19
     dict(nx=7, ny=6, p=32, overlap=2),                      # m = 37, three per stack, 48-column accumulator
-    dict(nx=16, ny=14, p=8, overlap=1, stretch=True),       # x geometric: a table per column
+    dict(nx=24, ny=24, p=8, overlap=1, stretch=True),       # x geometric: a table per column
     dict(nx=16, ny=16, p=8, overlap=1, nu=("contrast", 10.0)),  # 1 / nu_bar per subdomain
 ]
 
