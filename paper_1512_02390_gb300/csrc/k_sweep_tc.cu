@@ -238,25 +238,55 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
       cur_tx = tx;
       cur_ty = ty;
     }
-    // gather R_s r into the stack: warp w takes window rows w, w + 4, ...;
-    // lane b reads node b of the row (consecutive lanes, consecutive nodes)
-    for (int row = warp; row < rows; row += kTcThreads / 32) {
-      const int s = row / m, a = row - s * m;
-      const int sidx = sub[s];
-      const uint32_t ro = row_off(row, L.sbo);
-      int ey = 0, ex = 0, gy = -1;
-      if (sidx >= 0) {
-        ey = sidx / dx.n;
-        ex = sidx - ey * dx.n;
-        gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
-      }
-      for (int b = lane; b < m; b += 32) {
-        float x = 0.f;
-        if (gy >= 0) {
-          const int gx = node_or_wall(ex * p + b - no, Nx, dx.periodic, dx.segN);
-          if (gx >= 0) x = (float)r[(long)gy * Nx + gx];
+    // gather R_s r into the stack.  Lane l of every warp first finds the
+    // window origin of slots l and l + 32 (flag 1: window inside the grid and
+    // clear of stacked-problem walls, no per-node checks; 2: needs them;
+    // 0: empty slot); then warp w takes window rows w, w + 4, ... and lane b
+    // reads node b of the row (consecutive lanes, consecutive nodes).
+    int oy0 = 0, ox0 = 0, fl0 = 0, oy1 = 0, ox1 = 0, fl1 = 0;
+    {
+      auto origin = [&](int s, int& oy, int& ox, int& fl) {
+        const int sidx = s < G ? sub[s] : -1;
+        if (sidx < 0) return;
+        const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
+        oy = ey * p - no;
+        ox = ex * p - no;
+        // every node of the window an unknown: inside the walls, and no
+        // stacked-problem wall (multiple of segN) in [o, o + m - 1]
+        const bool in_y = oy > 0 && oy + m - 1 < dy.N - 1 &&
+                          (dy.segN == 0 || (oy - 1) / dy.segN == (oy + m - 1) / dy.segN);
+        const bool in_x = ox > 0 && ox + m - 1 < dx.N - 1 &&
+                          (dx.segN == 0 || (ox - 1) / dx.segN == (ox + m - 1) / dx.segN);
+        fl = (in_x && in_y && !dx.periodic && !dy.periodic) ? 1 : 2;
+      };
+      origin(lane, oy0, ox0, fl0);
+      origin(lane + 32, oy1, ox1, fl1);
+    }
+    {
+      int s = 0, a = warp;  // row = s m + a, advanced by 4 rows per step
+      while (a >= m) a -= m, ++s;
+#pragma unroll 2
+      for (int row = warp; row < rows; row += kTcThreads / 32) {
+        const int src = s & 31;
+        const bool hi = s >= 32;
+        const int oy = __shfl_sync(0xffffffffu, hi ? oy1 : oy0, src);
+        const int ox = __shfl_sync(0xffffffffu, hi ? ox1 : ox0, src);
+        const int fl = __shfl_sync(0xffffffffu, hi ? fl1 : fl0, src);
+        const uint32_t ro = row_off(row, L.sbo);
+        int gy = oy + a;
+        if (fl == 2) gy = node_or_wall(gy, dy.N, dy.periodic, dy.segN);
+        for (int b = lane; b < m; b += 32) {
+          float x = 0.f;
+          if (fl == 1) {
+            x = (float)r[(long)gy * Nx + ox + b];
+          } else if (fl == 2 && gy >= 0) {
+            const int gx = node_or_wall(ox + b, Nx, dx.periodic, dx.segN);
+            if (gx >= 0) x = (float)r[(long)gy * Nx + gx];
+          }
+          op_put<MODE>(sA, ro + k_off<MODE>(b), x);
         }
-        op_put<MODE>(sA, ro + k_off<MODE>(b), x);
+        a += kTcThreads / 32;
+        while (a >= m) a -= m, ++s;
       }
     }
     ok = tc_sync(ok);

@@ -15,6 +15,7 @@
 // projected to zero mean, the (0, 0) eigen-pair is dropped and the result is
 // made orthogonal to the constants: the Moore-Penrose solution A_0^+ f_0.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -324,8 +325,110 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
   }
 }
 
+// The same exact coarse solve, u_0 = A_0^+ f_0 by the global fast
+// diagonalisation U = S_y [(S_y^T F S_x) ./ (lambda_y + lambda_x^T)] S_x^T,
+// in FP32 by ONE CTA per problem for coarse grids of at most 64 x 64
+// unknowns (the mixed-precision V-cycle): the four products run back to back
+// in shared memory, each thread holding a 4 x 4 block of the 64 x 64 result.
+constexpr int kC32 = 64, kC32P = 65;  // tile and padded pitch (floats)
+
+template <typename LA, typename LB, typename EP>
+__device__ __forceinline__ void coarse_gemm32(int K, LA la, LB lb, EP ep) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  float acc[4][4] = {};
+  for (int k = 0; k < K; ++k) {
+    float a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = la(tr + 16 * i, k);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = lb(k, tc + 16 * j);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ep(tr + 16 * i, tc + 16 * j, acc[i][j]);
+}
+
+__global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
+                                                      float* __restrict__ u0) {
+  extern __shared__ __align__(16) unsigned char smem_c32[];
+  float* Sx = reinterpret_cast<float*>(smem_c32);  // 4 x 64 x 65 floats: S_x, S_y, W1, W2
+  float* Sy = Sx + kC32 * kC32P;
+  float* W1 = Sy + kC32 * kC32P;
+  float* W2 = W1 + kC32 * kC32P;
+  __shared__ float lx[kC32], ly[kC32], cx[kC32], cy[kC32];
+  __shared__ double sred[kRedThreads];
+  const int nux = c.nux, nuy = c.nuy, t = threadIdx.x;
+  const int fy0 = c.firsty + blockIdx.x * c.block_rows;
+  for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
+    const int a = idx / kC32, b = idx - a * kC32;
+    Sx[a * kC32P + b] = (a < nux && b < nux) ? (float)c.Sx[a * nux + b] : 0.f;
+    Sy[a * kC32P + b] = (a < nuy && b < nuy) ? (float)c.Sy[a * nuy + b] : 0.f;
+    float fv = 0.f;
+    if (a < nuy && b < nux) fv = f0[(long)(fy0 + a) * c.Nx + c.firstx + b];
+    W1[a * kC32P + b] = fv;
+  }
+  for (int i = t; i < kC32; i += blockDim.x) {
+    lx[i] = i < nux ? (float)c.lx[i] : 1.f;
+    ly[i] = i < nuy ? (float)c.ly[i] : 1.f;
+    cx[i] = (c.periodic && i < nux) ? (float)c.cx[i] : 0.f;
+    cy[i] = (c.periodic && i < nuy) ? (float)c.cy[i] : 0.f;
+  }
+  __syncthreads();
+  float shift = 0.f;
+  if (c.periodic) {  // right side projected to zero mean
+    double acc = 0.0;
+    for (int idx = t; idx < nux * nuy; idx += blockDim.x) acc += W1[(idx / nux) * kC32P + idx % nux];
+    shift = (float)(block_sum(acc, sred) / ((double)nux * nuy));
+    __syncthreads();
+    for (int idx = t; idx < nux * nuy; idx += blockDim.x) W1[(idx / nux) * kC32P + idx % nux] -= shift;
+    __syncthreads();
+  }
+  // W2 = S_y^T F
+  coarse_gemm32(nuy, [&](int r, int k) { return Sy[k * kC32P + r]; }, [&](int k, int q) { return W1[k * kC32P + q]; },
+                [&](int r, int q, float v) { W2[r * kC32P + q] = v; });
+  __syncthreads();
+  // W1 = (W2 S_x) ./ (lambda_y + lambda_x^T); the null pair dropped when periodic
+  coarse_gemm32(nux, [&](int r, int k) { return W2[r * kC32P + k]; }, [&](int k, int q) { return Sx[k * kC32P + q]; },
+                [&](int r, int q, float v) {
+                  W1[r * kC32P + q] = (c.periodic && r == 0 && q == 0) ? 0.f : v / (ly[r] + lx[q]);
+                });
+  __syncthreads();
+  float mean_u = 0.f;
+  if (c.periodic) {  // mean(U) = c_y^T W1 c_x / N: the solution is returned with zero mean
+    double acc = 0.0;
+    for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
+      const int a = idx / nux, b = idx - a * nux;
+      acc += (double)cy[a] * W1[a * kC32P + b] * cx[b];
+    }
+    mean_u = (float)(block_sum(acc, sred) / ((double)nux * nuy));
+  }
+  // W2 = S_y W1
+  coarse_gemm32(nuy, [&](int r, int k) { return Sy[r * kC32P + k]; }, [&](int k, int q) { return W1[k * kC32P + q]; },
+                [&](int r, int q, float v) { W2[r * kC32P + q] = v; });
+  __syncthreads();
+  // U = W2 S_x^T
+  coarse_gemm32(nux, [&](int r, int k) { return W2[r * kC32P + k]; }, [&](int k, int q) { return Sx[q * kC32P + k]; },
+                [&](int r, int q, float v) {
+                  if (r < nuy && q < nux) u0[(long)(fy0 + r) * c.Nx + c.firstx + q] = v - mean_u;
+                });
+}
+
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c.nux <= kC32 && c.nuy <= kC32) {
+      const size_t sm = 4 * sizeof(float) * kC32 * kC32P;
+      cudaError_t e = allow_smem(k_coarse_fdm32, sm);
+      if (e != cudaSuccess) return e;
+      k_coarse_fdm32<<<std::max(1, c.batch), 256, sm, s>>>(c, f0, u0);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8, std::max(1, c.batch));
   const size_t sm = 2 * 8 * sizeof(double) * (size_t)std::max(c.nux, c.nuy);
   cudaError_t e0 = allow_smem(k_coarse_gemm<T>, sm);

@@ -91,8 +91,11 @@ struct CoarseView {
   double* T1;  // batch x nuy x nux scratch (also holds S_y T2)
   double* T2;  // batch x nuy x nux scratch
 };
+// FP64: four multi-CTA products; FP32 with at most 64 x 64 unknowns: one CTA
+// per problem runs all four
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s);
+inline int coarse_launches(const CoarseView& c, bool fp32) { return (fp32 && c.nux <= 64 && c.nuy <= 64) ? 1 : 4; }
 // u0 = Binv f0 over the Dirichlet unknowns with a dense FP64 inverse (variable nu)
 template <typename T>
 cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s);

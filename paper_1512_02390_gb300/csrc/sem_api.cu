@@ -379,7 +379,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
     KL(h, SEM_K_COARSE, s,
        launch_coarse_dense<T>(h->coarse, h->Binv, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
   else
-    KLN(h, SEM_K_COARSE, 4, s,
+    KLN(h, SEM_K_COARSE, coarse_launches(h->coarse, !dbl), s,
         launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
   bool z_written = dbl;
   for (int l = 1; l <= L; ++l) {

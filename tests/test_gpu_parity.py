@@ -262,3 +262,25 @@ def test_mg_solve_rate_matches_oracle():
     # scale of the initial residual
     np.testing.assert_allclose(hist, hist_o, rtol=1e-8, atol=1e-13 * hist_o[0])
     assert abs(res.rbar - 1.29) < 0.05  # Table 1, p = 8, w_5
+
+
+@pytest.mark.parametrize("case", [dict(nx=4, ny=4, p=4), dict(nx=4, ny=6, p=8, periodic=True, overlap=3),
+                                  dict(nx=12, ny=10, p=4, overlap=1), dict(nx=9, ny=9, p=8, periodic=True, overlap=1),
+                                  dict(nx=65, ny=20, p=2, overlap=1), dict(nx=66, ny=12, p=2, overlap=1)], ids=_ids)
+def test_fp32_vcycle_matches_oracle(case):
+    """Alg. 3 in the FP32 V-cycle (SIMT sweeps; the one-CTA FP32 coarse solve
+    where the coarse grid has at most 64 x 64 unknowns, the four-launch
+    product beyond): the correction u_new - u_old agrees with the FP64
+    oracle's to FP32 accuracy (1e-5 of its maximum)."""
+    S, H = _pair(precision="fp32", **case)
+    lev = H.top
+    u0 = SI.uniform_nodal(7, (lev.NY, lev.NX)) * lev.unknown
+    f = lev.mass(SI.uniform_nodal(8, (lev.NY, lev.NX)))
+    ud = _dev(u0).reshape(-1)
+    S.vcycle(ud, _dev(f).reshape(-1))
+    ns1, ns2 = H.steps(1, 0)
+    want = H.vcycle(u0, f, ns1, ns2) - u0
+    got = _host(ud).reshape(lev.NY, lev.NX) - u0
+    if H.mx.periodic:
+        got, want = got - got.mean(), want - want.mean()
+    assert _rel(got, want) < 1e-5
