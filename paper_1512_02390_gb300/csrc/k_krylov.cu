@@ -30,16 +30,19 @@ __device__ __forceinline__ void segment(const PcgState& st, long n, int k, long&
 }
 
 // Iteration i = iter[0], problem k = blockIdx.y (skipped once done):
+// [z != null: p = z + beta p with beta = beta_k,iter[1], the direction update
+// of Alg. 4 fused here and into the operator that formed q]
 // alpha_k = delta_k,i-1 / (p.q)_k;  u += alpha p;  r -= alpha q;  then the
 // last CTA reduces every problem's ||r||^2 in fixed order, records the
 // scalars, sets done / status (convergence ||r|| <= r_max, breakdown, i_max),
 // advances the counter and, inside a graph, sets the WHILE condition to
 // "some problem still iterating".  npq: partials of p.q per problem.
 __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restrict__ u, double* __restrict__ r,
-                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         double* __restrict__ p, const double* __restrict__ q,
                                                          const double* __restrict__ part_pq, int npq, PcgState st,
                                                          double* __restrict__ part_rr, int i_max,
-                                                         cudaGraphConditionalHandle cond, int use_cond) {
+                                                         cudaGraphConditionalHandle cond, int use_cond,
+                                                         const double* __restrict__ z) {
   __shared__ double sred[kRedThreads];
   __shared__ int am_last;
   if (*st.active == 0) {  // nothing left (zero or invalid start of every problem)
@@ -59,11 +62,23 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
     }
     long lo, hi;
     segment(st, n, k, lo, hi);
-    for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-      u[i] += alpha * p[i];
-      const double ri = r[i] - alpha * q[i];
-      r[i] = ri;
-      acc += ri * ri;
+    if (z) {
+      const double beta = st.beta[(long)k * st.stride + st.iter[1]];
+      for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
+        const double pi = fma(beta, p[i], z[i]);  // the operator staged the same value
+        p[i] = pi;
+        u[i] += alpha * pi;
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+      }
+    } else {
+      for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+      }
     }
   }
   const double s = block_sum(acc, sred);
@@ -105,6 +120,53 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
     *st.ticket = 0u;
     if (use_cond) cudaGraphSetConditional(cond, active ? 1u : 0u);
   }
+}
+
+// i = iter[1], problem k: partials of z.q (q = A p of iteration i) and z.r;
+// the last CTA reduces every live problem's partials in fixed order and
+// records beta_i = z^T (r_i - r_{i-1}) / delta_{i-1} in the form
+// (i == 1 ? z^T r : -alpha_i z^T q) / delta_{i-1} (r_i - r_{i-1} = -alpha_i q,
+// and r_old = 0 before the first update, Alg. 4), and delta_i = z^T r.
+__global__ void __launch_bounds__(256) k_dot2_beta(long n, const double* __restrict__ z,
+                                                   const double* __restrict__ r, const double* __restrict__ q,
+                                                   double* __restrict__ part, PcgState st) {
+  __shared__ double sred[kRedThreads];
+  __shared__ int am_last;
+  const int k = blockIdx.y;
+  double a = 0.0, b = 0.0;
+  if (st.flags[2 * k] == 0) {
+    long lo, hi;
+    segment(st, n, k, lo, hi);
+    for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
+      const double zi = z[i];
+      a += zi * q[i];
+      b += zi * r[i];
+    }
+  }
+  const double sa = block_sum(a, sred);
+  const double sb = block_sum(b, sred);
+  if (threadIdx.x == 0) {
+    part[(long)k * gridDim.x + blockIdx.x] = sa;
+    part[(long)(st.nb + k) * gridDim.x + blockIdx.x] = sb;
+    __threadfence();
+    const unsigned ticket = atomicAdd(st.ticket, 1u);
+    am_last = ticket == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const int it = st.iter[1];
+  for (int kk = 0; kk < st.nb; ++kk) {
+    const double zq = sum_partials_cg(part + (long)kk * gridDim.x, gridDim.x, sred);
+    const double zr = sum_partials_cg(part + (long)(st.nb + kk) * gridDim.x, gridDim.x, sred);
+    if (threadIdx.x == 0 && st.flags[2 * kk] == 0) {
+      const long o = (long)kk * st.stride + it;
+      const double num = it == 1 ? zr : -st.alpha[o] * zq;
+      st.beta[o] = num / st.delta[o - 1];
+      st.delta[o] = zr;
+    }
+  }
+  if (threadIdx.x == 0) *st.ticket = 0u;
 }
 
 // per problem k: part[k G + c] = sum z.(r - r_old), part[(nb + k) G + c] = sum z.r
@@ -268,11 +330,19 @@ int chunk_grid(const PcgState& st) {
   return std::min(g, kMaxPartials / std::max(1, 2 * st.nb));
 }
 
-cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
+cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
-                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
+                                       const double* z) {
   dim3 grid(chunk_grid(st), st.nb);
-  k_update_ur_check<<<grid, 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond);
+  k_update_ur_check<<<grid, 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot2_beta(long n, const double* z, const double* r, const double* q, double* part, PcgState st,
+                             cudaStream_t s) {
+  dim3 grid(chunk_grid(st), st.nb);
+  k_dot2_beta<<<grid, 256, 0, s>>>(n, z, r, q, part, st);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,25 @@ struct Tile {
   static constexpr int NP = P + 1;
 };
 
+// beta of this tile's problem for the fused MGCG direction (0 when unused)
+__device__ __forceinline__ double fused_beta(const PcgFuse& pf) {
+  if (!pf.z) return 0.0;
+  const int k = blockIdx.y / (gridDim.y / pf.nb);
+  return pf.flags[2 * k] ? 0.0 : pf.beta[(long)k * pf.stride + pf.iter[1]];
+}
+
+// staged operand at node (gy, gx) (-1: wall, 0): u, the assembled Schwarz
+// correction (E), or the MGCG direction z + beta p
+template <typename T>
+__device__ __forceinline__ T stage_value(const T* __restrict__ u, const T* __restrict__ E, const DirView<T>& dx,
+                                         const DirView<T>& dy, const PcgFuse& pf, double beta, int gy, int gx) {
+  if (gx < 0 || gy < 0) return T(0);
+  if (E) return window_sum(dx, dy, E, gy, gx);
+  const long o = (long)gy * dx.N + gx;
+  if (pf.z) return T(fma(beta, (double)u[o], pf.z[o]));
+  return u[o];
+}
+
 template <typename T, int P>
 size_t apply_smem() {
   using Tl = Tile<P>;
@@ -37,7 +56,7 @@ template <typename T, typename TF, int P>
 __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
                                                const TF* __restrict__ f, T* __restrict__ out, int dot,
                                                double* __restrict__ part, const T* __restrict__ E,
-                                               T* __restrict__ uout) {
+                                               T* __restrict__ uout, PcgFuse pf) {
   using Tl = Tile<P>;
   constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,14 +70,13 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
   const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
   const int Nx = dx.N, Ny = dy.N;
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+  const double beta = fused_beta(pf);
 
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
     const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    T v = T(0);
-    if (gx >= 0 && gy >= 0) v = E ? window_sum(dx, dy, E, gy, gx) : u[(long)gy * Nx + gx];
-    su[ly * LP + lx] = v;
+    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
   }
   // element stiffness of the tile and of its low-side neighbour (slot 0)
   for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
@@ -231,7 +249,7 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
                                                   const T* __restrict__ f, T* __restrict__ out, int dot,
                                                   double* __restrict__ part, const T* __restrict__ E,
-                                                  T* __restrict__ uout) {
+                                                  T* __restrict__ uout, PcgFuse pf) {
   using Q = EOTile<P>;
   constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE,
                 NV = Q::NV;
@@ -249,13 +267,12 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
   const int Nx = dx.N, Ny = dy.N;
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+  const double beta = fused_beta(pf);
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
     const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    T v = T(0);
-    if (gx >= 0 && gy >= 0) v = E ? window_sum(dx, dy, E, gy, gx) : u[(long)gy * Nx + gx];
-    su[ly * LP + lx] = v;
+    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
   }
   // E/O tables of slot s = element ex0 + s - 1 (slot 0: low-side neighbour)
   for (int idx = threadIdx.x; idx < 2 * (TE + 1) * EO; idx += blockDim.x) {
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double
 
 template <typename T, typename TF, int P>
 cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
-                    double* part, int* nparts, cudaStream_t s, const T* E, T* uout) {
+                    double* part, int* nparts, cudaStream_t s, const T* E, T* uout, const PcgFuse& pf) {
   using Tl = Tile<P>;
   dim3 grid((dx.n + Tl::TE - 1) / Tl::TE, (dy.n + Tl::TE - 1) / Tl::TE);
   if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
@@ -444,12 +461,12 @@ cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, cons
     const size_t sm = apply_eo_smem<T, P>();
     cudaError_t e = allow_smem(k_apply_eo<T, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout);
+    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout, pf);
   } else {
     const size_t sm = apply_smem<T, P>();
     cudaError_t e = allow_smem(k_apply<T, TF, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply<T, TF, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout);
+    k_apply<T, TF, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout, pf);
   }
   return cudaGetLastError();
 }
@@ -458,14 +475,15 @@ cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, cons
 
 template <typename T, typename TF>
 cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
-                         double* part, int* nparts, cudaStream_t s, const T* E, T* uout) {
+                         double* part, int* nparts, cudaStream_t s, const T* E, T* uout, PcgFuse pf) {
+  if (pf.z && !std::is_same<T, double>::value) return cudaErrorInvalidValue;
   switch (dx.p) {
-    case 1: return apply_p<T, TF, 1>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
-    case 2: return apply_p<T, TF, 2>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
-    case 4: return apply_p<T, TF, 4>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
-    case 8: return apply_p<T, TF, 8>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
-    case 16: return apply_p<T, TF, 16>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
-    case 32: return apply_p<T, TF, 32>(dx, dy, u, f, out, dot, part, nparts, s, E, uout);
+    case 1: return apply_p<T, TF, 1>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 2: return apply_p<T, TF, 2>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 4: return apply_p<T, TF, 4>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 8: return apply_p<T, TF, 8>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 16: return apply_p<T, TF, 16>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 32: return apply_p<T, TF, 32>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -498,13 +516,13 @@ template cudaError_t launch_apply_var<float>(const DirView<float>&, const DirVie
 
 template cudaError_t launch_apply<double, double>(const DirView<double>&, const DirView<double>&, const double*,
                                                   const double*, double*, int, double*, int*, cudaStream_t,
-                                                  const double*, double*);
+                                                  const double*, double*, PcgFuse);
 template cudaError_t launch_apply<float, float>(const DirView<float>&, const DirView<float>&, const float*,
                                                 const float*, float*, int, double*, int*, cudaStream_t, const float*,
-                                                float*);
+                                                float*, PcgFuse);
 template cudaError_t launch_apply<float, double>(const DirView<float>&, const DirView<float>&, const float*,
                                                  const double*, float*, int, double*, int*, cudaStream_t,
-                                                 const float*, float*);
+                                                 const float*, float*, PcgFuse);
 
 cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f, double* b,
                         double* part, int* nparts, cudaStream_t s) {

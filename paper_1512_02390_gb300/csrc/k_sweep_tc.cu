@@ -171,6 +171,22 @@ __device__ __forceinline__ void tc_gemm(uint32_t tmem, uint32_t a, uint32_t b, c
   tc_commit(bar);
 }
 
+// One product of the stack: thread 0 issues it and waits (bounded) for its
+// commit; the other threads wait at the barrier, spending no issue slots on
+// polling.  Returns the CTA-uniform completion flag.
+template <int MODE>
+__device__ __forceinline__ bool tc_step(uint32_t tmem, uint32_t a, uint32_t b, const TcLay& L, uint32_t bar,
+                                        uint32_t& phase, volatile int* flag) {
+  if (threadIdx.x == 0) {
+    tc_gemm<MODE>(tmem, a, b, L, bar);
+    *flag = tc_wait(bar, phase) ? 1 : 0;
+  }
+  phase ^= 1u;
+  __syncthreads();
+  fence_after();
+  return *flag != 0;
+}
+
 // NPC = NP / 16: the accumulator row is held in registers (constant indices)
 template <typename TIn, int MODE, int NPC>
 __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirView<float> dy,
@@ -185,6 +201,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
   float* wys = wxs + 64;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
+  __shared__ int s_flag;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t bar = smem_addr(&mbar);
   if (t == 0) {
@@ -262,10 +279,41 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
       origin(lane, oy0, ox0, fl0);
       origin(lane + 32, oy1, ox1, fl1);
     }
-    {
+    if (m <= 32) {
+      // four rows per batch: all loads of a batch are issued before its stores
+      int s = 0, a = warp;  // row = s m + a, advanced by 4 rows at a time
+      while (a >= m) a -= m, ++s;
+      for (int row = warp; row < rows; row += 4 * (kTcThreads / 32)) {
+        float xv[4];
+        uint32_t ro[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rq = row + q * (kTcThreads / 32);
+          const int src = s & 31;
+          const bool hi = s >= 32;
+          const int oy = __shfl_sync(0xffffffffu, hi ? oy1 : oy0, src);
+          const int ox = __shfl_sync(0xffffffffu, hi ? ox1 : ox0, src);
+          const int fl = __shfl_sync(0xffffffffu, hi ? fl1 : fl0, src);
+          ro[q] = rq < rows ? row_off(rq, L.sbo) : 0xffffffffu;
+          xv[q] = 0.f;
+          if (rq < rows && lane < m && fl != 0) {
+            int gy = oy + a, gx = ox + lane;
+            if (fl == 2) {
+              gy = node_or_wall(gy, dy.N, dy.periodic, dy.segN);
+              gx = node_or_wall(gx, Nx, dx.periodic, dx.segN);
+            }
+            if (gx >= 0 && gy >= 0) xv[q] = (float)r[(long)gy * Nx + gx];
+          }
+          a += kTcThreads / 32;
+          while (a >= m) a -= m, ++s;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (ro[q] != 0xffffffffu && lane < m) op_put<MODE>(sA, ro[q] + k_off<MODE>(lane), xv[q]);
+      }
+    } else {
       int s = 0, a = warp;  // row = s m + a, advanced by 4 rows per step
       while (a >= m) a -= m, ++s;
-#pragma unroll 2
       for (int row = warp; row < rows; row += kTcThreads / 32) {
         const int src = s & 31;
         const bool hi = s >= 32;
@@ -292,10 +340,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     ok = tc_sync(ok);
     if (!ok) break;
     // G1: C1 = X S_x
-    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB), L, bar);
-    ok = tc_wait(bar, phase);
-    phase ^= 1u;
-    fence_after();
+    ok = tc_step<MODE>(tmem, a_s, smem_addr(sB), L, bar, phase, &s_flag);
     if (ok) {
       // A2[(s, bh)][a] = C1[(s, a)][bh]
       const uint32_t ko = k_off<MODE>(j_me);
@@ -313,10 +358,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     ok = tc_sync(ok);
     if (!ok) break;
     // G2: C2 = A2 S_y, then / (lambda_y + lambda_x)
-    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + L.b_bytes), L, bar);
-    ok = tc_wait(bar, phase);
-    phase ^= 1u;
-    fence_after();
+    ok = tc_step<MODE>(tmem, a_s, smem_addr(sB + L.b_bytes), L, bar, phase, &s_flag);
     if (ok) {
       const float lx = lxs[j_me];
       unsigned char* ro = sA + row_off(t, L.sbo);
@@ -336,10 +378,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     ok = tc_sync(ok);
     if (!ok) break;
     // G3: C3 = C2 S_y^T
-    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + 2 * L.b_bytes), L, bar);
-    ok = tc_wait(bar, phase);
-    phase ^= 1u;
-    fence_after();
+    ok = tc_step<MODE>(tmem, a_s, smem_addr(sB + 2 * L.b_bytes), L, bar, phase, &s_flag);
     if (ok) {
       // A4[(s, a)][bh] = C3[(s, bh)][a]
       const uint32_t ko = k_off<MODE>(j_me);
@@ -357,10 +396,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     ok = tc_sync(ok);
     if (!ok) break;
     // G4: E = A4 S_x^T, weighted
-    if (t == 0) tc_gemm<MODE>(tmem, a_s, smem_addr(sB + 3 * L.b_bytes), L, bar);
-    ok = tc_wait(bar, phase);
-    phase ^= 1u;
-    fence_after();
+    ok = tc_step<MODE>(tmem, a_s, smem_addr(sB + 3 * L.b_bytes), L, bar, phase, &s_flag);
     if (ok) {
       const int sidx = t < rows ? sub[s_me] : -1;
       const float sc = (sidx >= 0 && nu_inv) ? nu_inv[sidx] : 1.f;
@@ -381,10 +417,10 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
     }
     ok = tc_sync(ok);
   }
-  if (!ok) {
-    if (t == 0) atomicExch(wk.err, 1);
-    // let a commit still in flight land before the accumulator is freed
-    tc_wait(bar, phase);
+  if (!ok && t == 0) {
+    atomicExch(wk.err, 1);
+    // let the commit still in flight land before the accumulator is freed
+    tc_wait(bar, phase ^ 1u);
   }
   fence_before();
   __syncthreads();

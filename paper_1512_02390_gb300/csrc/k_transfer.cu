@@ -329,31 +329,33 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 // diagonalisation U = S_y [(S_y^T F S_x) ./ (lambda_y + lambda_x^T)] S_x^T,
 // in FP32 by ONE CTA per problem for coarse grids of at most 64 x 64
 // unknowns (the mixed-precision V-cycle): the four products run back to back
-// in shared memory, each thread holding a 4 x 4 block of the 64 x 64 result.
+// in shared memory, each of 1024 threads holding a 2 x 2 block of the 64 x 64
+// result.
 constexpr int kC32 = 64, kC32P = 65;  // tile and padded pitch (floats)
 
 template <typename LA, typename LB, typename EP>
 __device__ __forceinline__ void coarse_gemm32(int K, LA la, LB lb, EP ep) {
-  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  float acc[4][4] = {};
+  const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
+  float acc[2][2] = {};
+#pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    float a[4], b[4];
+    float a[2], b[2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = la(tr + 16 * i, k);
+    for (int i = 0; i < 2; ++i) a[i] = la(tr + 32 * i, k);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = lb(k, tc + 16 * j);
+    for (int j = 0; j < 2; ++j) b[j] = lb(k, tc + 32 * j);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      for (int j = 0; j < 2; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ep(tr + 16 * i, tc + 16 * j, acc[i][j]);
+    for (int j = 0; j < 2; ++j) ep(tr + 32 * i, tc + 32 * j, acc[i][j]);
 }
 
-__global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
+__global__ void __launch_bounds__(1024) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
                                                       float* __restrict__ u0) {
   extern __shared__ __align__(16) unsigned char smem_c32[];
   float* Sx = reinterpret_cast<float*>(smem_c32);  // 4 x 64 x 65 floats: S_x, S_y, W1, W2
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float*
   float* W1 = Sy + kC32 * kC32P;
   float* W2 = W1 + kC32 * kC32P;
   __shared__ float lx[kC32], ly[kC32], cx[kC32], cy[kC32];
-  __shared__ double sred[kRedThreads];
+  __shared__ double sred[1024];  // block_sum over all 1024 threads
   const int nux = c.nux, nuy = c.nuy, t = threadIdx.x;
   const int fy0 = c.firsty + blockIdx.x * c.block_rows;
   for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
@@ -425,7 +427,7 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
       const size_t sm = 4 * sizeof(float) * kC32 * kC32P;
       cudaError_t e = allow_smem(k_coarse_fdm32, sm);
       if (e != cudaSuccess) return e;
-      k_coarse_fdm32<<<std::max(1, c.batch), 256, sm, s>>>(c, f0, u0);
+      k_coarse_fdm32<<<std::max(1, c.batch), 1024, sm, s>>>(c, f0, u0);
       return cudaGetLastError();
     }
   }

@@ -16,6 +16,18 @@ constexpr int kMaxPartials = 1 << 17;
 __host__ __device__ constexpr int tile_elems(int P) { return P >= 32 ? 1 : (P <= 4 ? 16 / P : 32 / P); }
 
 // ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
+// The MGCG direction update of Alg. 4 fused into the FP64 operator: the
+// operand is z + beta_k p, beta_k = beta[k * stride + iter[1]] of the tile's
+// problem k (0 once the problem is done), formed with the same fma as the
+// vector update that stores p.  z == nullptr: the plain operand.
+struct PcgFuse {
+  const double* z = nullptr;
+  const double* beta = nullptr;
+  const int* flags = nullptr;
+  const int* iter = nullptr;
+  int stride = 0, nb = 1;
+};
+
 // out = A u (f == nullptr) or out = f - A u.  dot: 0 none, 1 part[cta] = sum
 // u.out, 2 part[cta] = sum out.out over the CTA's nodes.  *nparts receives
 // the number of partials written.  With E != nullptr the input u is not read:
@@ -24,7 +36,7 @@ __host__ __device__ constexpr int tile_elems(int P) { return P >= 32 ? 1 : (P <=
 template <typename T, typename TF>
 cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f,
                          T* out, int dot, double* part, int* nparts, cudaStream_t s, const T* E = nullptr,
-                         T* uout = nullptr);
+                         T* uout = nullptr, PcgFuse pf = PcgFuse());
 
 // Variable-diffusivity operator B(nu) (Sec. 4.3): element data of one level.
 template <typename T>
@@ -123,9 +135,16 @@ struct PcgState {
 int elementwise_grid(long n);
 // CTAs per problem of the batched vector kernels (grid = (chunks, nb))
 int chunk_grid(const PcgState& st);
-cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, const double* p, const double* q,
+// z != nullptr: first p = z + beta_i p (beta_i from launch_dot2_beta), stored
+cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
-                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+                                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
+                                       const double* z = nullptr);
+// i = iter[1]: per problem beta_i = z^T (r - r_old) / delta_{i-1} with
+// r - r_old = -alpha_i q (r_old = 0 at i = 1) and delta_i = z^T r, reduced by
+// the last CTA and stored in the scalar histories
+cudaError_t launch_dot2_beta(long n, const double* z, const double* r, const double* q, double* part, PcgState st,
+                             cudaStream_t s);
 cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old,
                         double* part, PcgState st, cudaStream_t s);
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,

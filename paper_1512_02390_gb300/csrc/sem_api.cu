@@ -246,7 +246,7 @@ const T* NUI(const Level& l) {
 // written to uout (Poisson operator only).
 template <typename T, typename TF = T>
 int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f, T* out, int dot, double* part,
-                int* np, cudaStream_t s, const T* E = nullptr, T* uout = nullptr) {
+                int* np, cudaStream_t s, const T* E = nullptr, T* uout = nullptr, PcgFuse pf = PcgFuse()) {
   if (l.var) {
     if constexpr (std::is_same<T, TF>::value) {
       if (E) return fail(SEM_BAD_ARG, "fused scatter needs the Poisson operator");
@@ -256,7 +256,7 @@ int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f,
       return fail(SEM_BAD_ARG, "variable operator needs a right side of its own type");
     }
   }
-  KL(h, cls, s, (launch_apply<T, TF>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s, E, uout)));
+  KL(h, cls, s, (launch_apply<T, TF>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s, E, uout, pf)));
   return SEM_OK;
 }
 
@@ -414,9 +414,14 @@ int precond(sem_handle* h, const double* r, double* z, cudaStream_t s) {
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
 
 int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s,
-            double* part = nullptr) {
-  return level_apply<double>(h, top(h), SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s);
+            double* part = nullptr, PcgFuse pf = PcgFuse()) {
+  return level_apply<double>(h, top(h), SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s, nullptr,
+                             nullptr, pf);
 }
+
+// The direction update p = z + beta p of Alg. 4 fused into the FP64 operator
+// and the u, r update (Poisson operator): beta from the z.q, z.r reduction.
+bool fused_direction(const sem_handle* h) { return !top(h).var; }
 
 // ---- MGCG, Alg. 4, on the internal vectors h->u, h->fi ---------------------
 // Iteration i is split as: [V-cycle z = M r_{i-1}; beta; p] (body start) and
@@ -424,13 +429,23 @@ int apply64(sem_handle* h, const double* u, const double* f, double* out, int do
 // the body and the loop needs no nested condition.  Iteration 1's second half
 // belongs to the prologue.
 
-// q = A p, p.q;  u, r update and the fused convergence check
-int pcg_tail(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+// q = A p, p.q;  u, r update and the fused convergence check.  fused: the
+// operand is z + beta p (stored as the new p by the update kernel)
+int pcg_tail(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond, bool fused) {
   int np = 0, rc;
-  if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s))) return rc;
+  PcgFuse pf;
+  if (fused) {
+    pf.z = h->z;
+    pf.beta = h->st.beta;
+    pf.flags = h->st.flags;
+    pf.iter = h->st.iter;
+    pf.stride = h->st.stride;
+    pf.nb = h->nb;
+  }
+  if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s, nullptr, pf))) return rc;
   KL(h, SEM_K_VECTOR, s,
      launch_pcg_update_ur_check(h->n, h->u, h->r, h->p, h->q, h->part, np / h->nb, h->st, h->part + kMaxPartials,
-                                h->cfg.i_max, cond, use_cond, s));
+                                h->cfg.i_max, cond, use_cond, s, fused ? h->z : nullptr));
   return SEM_OK;
 }
 
@@ -445,16 +460,20 @@ int pcg_prologue(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond,
   KLN(h, SEM_K_VECTOR, 2, s,
       launch_pcg_start(n, h->z, h->r, h->p, h->r_old, h->part, h->part + 2 * kMaxPartials, np / h->nb, h->st,
                        h->cfg.tol, s));
-  return pcg_tail(h, s, cond, use_cond);
+  return pcg_tail(h, s, cond, use_cond, false);
 }
 
 int pcg_body(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const long n = h->n;
   int rc;
   if ((rc = precond(h, h->r, h->z, s))) return rc;
+  if (fused_direction(h)) {
+    KL(h, SEM_K_VECTOR, s, launch_dot2_beta(n, h->z, h->r, h->q, h->part, h->st, s));
+    return pcg_tail(h, s, cond, use_cond, true);
+  }
   KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r_old, h->part, h->st, s));
   KL(h, SEM_K_VECTOR, s, launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, h->st, s));
-  return pcg_tail(h, s, cond, use_cond);
+  return pcg_tail(h, s, cond, use_cond, false);
 }
 
 // Add prologue + WHILE(body) of h's MGCG to the capture running on `cap`
