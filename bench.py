@@ -39,6 +39,10 @@ WORKLOAD = ("64x64 uniform elements, p=16, n_o=2 (also 1), Dirichlet unit square
 # FP64 and FP32-SIMT peaks of GB300: nominal FP64 1.25 TFLOP/s; FP32 from the
 # unit counts 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one k_apply_eo<double,16> launch on the 64 x 64,
+# p = 16 workload, from the ncu capture summarised in
+# profiles/k_apply_eo_fp64_p16_64x64.md (writes stay in L2 within the launch)
+APPLY_EO_DRAM_BYTES = 17.02e6
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -137,7 +141,11 @@ def _level_work(p, n_o_fixed, ne):
         no = min(n_o_fixed, pl - 1)
         m = pl + 1 + 2 * no
         sweep_flops += 8.0 * m**3 * ne  # four m^3 contractions per subdomain
-    return {"sweep_flops_per_cycle": sweep_flops, "sweep_launches_per_cycle": L}
+    # bytes: read the level residual once (8 B at the finest level of the mixed
+    # cycle, 4 B below) and write m^2 FP32 corrections per subdomain
+    sweep_bytes = sum((ne * (2**l) ** 2) * (8 if l == L else 4) + ne * (2**l + 1 + 2 * min(n_o_fixed, 2**l - 1)) ** 2 * 4
+                      for l in range(1, L + 1))
+    return {"sweep_flops_per_cycle": sweep_flops, "sweep_launches_per_cycle": L, "sweep_bytes_per_cycle": sweep_bytes}
 
 
 def c5_configs(seed=7, count=512, prec="tf32"):
@@ -160,7 +168,7 @@ def run_batched(args, flush, stream):
     batch = P.Batch(cfgs)
     setup_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    batch.autotune()
+    batch.autotune(args.tune_cache)
     tune_s = time.perf_counter() - t0
     bs, us = [], []
     for k, c in enumerate(cfgs):
@@ -270,7 +278,8 @@ def run_ours(args):
 
     def make(prec, n_o):
         S = P.Solver(nx=NX, ny=NY, p=P_ORDER, overlap=n_o, weight=5, precision=prec, tol=TOL, i_max=100)
-        S.tune = S.autotune()  # launch shapes per level, timed on this GPU (results unchanged)
+        # launch shapes per level, timed on this GPU (or read from --tune-cache)
+        S.tune = S.autotune(args.tune_cache)
         fn = SI.uniform_nodal(SEED + rank, S.shape)  # each replica solves its own problem
         b = torch.empty(S.nx_nodes * S.ny_nodes, dtype=torch.float64, device="cuda")
         S.mass(torch.from_numpy(fn.ravel()).cuda(), b)
@@ -375,26 +384,30 @@ def run_ours(args):
     iters = res.iterations
     ne = NX * NY
     roof = None
+    per_launch_ms = kprof[dom][0] / max(1, kprof[dom][1])
     if dom == "apply_fp64":
-        # even-odd sum factorisation: per element row (p/2+1)^2 + (p/2)^2 FMA
-        # + p adds (e/o) + p adds (outputs), two directions, per p nodes;
-        # plus mass scaling (3 flop) per node
-        h = P_ORDER // 2
-        per_row = 2 * ((h + 1) ** 2 + h * h) + 2 * P_ORDER
-        flops = (2 * per_row / P_ORDER + 3) * S.n_unknowns * kprof[dom][1]
-        ach = flops / (kprof[dom][0] * 1e-3) / 1e12
-        roof = {"kernel": "k_apply_eo<double,16> (q = A p, Eq. (system matrix), even-odd)", "bound": "alu",
-                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "nominal FP64 rate of GB300"}
+        # algorithmic count of the operator: two contractions of n_p^3 FMA per
+        # element, 4 n_p^3 / p^2 flop per unknown; the even-odd kernel executes
+        # 2 (2 ((p/2+1)^2 + (p/2)^2) + 2p) / p + 3 per unknown
+        np_ = P_ORDER + 1
+        alg = 4.0 * np_**3 / P_ORDER**2
+        hh = P_ORDER // 2
+        executed = 2 * (2 * ((hh + 1) ** 2 + hh * hh) + 2 * P_ORDER) / P_ORDER + 3
+        ach = alg * S.n_unknowns / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": APPLY_EO_DRAM_BYTES,
+                "kernel": "k_apply_eo<double,16>: q = A (z + beta p), Eq. (system matrix), even-odd",
+                "flop_per_dof_algorithmic": alg, "flop_per_dof_executed": executed,
+                "algorithmic_bytes_per_launch": 24 * S.n_unknowns,
+                "peak_source": "nominal GB300 FP64 rate (FMA probe: 1.196 TFLOP/s measured)"}
     elif dom == "sweep":
         w = _level_work(P_ORDER, N_O, ne)
         cycles = kprof[dom][1] / w["sweep_launches_per_cycle"]
-        flops = w["sweep_flops_per_cycle"] * cycles
-        ach = flops / (kprof[dom][0] * 1e-3) / 1e12
-        pk = FP64_PEAK_TFLOPS if HEADLINE == "fp64" else FP32_PEAK_TFLOPS
-        roof = {"kernel": "k_sweep_simt (gather + FDM + weights, Alg. 2)", "bound": "alu", "achieved": ach,
-                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
-                "peak_source": "FP32 SIMT from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+        ach = w["sweep_bytes_per_cycle"] * cycles / (kprof[dom][0] * 1e-3) / 1e9
+        pk = peaks.get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk, "traffic": None,
+                "kernel": "Schwarz sweep (gather + FDM + weights, Alg. 2), all levels",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks.get("hbm_gbs") else "fallback"}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None}
@@ -459,6 +472,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON-lines autotuner cache: read, else timed and written (a profiler run then uses the "
+                         "launch shapes of the plain run before it)")
     ap.add_argument("--variants", default="all", choices=["all", "headline"],
                     help="headline: time only the headline precision and the FP64 reference variant")
     args = ap.parse_args()

@@ -47,6 +47,11 @@ design notes of the repository):
   R8 lower-level corrections u_l (l < L) start from zero in every cycle.
   R9 n_{o,l} = min(rule(p_l), p_l - 1); level 0 is never smoothed.
   R10 nu_bar_s is the GLL-quadrature mean of nu over the embedded element.
+  R16 learned weights (not in the paper): per interface line a transition
+     half-width scale s in (0, 1] and a shape degree kt in [1, 7], phi the
+     convex blend of the two neighbouring odd-degree shape functions.
+  R18 variable diffusivity: B(nu) is the weak form with nu sampled at the GLL
+     nodes inside the GLL quadrature of each element.
 """
 from __future__ import annotations
 
@@ -237,7 +242,7 @@ def phi(kappa, x):
 
 def phi_blend(kt, x):
     """Shape function of continuous degree kt in [1, 7]: convex blend of the two
-    neighbouring odd degrees of Table (weighting) (learned weights, R15)."""
+    neighbouring odd degrees of Table (weighting) (learned weights, R16)."""
     t = min(3.0, max(0.0, 0.5 * (kt - 1.0)))
     k0 = min(2, int(t))
     fr = t - k0
@@ -362,7 +367,7 @@ class Level:
         return s
 
     def _weights_1d(self, mesh: Mesh1D, e: int, k: np.ndarray, axis: int = 0) -> np.ndarray:
-        """1D weights of Eq. (weight function), readings R3-R5 (learned: R15)."""
+        """1D weights of Eq. (weight function), readings R3-R5 (learned: R16)."""
         if self.weight == "I":
             return np.ones(len(k))
         if self.weight == "a":
