@@ -259,6 +259,65 @@ def run_learned(args, stream):
     return out
 
 
+def run_high_order(args, stream):
+    """32 x 32 elements, p = 32 (1,046,529 unknowns), n_o in {1, 2, 3}: BF16
+    tensor-core sweeps inside the FP64 MGCG.  Per iteration i the relative
+    residual and the error ||u_i - u*|| / ||u*|| against the converged FP64
+    solve u* (the FP64 path matches the CPU oracle to 1e-12, tests), the
+    iterate u_i taken by a solve with i_max = i; plus DOF/s of both."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    out = {}
+    for no in (1, 2, 3):
+        kw = dict(nx=32, ny=32, p=32, overlap=no, weight=5, tol=TOL)
+        S64 = P.Solver(precision="fp64", i_max=200, **kw)
+        fn = torch.from_numpy(SI.uniform_nodal(SEED, S64.shape).ravel()).cuda()
+        b = torch.empty_like(fn)
+        S64.mass(fn, b)
+        ustar = torch.zeros_like(b)
+        r64, hist64 = S64.pcg_solve(ustar, b, history_len=64)
+        nrm = ustar.norm().item()
+        row = {"m": 33 + 2 * no}
+        for prec in ("fp64", "bf16"):
+            S = S64 if prec == "fp64" else P.Solver(precision=prec, i_max=200, **kw)
+            if prec != "fp64":
+                S.autotune(args.tune_cache)
+            u = torch.zeros_like(b)
+            for _ in range(2):
+                u.zero_()
+                res, hist = S.pcg_solve(u, b, history_len=64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u.zero_()
+            e0.record(stream)
+            res, hist = S.pcg_solve(u, b, history_len=64)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            errs = []
+            for i in range(1, res.iterations + 1):
+                Si = P.Solver(precision=prec, i_max=i, **kw)
+                if prec != "fp64":
+                    Si.set_tune_from(S)
+                ui = torch.zeros_like(b)
+                Si.pcg_solve(ui, b)
+                errs.append((ui - ustar).norm().item() / nrm)
+                Si.close()
+            row[prec] = {"iterations": res.iterations, "status": res.status, "ms": ms,
+                         "dof_per_s": S.n_unknowns / (ms * 1e-3) if res.status == 0 else 0.0,
+                         "rel_residual_per_iteration": [float(h / hist[0]) for h in hist[:res.iterations + 1]],
+                         "rel_error_vs_fp64_per_iteration": errs,
+                         "final_rel_error_vs_fp64": (u - ustar).norm().item() / nrm}
+            if prec != "fp64":
+                S.close()
+        S64.close()
+        out["n_o=%d" % no] = row
+    out["workload"] = ("32x32 elements, p = 32 (1,046,529 unknowns), Dirichlet, b = M f, f ~ U[-1,1] seed 1, "
+                       "MGCG(1,0) w_5 to 1e-10; errors against the converged FP64 solve")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -312,6 +371,7 @@ def run_ours(args):
         return times, res, S.profile_read()
 
     variants = {}
+    fp64_solution = {}
     head = None
     todo = [("fp64", N_O), (HEADLINE, N_O)]
     if args.variants == "all":
@@ -337,9 +397,18 @@ def run_ours(args):
             t = torch.tensor([ms], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
+        # solution error against the FP64 solve of the same problem (the FP64
+        # path matches the CPU oracle to 1e-12 in the tests)
+        u_chk = torch.zeros_like(b)
+        S.pcg_solve(u_chk, b)
+        if prec == "fp64":
+            fp64_solution[n_o] = u_chk
+        ref = fp64_solution.get(n_o)
+        err = (u_chk - ref).norm().item() / ref.norm().item() if ref is not None else None
         variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
                          "iterations": res.iterations, "status": res.status,
                          "final_rel_residual": res.res / res.res0 if res.res0 else 0.0,
+                         "rel_error_vs_fp64": err,
                          "launch_shapes": {"p%d" % (1 << l): {"fuse": t["fuse"], "tc": t["tc"], "spw": t["spw"],
                                                               "us": round(t["us"], 2)}
                                            for l, t in S.tune.items()}}
@@ -435,6 +504,7 @@ def run_ours(args):
     if args.variants == "all" and rank == 0:
         line["batched"] = run_batched(args, flush, stream)
         line["learned"] = run_learned(args, stream)
+        line["high_order_bf16"] = run_high_order(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
         line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",

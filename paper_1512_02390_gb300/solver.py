@@ -104,6 +104,13 @@ class Solver:
     def get_tune(self, level):
         return B.sem_get_tune(self.h, level)
 
+    def set_tune_from(self, other):
+        """Copy the launch shapes of a handle with the same levels."""
+        for l in range(1, self.levels + 1):
+            t = other.get_tune(l)
+            tc = t["tc"] if self.get_tune(l)["tc_available"] else 0
+            B.sem_set_tune(self.h, l, t["fuse"], t["spw"], tc)
+
 
 class Batch:
     """Many independent problems solved together (sem_batch_*)."""
