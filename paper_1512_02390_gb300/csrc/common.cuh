@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace sem {
 
@@ -109,6 +110,38 @@ __device__ __forceinline__ T window_sum(const DirView<T>& dx, const DirView<T>& 
     }
   }
   return s;
+}
+
+}  // namespace sem
+
+namespace sem {
+
+// Programmatic dependent launch (sm_90+).  Every kernel of the solver opens
+// with pdl_enter(): wait until the kernel before it in the stream has completed
+// and its writes are visible (returns at once when the launch carried no
+// programmatic dependency), then allow the next kernel to start launching.
+// launch_pdl() enqueues with the programmatic-serialization attribute, so the
+// next kernel's launch and CTA scheduling overlap this kernel's tail while no
+// kernel reads anything before its predecessor has finished.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace sem

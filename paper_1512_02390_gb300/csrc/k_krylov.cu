@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
                                                          double* __restrict__ part_rr, int i_max,
                                                          cudaGraphConditionalHandle cond, int use_cond,
                                                          const double* __restrict__ z) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   __shared__ int am_last;
   if (*st.active == 0) {  // nothing left (zero or invalid start of every problem)
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
 __global__ void __launch_bounds__(256) k_dot2_beta(long n, const double* __restrict__ z,
                                                    const double* __restrict__ r, const double* __restrict__ q,
                                                    double* __restrict__ part, PcgState st) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   __shared__ int am_last;
   const int k = blockIdx.y;
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(256) k_dot2_beta(long n, const double* __restr
 __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__ z, const double* __restrict__ r,
                                               const double* __restrict__ r_old, double* __restrict__ part,
                                               PcgState st) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const int k = blockIdx.y;
   long lo, hi;
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__
 __global__ void __launch_bounds__(256) k_update_p(long n, const double* __restrict__ z, double* __restrict__ p,
                                                   const double* __restrict__ r, double* __restrict__ r_old,
                                                   const double* __restrict__ part, int np, PcgState st) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const int k = blockIdx.y;
   if (st.flags[2 * k]) return;
@@ -222,6 +226,7 @@ __global__ void __launch_bounds__(256) k_start(long n, const double* __restrict_
                                                const double* __restrict__ part_zr, int nzr,
                                                const double* __restrict__ part_rr, int nrr, PcgState st,
                                                double tol) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const int k = blockIdx.y;
   const double zr = sum_partials(part_zr + (long)(st.nb + k) * nzr, nzr, sred);
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(256) k_start(long n, const double* __restrict_
 
 // reset the lockstep counters before k_start
 __global__ void k_reset(PcgState st) {
+  pdl_enter();
   st.iter[0] = 1;
   st.iter[1] = 0;
   *st.ticket = 0u;
@@ -255,24 +261,28 @@ __global__ void k_reset(PcgState st) {
 
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) k_convert(long n, const TA* __restrict__ a, TB* __restrict__ b) {
+  pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     b[i] = TB(a[i]);
 }
 
 __global__ void __launch_bounds__(256) k_axpy(long n, double alpha, const double* __restrict__ x,
                                               double* __restrict__ y) {
+  pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     y[i] += alpha * x[i];
 }
 
 __global__ void __launch_bounds__(256) k_sub_mean(long n, double* __restrict__ b, const double* __restrict__ part,
                                                   int np, double count) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const double mu = sum_partials(part, np, sred) / count;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] -= mu;
 }
 
 __global__ void __launch_bounds__(256) k_norm2(long n, const double* __restrict__ x, double* __restrict__ part) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   double a = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -285,6 +295,7 @@ __global__ void __launch_bounds__(256) k_norm2(long n, const double* __restrict_
 // column) written as 0
 __global__ void __launch_bounds__(256) k_stack_in(const double* const* __restrict__ srcs, const double* one,
                                                   double* __restrict__ stack, int rows, int Nx, long seg_len) {
+  pdl_enter();
   const int k = blockIdx.y;
   const double* src = srcs ? srcs[k] : one;
   const long per = (long)(rows + 1) * Nx;
@@ -297,6 +308,7 @@ __global__ void __launch_bounds__(256) k_stack_in(const double* const* __restric
 
 __global__ void __launch_bounds__(256) k_stack_out(const double* __restrict__ stack, double* const* __restrict__ dsts,
                                                    double* one, int rows, int Nx, long seg_len) {
+  pdl_enter();
   const int k = blockIdx.y;
   double* dst = dsts ? dsts[k] : one;
   const long per = (long)(rows + 1) * Nx;
@@ -310,7 +322,10 @@ cudaError_t launch_stack_in(const double* const* srcs, const double* one, double
                             long seg_len, cudaStream_t s) {
   const long per = (long)(rows + 1) * Nx;
   dim3 grid((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, 1024)), nmem);
-  k_stack_in<<<grid, 256, 0, s>>>(srcs, one, stack, rows, Nx, seg_len);
+  {
+    const cudaError_t e_ = launch_pdl(k_stack_in, dim3(grid), dim3(256), 0, s, srcs, one, stack, rows, Nx, seg_len);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -318,7 +333,10 @@ cudaError_t launch_stack_out(const double* stack, double* const* dsts, double* o
                              long seg_len, cudaStream_t s) {
   const long per = (long)(rows + 1) * Nx;
   dim3 grid((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, 1024)), nmem);
-  k_stack_out<<<grid, 256, 0, s>>>(stack, dsts, one, rows, Nx, seg_len);
+  {
+    const cudaError_t e_ = launch_pdl(k_stack_out, dim3(grid), dim3(256), 0, s, stack, dsts, one, rows, Nx, seg_len);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -335,60 +353,90 @@ cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, 
                                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
                                        const double* z) {
   dim3 grid(chunk_grid(st), st.nb);
-  k_update_ur_check<<<grid, 256, 0, s>>>(n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z);
+  {
+    const cudaError_t e_ = launch_pdl(k_update_ur_check, dim3(grid), dim3(256), 0, s, n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot2_beta(long n, const double* z, const double* r, const double* q, double* part, PcgState st,
                              cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
-  k_dot2_beta<<<grid, 256, 0, s>>>(n, z, r, q, part, st);
+  {
+    const cudaError_t e_ = launch_pdl(k_dot2_beta, dim3(grid), dim3(256), 0, s, n, z, r, q, part, st);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot2(long n, const double* z, const double* r, const double* r_old, double* part, PcgState st,
                         cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
-  k_dot2<<<grid, 256, 0, s>>>(n, z, r, r_old, part, st);
+  {
+    const cudaError_t e_ = launch_pdl(k_dot2, dim3(grid), dim3(256), 0, s, n, z, r, r_old, part, st);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double* r, double* r_old,
                                 const double* part, PcgState st, cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
-  k_update_p<<<grid, 256, 0, s>>>(n, z, p, r, r_old, part, grid.x, st);
+  {
+    const cudaError_t e_ = launch_pdl(k_update_p, dim3(grid), dim3(256), 0, s, n, z, p, r, r_old, part, grid.x, st);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_start(long n, const double* z, const double* r, double* p, double* r_old,
                              const double* part_zr, const double* part_rr, int nrr, PcgState st, double tol,
                              cudaStream_t s) {
-  k_reset<<<1, 1, 0, s>>>(st);
+  {
+    const cudaError_t e_ = launch_pdl(k_reset, dim3(1), dim3(1), 0, s, st);
+    if (e_ != cudaSuccess) return e_;
+  }
   dim3 grid(chunk_grid(st), st.nb);
-  k_start<<<grid, 256, 0, s>>>(n, z, r, p, r_old, part_zr, grid.x, part_rr, nrr, st, tol);
+  {
+    const cudaError_t e_ = launch_pdl(k_start, dim3(grid), dim3(256), 0, s, n, z, r, p, r_old, part_zr, grid.x, part_rr, nrr, st, tol);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 template <typename TA, typename TB>
 cudaError_t launch_convert(long n, const TA* a, TB* b, cudaStream_t s) {
-  k_convert<TA, TB><<<elementwise_grid(n), 256, 0, s>>>(n, a, b);
+  {
+    const cudaError_t e_ = launch_pdl(k_convert<TA, TB>, dim3(elementwise_grid(n)), dim3(256), 0, s, n, a, b);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 template cudaError_t launch_convert<double, float>(long, const double*, float*, cudaStream_t);
 template cudaError_t launch_convert<float, double>(long, const float*, double*, cudaStream_t);
 
 cudaError_t launch_axpy(long n, double alpha, const double* x, double* y, cudaStream_t s) {
-  k_axpy<<<elementwise_grid(n), 256, 0, s>>>(n, alpha, x, y);
+  {
+    const cudaError_t e_ = launch_pdl(k_axpy, dim3(elementwise_grid(n)), dim3(256), 0, s, n, alpha, x, y);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub_mean(long n, double* b, const double* part, int np, cudaStream_t s) {
-  k_sub_mean<<<elementwise_grid(n), 256, 0, s>>>(n, b, part, np, (double)n);
+  {
+    const cudaError_t e_ = launch_pdl(k_sub_mean, dim3(elementwise_grid(n)), dim3(256), 0, s, n, b, part, np, (double)n);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_norm2(long n, const double* x, double* part, cudaStream_t s) {
-  k_norm2<<<elementwise_grid(n), 256, 0, s>>>(n, x, part);
+  {
+    const cudaError_t e_ = launch_pdl(k_norm2, dim3(elementwise_grid(n)), dim3(256), 0, s, n, x, part);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
                                                const TF* __restrict__ f, T* __restrict__ out, int dot,
                                                double* __restrict__ part, const T* __restrict__ E,
                                                T* __restrict__ uout, PcgFuse pf) {
+  pdl_enter();
   using Tl = Tile<P>;
   constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
                                                   const T* __restrict__ f, T* __restrict__ out, int dot,
                                                   double* __restrict__ part, const T* __restrict__ E,
                                                   T* __restrict__ uout, PcgFuse pf) {
+  pdl_enter();
   using Q = EOTile<P>;
   constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, EO = Q::EO, NE = Q::NE,
                 NV = Q::NV;
@@ -352,6 +354,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_var_local(DirView<T> dx, DirView<T> dy, VarView<T> v,
                                                    const T* __restrict__ u) {
+  pdl_enter();
   constexpr int NP = P + 1, NN = NP * NP;
   __shared__ T sU[NN], sD[NN], sA[NN], sB[NN];
   const int ex = blockIdx.x, ey = blockIdx.y;
@@ -391,6 +394,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_var_gather(DirView<T> dx, DirView<T> dy, const T* __restrict__ E,
                                                     const T* __restrict__ u, const T* __restrict__ f,
                                                     T* __restrict__ out, int dot, double* __restrict__ part) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const int p = dx.p, np1 = p + 1, nn = np1 * np1;
   const long n = (long)dx.N * dy.N;
@@ -430,12 +434,16 @@ __global__ void __launch_bounds__(256) k_var_gather(DirView<T> dx, DirView<T> dy
 template <typename T, int P>
 cudaError_t var_p(const DirView<T>& dx, const DirView<T>& dy, const VarView<T>& v, const T* u, cudaStream_t s) {
   dim3 grid(dx.n, dy.n);
-  k_var_local<T, P><<<grid, 256, 0, s>>>(dx, dy, v, u);
+  {
+    const cudaError_t e_ = launch_pdl(k_var_local<T, P>, dim3(grid), dim3(256), 0, s, dx, dy, v, u);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double> dy, const double* __restrict__ f,
                                                double* __restrict__ b, double* __restrict__ part) {
+  pdl_enter();
   __shared__ double sred[kRedThreads];
   const long n = (long)dx.N * dy.N;
   double acc = 0.0;
@@ -461,12 +469,18 @@ cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, cons
     const size_t sm = apply_eo_smem<T, P>();
     cudaError_t e = allow_smem(k_apply_eo<T, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply_eo<T, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout, pf);
+    {
+      const cudaError_t e_ = launch_pdl(k_apply_eo<T, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout, pf);
+      if (e_ != cudaSuccess) return e_;
+    }
   } else {
     const size_t sm = apply_smem<T, P>();
     cudaError_t e = allow_smem(k_apply<T, TF, P>, sm);
     if (e != cudaSuccess) return e;
-    k_apply<T, TF, P><<<grid, 256, sm, s>>>(dx, dy, u, f, out, dot, part, E, uout, pf);
+    {
+      const cudaError_t e_ = launch_pdl(k_apply<T, TF, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout, pf);
+      if (e_ != cudaSuccess) return e_;
+    }
   }
   return cudaGetLastError();
 }
@@ -504,7 +518,10 @@ cudaError_t launch_apply_var(const DirView<T>& dx, const DirView<T>& dy, const V
   const long n = (long)dx.N * dy.N;
   const int grid = (int)std::max<long>(1, std::min<long>((n + 255) / 256, 4 * 152));
   if (nparts) *nparts = grid;
-  k_var_gather<T><<<grid, 256, 0, s>>>(dx, dy, v.E, u, f, out, dot, part);
+  {
+    const cudaError_t e_ = launch_pdl(k_var_gather<T>, dim3(grid), dim3(256), 0, s, dx, dy, v.E, u, f, out, dot, part);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -528,7 +545,10 @@ cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, co
                         double* part, int* nparts, cudaStream_t s) {
   const int grid = 256;
   if (nparts) *nparts = grid;
-  k_mass<<<grid, kRedThreads, 0, s>>>(dx, dy, f, b, part);
+  {
+    const cudaError_t e_ = launch_pdl(k_mass, dim3(grid), dim3(kRedThreads), 0, s, dx, dy, f, b, part);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

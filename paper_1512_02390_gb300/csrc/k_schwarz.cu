@@ -23,6 +23,7 @@ namespace {
 template <typename T, typename TIn>
 __global__ void __launch_bounds__(256) k_sweep_simt(DirView<T> dx, DirView<T> dy, const TIn* __restrict__ r,
                                                     T* __restrict__ E, const T* __restrict__ nu_inv) {
+  pdl_enter();
   const int ex = blockIdx.x, ey = blockIdx.y;
   const int m = dx.m, mm = m * m, p = dx.p, no = dx.n_o;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,6 +202,7 @@ template <typename TIn, int MODE, int MP>
 __global__ void __launch_bounds__(32 * kMmaWarps) k_sweep_mma(DirView<float> dx, DirView<float> dy,
                                                               const TIn* __restrict__ r, float* __restrict__ E,
                                                               const float* __restrict__ nu_inv, int nsub) {
+  pdl_enter();
   using Q = MmaSmem<MP>;
   constexpr int SA = Q::SA;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -306,7 +308,10 @@ cudaError_t sweep_mma_launch(const DirView<float>& dx, const DirView<float>& dy,
   // the next subdomain has the same type
   const int per = kMmaWarps * std::max(1, spw);
   const int grid = std::max(1, std::min((nsub + per - 1) / per, 152 * 16));
-  k_sweep_mma<TIn, MODE, MP><<<grid, 32 * kMmaWarps, sm, s>>>(dx, dy, r, E, nu_inv, nsub);
+  {
+    const cudaError_t e_ = launch_pdl(k_sweep_mma<TIn, MODE, MP>, dim3(grid), dim3(32 * kMmaWarps), sm, s, dx, dy, r, E, nu_inv, nsub);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -322,6 +327,7 @@ cudaError_t sweep_mma(const DirView<float>& dx, const DirView<float>& dy, const 
 template <typename T, typename TOut>
 __global__ void __launch_bounds__(256) k_scatter(DirView<T> dx, DirView<T> dy, const T* __restrict__ E,
                                                  TOut* __restrict__ u, int accum) {
+  pdl_enter();
   const int p = dx.p, no = dx.n_o, m = dx.m, mm = m * m;
   const long n = (long)dx.N * dy.N;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
@@ -366,7 +372,10 @@ cudaError_t launch_sweep(const DirView<T>& dx, const DirView<T>& dy, const TIn* 
   cudaError_t e = allow_smem(k_sweep_simt<T, TIn>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid(dx.n, dy.n);
-  k_sweep_simt<T, TIn><<<grid, 256, sm, s>>>(dx, dy, r, E, nu_inv);
+  {
+    const cudaError_t e_ = launch_pdl(k_sweep_simt<T, TIn>, dim3(grid), dim3(256), sm, s, dx, dy, r, E, nu_inv);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -375,7 +384,10 @@ cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* 
                            cudaStream_t s) {
   const long n = (long)dx.N * dy.N;
   const int grid = (int)std::min<long>((n + 255) / 256, 4 * 152 * 8);
-  k_scatter<T, TOut><<<grid, 256, 0, s>>>(dx, dy, E, u, accum ? 1 : 0);
+  {
+    const cudaError_t e_ = launch_pdl(k_scatter<T, TOut>, dim3(grid), dim3(256), 0, s, dx, dy, E, u, accum ? 1 : 0);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

@@ -192,6 +192,7 @@ template <typename TIn, int MODE, int NPC>
 __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirView<float> dy,
                                                          const TIn* __restrict__ r, float* __restrict__ E,
                                                          const float* __restrict__ nu_inv, TcWork wk, TcLay L) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
   unsigned char* sB = smem + L.a_bytes;  // tables B1 = S_x^T, B2 = S_y^T, B3 = S_y, B4 = S_x (N x K rows)
@@ -457,7 +458,10 @@ cudaError_t sweep_tc_launch(const DirView<float>& dx, const DirView<float>& dy, 
   cudaError_t e = allow_smem(k_sweep_tc<TIn, MODE, NPC>, smem);
   if (e != cudaSuccess) return e;
   const int grid = std::min(wk.ngroups, 152 * 8);
-  k_sweep_tc<TIn, MODE, NPC><<<grid, kTcThreads, smem, s>>>(dx, dy, r, E, nu_inv, wk, L);
+  {
+    const cudaError_t e_ = launch_pdl(k_sweep_tc<TIn, MODE, NPC>, dim3(grid), dim3(kTcThreads), smem, s, dx, dy, r, E, nu_inv, wk, L);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ template <typename T, int PF>
 __global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                   const T* __restrict__ J, const T* __restrict__ rf,
                                                   T* __restrict__ fc) {
+  pdl_enter();
   using Q = TT<PF>;
   constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
   constexpr int LN = TNF + PF + 1, LP = LN + 1, TP = TNC + 2;
@@ -104,6 +105,7 @@ template <typename T, typename TOut, int PF>
 __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                  const T* __restrict__ J, const T* __restrict__ uc,
                                                  const T* in, TOut* out) {
+  pdl_enter();
   using Q = TT<PF>;
   constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
   constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
@@ -165,6 +167,7 @@ enum CoarseStep { kStep1 = 0, kStep2 = 1, kStep3 = 2, kStep4 = 3 };
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, const T* __restrict__ f0,
                                                      T* __restrict__ u0) {
+  pdl_enter();
   constexpr int TM = 8, TK = 4;
   __shared__ double sred[kRedThreads];
   __shared__ double part[TK][TM][TM + 1];
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(CoarseView c, int step, con
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_dense(CoarseView c, const double* __restrict__ Binv,
                                                       const T* __restrict__ f0, T* __restrict__ u0) {
+  pdl_enter();
   const int n = c.nux * c.nuy;
   const int fy0 = c.firsty + blockIdx.y * c.block_rows;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -280,7 +284,10 @@ cudaError_t restrict_p(const DirView<T>& fx, const DirView<T>& fy, const DirView
   cudaError_t e = allow_smem(k_restrict<T, PF>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((cx.n + Q::TE - 1) / Q::TE, (cy.n + Q::TE - 1) / Q::TE);
-  k_restrict<T, PF><<<grid, 256, sm, s>>>(fx, fy, cx, cy, J, rf, fc);
+  {
+    const cudaError_t e_ = launch_pdl(k_restrict<T, PF>, dim3(grid), dim3(256), sm, s, fx, fy, cx, cy, J, rf, fc);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -293,7 +300,10 @@ cudaError_t prolong_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<
   cudaError_t e = allow_smem(k_prolong<T, TOut, PF>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((fx.n + Q::TE - 1) / Q::TE, (fy.n + Q::TE - 1) / Q::TE);
-  k_prolong<T, TOut, PF><<<grid, 256, sm, s>>>(fx, fy, cx, cy, J, uc, in, out);
+  {
+    const cudaError_t e_ = launch_pdl(k_prolong<T, TOut, PF>, dim3(grid), dim3(256), sm, s, fx, fy, cx, cy, J, uc, in, out);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -357,6 +367,7 @@ __device__ __forceinline__ void coarse_gemm32(int K, LA la, LB lb, EP ep) {
 
 __global__ void __launch_bounds__(1024) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
                                                       float* __restrict__ u0) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_c32[];
   float* Sx = reinterpret_cast<float*>(smem_c32);  // 4 x 64 x 65 floats: S_x, S_y, W1, W2
   float* Sy = Sx + kC32 * kC32P;
@@ -427,7 +438,11 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
       const size_t sm = 4 * sizeof(float) * kC32 * kC32P;
       cudaError_t e = allow_smem(k_coarse_fdm32, sm);
       if (e != cudaSuccess) return e;
-      k_coarse_fdm32<<<std::max(1, c.batch), 1024, sm, s>>>(c, f0, u0);
+      const int nblk = std::max(1, c.batch);
+      {
+        const cudaError_t e_ = launch_pdl(k_coarse_fdm32, dim3(nblk), dim3(1024), sm, s, c, f0, u0);
+        if (e_ != cudaSuccess) return e_;
+      }
       return cudaGetLastError();
     }
   }
@@ -436,7 +451,10 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
   cudaError_t e0 = allow_smem(k_coarse_gemm<T>, sm);
   if (e0 != cudaSuccess) return e0;
   for (int step = kStep1; step <= kStep4; ++step) {
-    k_coarse_gemm<T><<<grid, 256, sm, s>>>(c, step, f0, u0);
+    {
+      const cudaError_t e_ = launch_pdl(k_coarse_gemm<T>, dim3(grid), dim3(256), sm, s, c, step, f0, u0);
+      if (e_ != cudaSuccess) return e_;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -446,7 +464,11 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
 template <typename T>
 cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s) {
   const int n = c.nux * c.nuy;
-  k_coarse_dense<T><<<dim3((n + 7) / 8, std::max(1, c.batch)), 256, 0, s>>>(c, Binv, f0, u0);
+  const dim3 grid((n + 7) / 8, std::max(1, c.batch));
+  {
+    const cudaError_t e_ = launch_pdl(k_coarse_dense<T>, dim3(grid), dim3(256), 0, s, c, Binv, f0, u0);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_dense<double>(const CoarseView&, const double*, const double*, double*, cudaStream_t);
