@@ -119,14 +119,14 @@ namespace sem {
 // Programmatic dependent launch (sm_90+).  Every kernel of the solver opens
 // with pdl_enter(): wait until the kernel before it in the stream has completed
 // and its writes are visible (returns at once when the launch carried no
-// programmatic dependency), then allow the next kernel to start launching.
-// launch_pdl() enqueues with the programmatic-serialization attribute, so the
-// next kernel's launch and CTA scheduling overlap this kernel's tail while no
-// kernel reads anything before its predecessor has finished.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// programmatic dependency).  launch_pdl() enqueues with the programmatic-
+// serialization attribute, so the launch of the next kernel is prepared while
+// this one finishes; no kernel reads anything before its predecessor has
+// completed.  No kernel triggers its dependents early: measured on the 64 x 64,
+// p = 16 solve, an early trigger let waiting CTAs of the next kernel hold SM
+// resources (2.71 ms per solve against 2.56 ms without it, 2.58 ms with the
+// attribute off).
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
