@@ -178,7 +178,7 @@ size_t apply_eo_smem() {
   const size_t t = (size_t)Q::LN * Q::LP                     // staged u
                    + 2 * (Q::TE + 1) * Q::EO                  // E/O per element, x and y
                    + (size_t)(Q::TE + 1) * Q::NV * Q::TN      // e/o vectors of one direction
-                   + 2 * (size_t)Q::TN * (Q::TE + 1) * Q::NP  // element-local row / column products
+                   + (size_t)Q::TN * (Q::TE + 1) * Q::NP      // x products (y products reuse the staged tile)
                    + 2 * (Q::TN + 1);                        // mass diagonals
   return sizeof(T) * t + sizeof(double) * kRedThreads;
 }
@@ -261,8 +261,10 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   T* eoy = eox + (TE + 1) * EO;
   T* ev = eoy + (TE + 1) * EO;                // (TE+1) x NV x TN, reused by x then y
   T* xb = ev + (TE + 1) * NV * TN;            // [row][slot][a]  x-products
-  T* yb = xb + TN * (TE + 1) * NP;            // [slot][b][col]  y-products
-  T* sMx = yb + TN * (TE + 1) * NP;
+  T* yb = su;                                 // [slot][b][col]  y-products, over the staged tile once
+                                              // the y e/o vectors are formed
+  static_assert(TN * (TE + 1) * NP <= LN * LP, "y products must fit in the staged tile");
+  T* sMx = xb + TN * (TE + 1) * NP;
   T* sMy = sMx + (TN + 1);
   double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
 
@@ -303,6 +305,22 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
   }
   __syncthreads();
+  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
+  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  // staged values of this thread's owned nodes, kept for the dot product and
+  // the assembled-correction output (the y products overwrite the tile)
+  constexpr int KOWN = ((TN + 1) * (TN + 1) + 255) / 256;
+  T own[KOWN];
+#pragma unroll
+  for (int q = 0; q < KOWN; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    own[q] = T(0);
+    if (idx < ownx * owny) {
+      const int jy = idx / ownx, ix = idx - jy * ownx;
+      own[q] = su[(jy + P) * LP + ix + P];
+    }
+  }
   form_eo<T, P, true>(su, ev);
   __syncthreads();
   eo_products<T, P, true>(eox, ev, xb);
@@ -312,11 +330,11 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   eo_products<T, P, false>(eoy, ev, yb);
   __syncthreads();
 
-  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
-  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
-  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
   double acc = 0.0;
-  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
+#pragma unroll
+  for (int q = 0; q < KOWN; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    if (idx >= ownx * owny) break;
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
@@ -335,8 +353,8 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
       if (f) val = T(f[o]) - val;
     }
     out[o] = val;
-    if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
-    if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
+    if (uout) uout[o] = wall ? T(0) : own[q];
+    if (dot == 1) acc += (double)own[q] * (double)val;
     else if (dot == 2) acc += (double)val * (double)val;
   }
   if (dot) {
