@@ -14,6 +14,8 @@
 // lam_x^T)] S_x^T, FP64.  For a periodic (singular) A_0 the right side is
 // projected to zero mean, the (0, 0) eigen-pair is dropped and the result is
 // made orthogonal to the constants: the Moore-Penrose solution A_0^+ f_0.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -337,53 +339,36 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 
 // The same exact coarse solve, u_0 = A_0^+ f_0 by the global fast
 // diagonalisation U = S_y [(S_y^T F S_x) ./ (lambda_y + lambda_x^T)] S_x^T,
-// in FP32 by ONE CTA per problem for coarse grids of at most 64 x 64
-// unknowns (the mixed-precision V-cycle): the four products run back to back
-// in shared memory, each of 1024 threads holding a 2 x 2 block of the 64 x 64
-// result.
-constexpr int kC32 = 64, kC32P = 65;  // tile and padded pitch (floats)
+// in FP32 for coarse grids of at most 64 x 64 unknowns (the mixed-precision
+// V-cycle) by ONE thread-block cluster of 8 CTAs per problem: CTA c owns rows
+// 8c .. 8c+7 of every product.  The first two products and the scaling need
+// only the CTA's own rows; the third contracts over all rows, which each CTA
+// reads from its peers' shared memory (distributed shared memory) after a
+// cluster barrier.
+constexpr int kC32 = 64, kC32P = 65, kCl = 8, kClRows = kC32 / kCl;  // tile, pitch, cluster, rows per CTA
 
-template <typename LA, typename LB, typename EP>
-__device__ __forceinline__ void coarse_gemm32(int K, LA la, LB lb, EP ep) {
-  const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
-  float acc[2][2] = {};
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    float a[2], b[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) a[i] = la(tr + 32 * i, k);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) b[j] = lb(k, tc + 32 * j);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) ep(tr + 32 * i, tc + 32 * j, acc[i][j]);
-}
-
-__global__ void __launch_bounds__(1024) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
-                                                      float* __restrict__ u0) {
+__global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
+                                                     float* __restrict__ u0) {
   pdl_enter();
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char smem_c32[];
-  float* Sx = reinterpret_cast<float*>(smem_c32);  // 4 x 64 x 65 floats: S_x, S_y, W1, W2
-  float* Sy = Sx + kC32 * kC32P;
-  float* W1 = Sy + kC32 * kC32P;
-  float* W2 = W1 + kC32 * kC32P;
+  float* Sx = reinterpret_cast<float*>(smem_c32);  // 64 x 65
+  float* Sy = Sx + kC32 * kC32P;                    // 64 x 65
+  float* F = Sy + kC32 * kC32P;                     // 64 x 65: the right side, then the gathered W1
+  float* Wa = F + kC32 * kC32P;                     // 8 x 65: own rows of S_y^T F, then of S_y W1
+  float* Wb = Wa + kClRows * kC32P;                 // 8 x 65: own rows of the scaled W1 (read by peers)
   __shared__ float lx[kC32], ly[kC32], cx[kC32], cy[kC32];
-  __shared__ double sred[1024];  // block_sum over all 1024 threads
+  __shared__ double sred[kRedThreads];
   const int nux = c.nux, nuy = c.nuy, t = threadIdx.x;
-  const int fy0 = c.firsty + blockIdx.x * c.block_rows;
+  const int r0 = rank * kClRows;
+  const int fy0 = c.firsty + (blockIdx.x / kCl) * c.block_rows;
   for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
     const int a = idx / kC32, b = idx - a * kC32;
     Sx[a * kC32P + b] = (a < nux && b < nux) ? (float)c.Sx[a * nux + b] : 0.f;
     Sy[a * kC32P + b] = (a < nuy && b < nuy) ? (float)c.Sy[a * nuy + b] : 0.f;
-    float fv = 0.f;
-    if (a < nuy && b < nux) fv = f0[(long)(fy0 + a) * c.Nx + c.firstx + b];
-    W1[a * kC32P + b] = fv;
+    F[a * kC32P + b] = (a < nuy && b < nux) ? f0[(long)(fy0 + a) * c.Nx + c.firstx + b] : 0.f;
   }
   for (int i = t; i < kC32; i += blockDim.x) {
     lx[i] = i < nux ? (float)c.lx[i] : 1.f;
@@ -393,57 +378,99 @@ __global__ void __launch_bounds__(1024) k_coarse_fdm32(CoarseView c, const float
   }
   __syncthreads();
   float shift = 0.f;
-  if (c.periodic) {  // right side projected to zero mean
+  if (c.periodic) {  // right side projected to zero mean (every CTA computes it)
     double acc = 0.0;
-    for (int idx = t; idx < nux * nuy; idx += blockDim.x) acc += W1[(idx / nux) * kC32P + idx % nux];
+    for (int idx = t; idx < nux * nuy; idx += blockDim.x) acc += F[(idx / nux) * kC32P + idx % nux];
     shift = (float)(block_sum(acc, sred) / ((double)nux * nuy));
-    __syncthreads();
-    for (int idx = t; idx < nux * nuy; idx += blockDim.x) W1[(idx / nux) * kC32P + idx % nux] -= shift;
-    __syncthreads();
   }
-  // W2 = S_y^T F
-  coarse_gemm32(nuy, [&](int r, int k) { return Sy[k * kC32P + r]; }, [&](int k, int q) { return W1[k * kC32P + q]; },
-                [&](int r, int q, float v) { W2[r * kC32P + q] = v; });
+  // thread t: own row rr = t / 32, columns q = t % 32 and t % 32 + 32
+  const int rr = t >> 5, q0 = t & 31, row = r0 + rr;
+  {  // Wa = rows of S_y^T (F - shift)
+    float a0 = 0.f, a1 = 0.f;
+    for (int j = 0; j < nuy; ++j) {
+      const float s = Sy[j * kC32P + row];
+      a0 = fmaf(s, F[j * kC32P + q0] - shift, a0);
+      a1 = fmaf(s, F[j * kC32P + q0 + 32] - shift, a1);
+    }
+    Wa[rr * kC32P + q0] = a0;
+    Wa[rr * kC32P + q0 + 32] = a1;
+  }
   __syncthreads();
-  // W1 = (W2 S_x) ./ (lambda_y + lambda_x^T); the null pair dropped when periodic
-  coarse_gemm32(nux, [&](int r, int k) { return W2[r * kC32P + k]; }, [&](int k, int q) { return Sx[k * kC32P + q]; },
-                [&](int r, int q, float v) {
-                  W1[r * kC32P + q] = (c.periodic && r == 0 && q == 0) ? 0.f : v / (ly[r] + lx[q]);
-                });
-  __syncthreads();
+  {  // Wb = rows of (Wa S_x) ./ (lambda_y + lambda_x^T); the null pair dropped when periodic
+    float a0 = 0.f, a1 = 0.f;
+    for (int i = 0; i < nux; ++i) {
+      const float w = Wa[rr * kC32P + i];
+      a0 = fmaf(w, Sx[i * kC32P + q0], a0);
+      a1 = fmaf(w, Sx[i * kC32P + q0 + 32], a1);
+    }
+    Wb[rr * kC32P + q0] = (c.periodic && row == 0 && q0 == 0) ? 0.f : a0 / (ly[row] + lx[q0]);
+    Wb[rr * kC32P + q0 + 32] = a1 / (ly[row] + lx[q0 + 32]);
+  }
+  cluster.sync();
+  // gather every CTA's rows of W1 (over the right side, no longer needed)
+  for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
+    const int a = idx / kC32, b = idx - a * kC32;
+    const float* peer = cluster.map_shared_rank(Wb, a / kClRows);
+    F[a * kC32P + b] = peer[(a % kClRows) * kC32P + b];
+  }
+  cluster.sync();  // peers are done reading this CTA's rows
   float mean_u = 0.f;
   if (c.periodic) {  // mean(U) = c_y^T W1 c_x / N: the solution is returned with zero mean
     double acc = 0.0;
     for (int idx = t; idx < nux * nuy; idx += blockDim.x) {
       const int a = idx / nux, b = idx - a * nux;
-      acc += (double)cy[a] * W1[a * kC32P + b] * cx[b];
+      acc += (double)cy[a] * F[a * kC32P + b] * cx[b];
     }
     mean_u = (float)(block_sum(acc, sred) / ((double)nux * nuy));
   }
-  // W2 = S_y W1
-  coarse_gemm32(nuy, [&](int r, int k) { return Sy[r * kC32P + k]; }, [&](int k, int q) { return W1[k * kC32P + q]; },
-                [&](int r, int q, float v) { W2[r * kC32P + q] = v; });
+  {  // Wa = rows of S_y W1
+    float a0 = 0.f, a1 = 0.f;
+    for (int a = 0; a < nuy; ++a) {
+      const float s = Sy[row * kC32P + a];
+      a0 = fmaf(s, F[a * kC32P + q0], a0);
+      a1 = fmaf(s, F[a * kC32P + q0 + 32], a1);
+    }
+    Wa[rr * kC32P + q0] = a0;
+    Wa[rr * kC32P + q0 + 32] = a1;
+  }
   __syncthreads();
-  // U = W2 S_x^T
-  coarse_gemm32(nux, [&](int r, int k) { return W2[r * kC32P + k]; }, [&](int k, int q) { return Sx[q * kC32P + k]; },
-                [&](int r, int q, float v) {
-                  if (r < nuy && q < nux) u0[(long)(fy0 + r) * c.Nx + c.firstx + q] = v - mean_u;
-                });
+  {  // U = rows of Wa S_x^T
+    float a0 = 0.f, a1 = 0.f;
+    for (int b = 0; b < nux; ++b) {
+      const float w = Wa[rr * kC32P + b];
+      a0 = fmaf(w, Sx[q0 * kC32P + b], a0);
+      a1 = fmaf(w, Sx[(q0 + 32) * kC32P + b], a1);
+    }
+    if (row < nuy) {
+      float* out = u0 + (long)(fy0 + row) * c.Nx + c.firstx;
+      if (q0 < nux) out[q0] = a0 - mean_u;
+      if (q0 + 32 < nux) out[q0 + 32] = a1 - mean_u;
+    }
+  }
 }
 
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (c.nux <= kC32 && c.nuy <= kC32) {
-      const size_t sm = 4 * sizeof(float) * kC32 * kC32P;
+      const size_t sm = sizeof(float) * (3 * kC32 + 2 * kClRows) * kC32P;
       cudaError_t e = allow_smem(k_coarse_fdm32, sm);
       if (e != cudaSuccess) return e;
-      const int nblk = std::max(1, c.batch);
-      {
-        const cudaError_t e_ = launch_pdl(k_coarse_fdm32, dim3(nblk), dim3(1024), sm, s, c, f0, u0);
-        if (e_ != cudaSuccess) return e_;
-      }
-      return cudaGetLastError();
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kCl * std::max(1, c.batch));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = sm;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[2];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kCl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[1].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 2;
+      return cudaLaunchKernelEx(&cfg, k_coarse_fdm32, c, f0, u0);
     }
   }
   dim3 grid((c.nux + 7) / 8, (c.nuy + 7) / 8, std::max(1, c.batch));

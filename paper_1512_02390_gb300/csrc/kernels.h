@@ -103,8 +103,8 @@ struct CoarseView {
   double* T1;  // batch x nuy x nux scratch (also holds S_y T2)
   double* T2;  // batch x nuy x nux scratch
 };
-// FP64: four multi-CTA products; FP32 with at most 64 x 64 unknowns: one CTA
-// per problem runs all four
+// FP64: four multi-CTA products; FP32 with at most 64 x 64 unknowns: one
+// cluster of 8 CTAs per problem runs all four
 template <typename T>
 cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t s);
 inline int coarse_launches(const CoarseView& c, bool fp32) { return (fp32 && c.nux <= 64 && c.nuy <= 64) ? 1 : 4; }
