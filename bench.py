@@ -410,7 +410,7 @@ def run_ours(args):
                          "final_rel_residual": res.res / res.res0 if res.res0 else 0.0,
                          "rel_error_vs_fp64": err,
                          "launch_shapes": {"p%d" % (1 << l): {"fuse": t["fuse"], "tc": t["tc"], "spw": t["spw"],
-                                                              "us": round(t["us"], 2)}
+                                                              "eo": t["eo"], "us": round(t["us"], 2)}
                                            for l, t in S.tune.items()}}
         if not is_head:
             variants[key]["class_ms_per_solve"] = {k: round(v[0] / 2, 4) for k, v in vprof.items()}

@@ -242,7 +242,10 @@ int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
  *         one subdomain per warp at a time.
  *   spw   mma.sync sweep: subdomains per warp (sets the grid size; a warp
  *         that loops reuses its factor tables).
- * Defaults (no tuning): fuse 0, tc 1 where available, spw 1.  sem_autotune (sync) times every
+ *   eo    form of the level residual: -1 the even-odd sum factorisation in
+ *         FP64 and the plain one in FP32, 0 plain, 1 even-odd (p_l >= 4); the
+ *         two forms round differently (the results agree to the precision).
+ * Defaults (no tuning): fuse 0, tc 1 where available, spw 1, eo -1.  sem_autotune (sync) times every
  * candidate on the handle's own level vectors (best of 3 x 10 steps, CUDA
  * events) and keeps the fastest; with cache_path != NULL it first looks each
  * level up in that JSON-lines file (key: device name, p_l, n_o, precision,
@@ -255,6 +258,7 @@ typedef struct sem_level_tune {
   int32_t spw;          /* 1..64 */
   int32_t tc;           /* 0 or 1 */
   int32_t tc_available; /* sem_get_tune: 1 if the level has tcgen05 stacks (ignored by sem_set_tune) */
+  int32_t eo;           /* -1, 0 or 1 */
   double us;            /* measured time of the level's down-sweep step (microseconds; 0 if not timed) */
 } sem_level_tune;
 int sem_autotune(sem_handle* h, const char* cache_path, void* stream);

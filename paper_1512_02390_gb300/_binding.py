@@ -65,7 +65,7 @@ class sem_level_info(ctypes.Structure):
 
 class sem_level_tune(ctypes.Structure):
     _fields_ = [("fuse", ctypes.c_int32), ("spw", ctypes.c_int32), ("tc", ctypes.c_int32),
-                ("tc_available", ctypes.c_int32), ("us", ctypes.c_double)]
+                ("tc_available", ctypes.c_int32), ("eo", ctypes.c_int32), ("us", ctypes.c_double)]
 
 
 class sem_sweep_tables(ctypes.Structure):
@@ -370,11 +370,11 @@ def sem_get_tune(h, level: int):
     """dict(fuse, spw, tc, tc_available, us) of level `level` (1..log2 p)."""
     t = sem_level_tune()
     _check(load_library().sem_get_tune(h, int(level), ctypes.byref(t)))
-    return dict(fuse=t.fuse, spw=t.spw, tc=t.tc, tc_available=t.tc_available, us=t.us)
+    return dict(fuse=t.fuse, spw=t.spw, tc=t.tc, tc_available=t.tc_available, eo=t.eo, us=t.us)
 
 
-def sem_set_tune(h, level: int, fuse: int, spw: int = 1, tc: int = 0) -> None:
-    t = sem_level_tune(int(fuse), int(spw), int(tc), 0, 0.0)
+def sem_set_tune(h, level: int, fuse: int, spw: int = 1, tc: int = 0, eo: int = -1) -> None:
+    t = sem_level_tune(int(fuse), int(spw), int(tc), 0, int(eo), 0.0)
     _check(load_library().sem_set_tune(h, int(level), ctypes.byref(t)))
 
 

@@ -46,14 +46,21 @@ constexpr int kRedThreads = 256;
 
 // Deterministic block sum of one double per thread (fixed tree order).
 __device__ __forceinline__ double block_sum(double v, double* sbuf) {
-  const int t = threadIdx.x;
-  sbuf[t] = v;
+  // fixed-order tree: butterfly within each warp (lane 0's result is used),
+  // then warp 0 over the warp totals; blockDim.x a multiple of 32, sbuf >= 33
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sbuf[warp] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) sbuf[t] += sbuf[t + s];
-    __syncthreads();
+  if (warp == 0) {
+    double r = lane < nw ? sbuf[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) sbuf[32] = r;
   }
-  double r = sbuf[0];
+  __syncthreads();
+  const double r = sbuf[32];
   __syncthreads();
   return r;
 }

@@ -246,9 +246,9 @@ __device__ __forceinline__ void eo_products(const T* eo, const T* ev, T* dst_bas
   }
 }
 
-template <typename T, int P>
+template <typename T, typename TF, int P>
 __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
-                                                  const T* __restrict__ f, T* __restrict__ out, int dot,
+                                                  const TF* __restrict__ f, T* __restrict__ out, int dot,
                                                   double* __restrict__ part, const T* __restrict__ E,
                                                   T* __restrict__ uout, PcgFuse pf) {
   pdl_enter();
@@ -478,44 +478,41 @@ __global__ void __launch_bounds__(256) k_mass(DirView<double> dx, DirView<double
 
 template <typename T, typename TF, int P>
 cudaError_t apply_p(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
-                    double* part, int* nparts, cudaStream_t s, const T* E, T* uout, const PcgFuse& pf) {
+                    double* part, int* nparts, cudaStream_t s, const T* E, T* uout, const PcgFuse& pf, int eo) {
   using Tl = Tile<P>;
   dim3 grid((dx.n + Tl::TE - 1) / Tl::TE, (dy.n + Tl::TE - 1) / Tl::TE);
   if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
   if (nparts) *nparts = grid.x * grid.y;
-  if constexpr (std::is_same<T, double>::value && std::is_same<TF, double>::value && P >= 4) {
-    const size_t sm = apply_eo_smem<T, P>();
-    cudaError_t e = allow_smem(k_apply_eo<T, P>, sm);
-    if (e != cudaSuccess) return e;
-    {
-      const cudaError_t e_ = launch_pdl(k_apply_eo<T, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout, pf);
-      if (e_ != cudaSuccess) return e_;
-    }
-  } else {
-    const size_t sm = apply_smem<T, P>();
-    cudaError_t e = allow_smem(k_apply<T, TF, P>, sm);
-    if (e != cudaSuccess) return e;
-    {
-      const cudaError_t e_ = launch_pdl(k_apply<T, TF, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout, pf);
-      if (e_ != cudaSuccess) return e_;
+  // the even-odd form for P >= 4: always in FP64 (the FP64 pipe bounds it),
+  // on request in FP32 (eo = 1; the autotuner decides)
+  if constexpr (P >= 4) {  // below P = 4 the plain form only
+    if (eo == 1 || (eo < 0 && std::is_same<T, double>::value)) {
+      const size_t sm = apply_eo_smem<T, P>();
+      cudaError_t e = allow_smem(k_apply_eo<T, TF, P>, sm);
+      if (e != cudaSuccess) return e;
+      return launch_pdl(k_apply_eo<T, TF, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout,
+                        pf);
     }
   }
-  return cudaGetLastError();
+  const size_t sm = apply_smem<T, P>();
+  cudaError_t e = allow_smem(k_apply<T, TF, P>, sm);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_apply<T, TF, P>, dim3(grid), dim3(256), sm, s, dx, dy, u, f, out, dot, part, E, uout, pf);
 }
 
 }  // namespace
 
 template <typename T, typename TF>
 cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f, T* out, int dot,
-                         double* part, int* nparts, cudaStream_t s, const T* E, T* uout, PcgFuse pf) {
+                         double* part, int* nparts, cudaStream_t s, const T* E, T* uout, PcgFuse pf, int eo) {
   if (pf.z && !std::is_same<T, double>::value) return cudaErrorInvalidValue;
   switch (dx.p) {
-    case 1: return apply_p<T, TF, 1>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
-    case 2: return apply_p<T, TF, 2>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
-    case 4: return apply_p<T, TF, 4>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
-    case 8: return apply_p<T, TF, 8>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
-    case 16: return apply_p<T, TF, 16>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
-    case 32: return apply_p<T, TF, 32>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf);
+    case 1: return apply_p<T, TF, 1>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
+    case 2: return apply_p<T, TF, 2>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
+    case 4: return apply_p<T, TF, 4>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
+    case 8: return apply_p<T, TF, 8>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
+    case 16: return apply_p<T, TF, 16>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
+    case 32: return apply_p<T, TF, 32>(dx, dy, u, f, out, dot, part, nparts, s, E, uout, pf, eo);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -551,13 +548,13 @@ template cudaError_t launch_apply_var<float>(const DirView<float>&, const DirVie
 
 template cudaError_t launch_apply<double, double>(const DirView<double>&, const DirView<double>&, const double*,
                                                   const double*, double*, int, double*, int*, cudaStream_t,
-                                                  const double*, double*, PcgFuse);
+                                                  const double*, double*, PcgFuse, int);
 template cudaError_t launch_apply<float, float>(const DirView<float>&, const DirView<float>&, const float*,
                                                 const float*, float*, int, double*, int*, cudaStream_t, const float*,
-                                                float*, PcgFuse);
+                                                float*, PcgFuse, int);
 template cudaError_t launch_apply<float, double>(const DirView<float>&, const DirView<float>&, const float*,
                                                  const double*, float*, int, double*, int*, cudaStream_t,
-                                                 const float*, float*, PcgFuse);
+                                                 const float*, float*, PcgFuse, int);
 
 cudaError_t launch_mass(const DirView<double>& dx, const DirView<double>& dy, const double* f, double* b,
                         double* part, int* nparts, cudaStream_t s) {

@@ -366,15 +366,15 @@ __global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float*
   const int fy0 = c.firsty + (blockIdx.x / kCl) * c.block_rows;
   for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
     const int a = idx / kC32, b = idx - a * kC32;
-    Sx[a * kC32P + b] = (a < nux && b < nux) ? (float)c.Sx[a * nux + b] : 0.f;
-    Sy[a * kC32P + b] = (a < nuy && b < nuy) ? (float)c.Sy[a * nuy + b] : 0.f;
+    Sx[a * kC32P + b] = (a < nux && b < nux) ? c.Sx32[a * nux + b] : 0.f;
+    Sy[a * kC32P + b] = (a < nuy && b < nuy) ? c.Sy32[a * nuy + b] : 0.f;
     F[a * kC32P + b] = (a < nuy && b < nux) ? f0[(long)(fy0 + a) * c.Nx + c.firstx + b] : 0.f;
   }
   for (int i = t; i < kC32; i += blockDim.x) {
-    lx[i] = i < nux ? (float)c.lx[i] : 1.f;
-    ly[i] = i < nuy ? (float)c.ly[i] : 1.f;
-    cx[i] = (c.periodic && i < nux) ? (float)c.cx[i] : 0.f;
-    cy[i] = (c.periodic && i < nuy) ? (float)c.cy[i] : 0.f;
+    lx[i] = i < nux ? c.lx32[i] : 1.f;
+    ly[i] = i < nuy ? c.ly32[i] : 1.f;
+    cx[i] = (c.periodic && i < nux) ? c.cx32[i] : 0.f;
+    cy[i] = (c.periodic && i < nuy) ? c.cy32[i] : 0.f;
   }
   __syncthreads();
   float shift = 0.f;

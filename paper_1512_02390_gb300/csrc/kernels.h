@@ -28,6 +28,7 @@ struct PcgFuse {
   int stride = 0, nb = 1;
 };
 
+// eo: -1 the even-odd form in FP64 only, 0 never, 1 for P >= 4 in any type.
 // out = A u (f == nullptr) or out = f - A u.  dot: 0 none, 1 part[cta] = sum
 // u.out, 2 part[cta] = sum out.out over the CTA's nodes.  *nparts receives
 // the number of partials written.  With E != nullptr the input u is not read:
@@ -36,7 +37,7 @@ struct PcgFuse {
 template <typename T, typename TF>
 cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u, const TF* f,
                          T* out, int dot, double* part, int* nparts, cudaStream_t s, const T* E = nullptr,
-                         T* uout = nullptr, PcgFuse pf = PcgFuse());
+                         T* uout = nullptr, PcgFuse pf = PcgFuse(), int eo = -1);
 
 // Variable-diffusivity operator B(nu) (Sec. 4.3): element data of one level.
 template <typename T>
@@ -100,6 +101,7 @@ struct CoarseView {
   int batch;       // stacked independent problems (coarse blocks)
   int block_rows;  // node rows between consecutive blocks
   const double *Sx, *Sy, *lx, *ly, *cx, *cy;
+  const float *Sx32, *Sy32, *lx32, *ly32, *cx32, *cy32;  // FP32 copies (the FP32 coarse kernel)
   double* T1;  // batch x nuy x nux scratch (also holds S_y T2)
   double* T2;  // batch x nuy x nux scratch
 };

@@ -18,18 +18,19 @@ bool parse_line(const std::string& line, std::string& key, TuneVal& v) {
   if (e == std::string::npos) return false;
   key = line.substr(k0.size(), e - k0.size());
   TuneVal t;
-  if (std::sscanf(line.c_str() + e, "\", \"fuse\": %d, \"spw\": %d, \"tc\": %d, \"us\": %lf}", &t.fuse, &t.spw,
-                  &t.tc, &t.us) != 4)
+  if (std::sscanf(line.c_str() + e, "\", \"fuse\": %d, \"spw\": %d, \"tc\": %d, \"eo\": %d, \"us\": %lf}", &t.fuse,
+                  &t.spw, &t.tc, &t.eo, &t.us) != 5)
     return false;
-  if (t.fuse < 0 || t.fuse > 1 || t.spw < 1 || t.spw > 64 || t.tc < 0 || t.tc > 1) return false;
+  if (t.fuse < 0 || t.fuse > 1 || t.spw < 1 || t.spw > 64 || t.tc < 0 || t.tc > 1 || t.eo < -1 || t.eo > 1)
+    return false;
   v = t;
   return true;
 }
 
 std::string format_line(const std::string& key, const TuneVal& v) {
   char buf[128];
-  std::snprintf(buf, sizeof(buf), "\", \"fuse\": %d, \"spw\": %d, \"tc\": %d, \"us\": %.3f}", v.fuse, v.spw, v.tc,
-                v.us);
+  std::snprintf(buf, sizeof(buf), "\", \"fuse\": %d, \"spw\": %d, \"tc\": %d, \"eo\": %d, \"us\": %.3f}", v.fuse,
+                v.spw, v.tc, v.eo, v.us);
   return "{\"key\": \"" + key + buf;
 }
 

@@ -98,8 +98,8 @@ class Solver:
         B.sem_autotune(self.h, cache_path, stream)
         return {l: B.sem_get_tune(self.h, l) for l in range(1, self.levels + 1)}
 
-    def set_tune(self, level, fuse, spw=1, tc=0):
-        B.sem_set_tune(self.h, level, fuse, spw, tc)
+    def set_tune(self, level, fuse, spw=1, tc=0, eo=-1):
+        B.sem_set_tune(self.h, level, fuse, spw, tc, eo)
 
     def get_tune(self, level):
         return B.sem_get_tune(self.h, level)
@@ -109,7 +109,7 @@ class Solver:
         for l in range(1, self.levels + 1):
             t = other.get_tune(l)
             tc = t["tc"] if self.get_tune(l)["tc_available"] else 0
-            B.sem_set_tune(self.h, l, t["fuse"], t["spw"], tc)
+            B.sem_set_tune(self.h, l, t["fuse"], t["spw"], tc, t["eo"])
 
 
 class Batch:

@@ -99,7 +99,7 @@ def test_autotune_cache_roundtrip(tmp_path):
     S2 = P.Solver(**cfg)
     again = S2.autotune(path)
     for l in tuned:
-        for k in ("fuse", "spw", "tc"):
+        for k in ("fuse", "spw", "tc", "eo"):
             assert again[l][k] == tuned[l][k]
         assert abs(again[l]["us"] - round(tuned[l]["us"], 3)) < 1e-9
     assert len(open(path).read().splitlines()) == S.levels

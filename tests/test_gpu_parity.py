@@ -267,12 +267,16 @@ def test_mg_solve_rate_matches_oracle():
 @pytest.mark.parametrize("case", [dict(nx=4, ny=4, p=4), dict(nx=4, ny=6, p=8, periodic=True, overlap=3),
                                   dict(nx=12, ny=10, p=4, overlap=1), dict(nx=9, ny=9, p=8, periodic=True, overlap=1),
                                   dict(nx=65, ny=20, p=2, overlap=1), dict(nx=66, ny=12, p=2, overlap=1)], ids=_ids)
-def test_fp32_vcycle_matches_oracle(case):
-    """Alg. 3 in the FP32 V-cycle (SIMT sweeps; the one-CTA FP32 coarse solve
+@pytest.mark.parametrize("eo", [0, 1])
+def test_fp32_vcycle_matches_oracle(case, eo):
+    """Alg. 3 in the FP32 V-cycle (SIMT sweeps; the clustered FP32 coarse solve
     where the coarse grid has at most 64 x 64 unknowns, the four-launch
-    product beyond): the correction u_new - u_old agrees with the FP64
-    oracle's to FP32 accuracy (1e-5 of its maximum)."""
+    product beyond; level residuals in the plain or the even-odd form): the
+    correction u_new - u_old agrees with the FP64 oracle's to FP32 accuracy
+    (1e-5 of its maximum)."""
     S, H = _pair(precision="fp32", **case)
+    for l in range(1, S.levels + 1):
+        S.set_tune(l, 0, 1, 0, eo)
     lev = H.top
     u0 = SI.uniform_nodal(7, (lev.NY, lev.NX)) * lev.unknown
     f = lev.mass(SI.uniform_nodal(8, (lev.NY, lev.NX)))
