@@ -212,7 +212,8 @@ typedef enum sem_kernel_class {
   SEM_K_PROLONG = 5,    /* I_l                                                              */
   SEM_K_COARSE = 6,     /* A_0^+ (four kernels per solve)                                   */
   SEM_K_VECTOR = 7,     /* MGCG vector updates, dots, conversions                           */
-  SEM_K_NCLASS = 8
+  SEM_K_LOW_CYCLE = 8,  /* the levels p_l <= 8 and the coarse solve in one persistent kernel */
+  SEM_K_NCLASS = 9
 } sem_kernel_class;
 
 /* Tracing.  sem_profile resets the per-class kernel-launch counters of the
@@ -262,6 +263,19 @@ typedef struct sem_level_tune {
   double us;            /* measured time of the level's down-sweep step (microseconds; 0 if not timed) */
 } sem_level_tune;
 int sem_autotune(sem_handle* h, const char* cache_path, void* stream);
+/* The lower part of the V-cycle as ONE persistent cooperative kernel (not in
+ * the paper): on levels 1 .. min(log2(p) - 1, 3) one Schwarz step from zero
+ * (tensor-core sweep, scatter fused into the residual), the restrictions, the
+ * FP32 coarse solve and the prolongations, with grid barriers instead of kernel
+ * boundaries.  Available for the TF32 / BF16 modes of the Poisson operator with
+ * one pre-smoothing step and no post-smoothing, windows m <= 16 and coarse
+ * grids of at most 64 x 64 unknowns; on by default where available, and
+ * sem_autotune keeps it only where it is faster than the per-level launches.
+ * A grid barrier that waits more than about a second makes the next
+ * synchronous solve return SEM_TIMEOUT.  sem_set_low_cycle(h, 1) fails with
+ * SEM_BAD_ARG where it is not available; both calls discard the captured graph. */
+int sem_set_low_cycle(sem_handle* h, int32_t enable);
+int sem_get_low_cycle(const sem_handle* h, int32_t* available, int32_t* enabled);
 int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t);
 int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t);
 

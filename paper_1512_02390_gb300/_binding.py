@@ -32,12 +32,13 @@ EXPORTS = [
     "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
     "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
-    "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune",
+    "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
     "sem_status_string", "sem_last_error",
 ]
 SEM_MLP_PARAMS = 4610
 # sem_kernel_class
-KERNEL_CLASSES = ["apply_fp64", "apply_mg", "sweep", "scatter", "restrict", "prolong", "coarse", "vector"]
+KERNEL_CLASSES = ["apply_fp64", "apply_mg", "sweep", "scatter", "restrict", "prolong", "coarse", "vector",
+                  "low_cycle"]
 
 
 class sem_config(ctypes.Structure):
@@ -125,6 +126,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_get_tune": (i32, [vp, i32, ctypes.POINTER(sem_level_tune)]),
         "sem_set_tune": (i32, [vp, i32, ctypes.POINTER(sem_level_tune)]),
         "sem_batch_autotune": (i32, [vp, ctypes.c_char_p, vp]),
+        "sem_set_low_cycle": (i32, [vp, i32]),
+        "sem_get_low_cycle": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -380,3 +383,14 @@ def sem_set_tune(h, level: int, fuse: int, spw: int = 1, tc: int = 0, eo: int = 
 
 def sem_batch_autotune(b, cache_path=None, stream=None) -> None:
     _check(load_library().sem_batch_autotune(b, _path_arg(cache_path), _stream(stream)))
+
+
+def sem_set_low_cycle(h, enable: bool) -> None:
+    _check(load_library().sem_set_low_cycle(h, int(bool(enable))))
+
+
+def sem_get_low_cycle(h):
+    """(available, enabled) of the persistent low-level cycle."""
+    a, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().sem_get_low_cycle(h, ctypes.byref(a), ctypes.byref(e)))
+    return bool(a.value), bool(e.value)

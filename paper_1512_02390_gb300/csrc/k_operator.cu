@@ -12,45 +12,11 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "level_ops.cuh"
 
 namespace sem {
 
 namespace {
-
-template <int P>
-struct Tile {
-  static constexpr int TE = tile_elems(P);           // elements per direction
-  static constexpr int TN = TE * P;                  // owned nodes per direction
-  static constexpr int LN = TN + P + 1;              // staged nodes per direction
-  static constexpr int LP = LN + 1;                  // padded row pitch
-  static constexpr int NP = P + 1;
-};
-
-// beta of this tile's problem for the fused MGCG direction (0 when unused)
-__device__ __forceinline__ double fused_beta(const PcgFuse& pf) {
-  if (!pf.z) return 0.0;
-  const int k = blockIdx.y / (gridDim.y / pf.nb);
-  return pf.flags[2 * k] ? 0.0 : pf.beta[(long)k * pf.stride + pf.iter[1]];
-}
-
-// staged operand at node (gy, gx) (-1: wall, 0): u, the assembled Schwarz
-// correction (E), or the MGCG direction z + beta p
-template <typename T>
-__device__ __forceinline__ T stage_value(const T* __restrict__ u, const T* __restrict__ E, const DirView<T>& dx,
-                                         const DirView<T>& dy, const PcgFuse& pf, double beta, int gy, int gx) {
-  if (gx < 0 || gy < 0) return T(0);
-  if (E) return window_sum(dx, dy, E, gy, gx);
-  const long o = (long)gy * dx.N + gx;
-  if (pf.z) return T(fma(beta, (double)u[o], pf.z[o]));
-  return u[o];
-}
-
-template <typename T, int P>
-size_t apply_smem() {
-  using Tl = Tile<P>;
-  return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1)) +
-         sizeof(double) * kRedThreads;
-}
 
 template <typename T, typename TF, int P>
 __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, const T* __restrict__ u,
@@ -58,95 +24,9 @@ __global__ void __launch_bounds__(256) k_apply(DirView<T> dx, DirView<T> dy, con
                                                double* __restrict__ part, const T* __restrict__ E,
                                                T* __restrict__ uout, PcgFuse pf) {
   pdl_enter();
-  using Tl = Tile<P>;
-  constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);          // LN x LP staged u
-  T* sLx = su + LN * LP;                           // (TE+1) x NP x NP
-  T* sLy = sLx + (TE + 1) * NP * NP;
-  T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
-  T* sMy = sMx + (TN + 1);
-  double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
-
-  const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
-  const int Nx = dx.N, Ny = dy.N;
-  const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
-  const double beta = fused_beta(pf);
-
-  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
-    const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
-    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
-  }
-  // element stiffness of the tile and of its low-side neighbour (slot 0)
-  for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
-    const int le = idx / (NP * NP), ab = idx - le * NP * NP;
-    int exx = ex0 + le - 1, eyy = ey0 + le - 1;
-    if (dx.periodic) exx = (exx + dx.n) % dx.n;
-    if (dy.periodic) eyy = (eyy + dy.n) % dy.n;
-    sLx[idx] = (exx >= 0 && exx < dx.n) ? dx.Le[(long)exx * NP * NP + ab] : T(0);
-    sLy[idx] = (eyy >= 0 && eyy < dy.n) ? dy.Le[(long)eyy * NP * NP + ab] : T(0);
-  }
-  for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
-    const int gx = ex0 * P + idx, gy = ey0 * P + idx;
-    sMx[idx] = gx < Nx ? dx.Mg[gx] : T(0);
-    sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
-  }
-  __syncthreads();
-
-  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
-  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
-  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
-  double acc = 0.0;
-  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
-    const int jy = idx / ownx, ix = idx - jy * ownx;
-    const int gi = ex0 * P + ix, gj = ey0 * P + jy;
-    const long o = (long)gj * Nx + gi;
-    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
-    T val = T(0);
-    if (!wall) {
-      const int lex = ix / P, a = ix - lex * P;
-      const int ley = jy / P, b = jy - ley * P;
-      const T* row = su + (jy + P) * LP;          // staged row of node (j, .)
-      // x direction: element row a of element lex (+ left neighbour's last row)
-      T xs = T(0), ys = T(0);
-      {
-        const T* L = sLx + (lex + 1) * NP * NP + a * NP;
-        const T* uu = row + lex * P + P;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) xs += L[k] * uu[k];
-        if (a == 0) {
-          const T* Ll = sLx + lex * NP * NP + P * NP;
-          const T* ul = row + lex * P;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) xs += Ll[k] * ul[k];
-        }
-      }
-      {
-        const T* L = sLy + (ley + 1) * NP * NP + b * NP;
-        const T* uu = su + (ley * P + P) * LP + ix + P;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) ys += L[k] * uu[k * LP];
-        if (b == 0) {
-          const T* Ll = sLy + ley * NP * NP + P * NP;
-          const T* ul = su + (ley * P) * LP + ix + P;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) ys += Ll[k] * ul[k * LP];
-        }
-      }
-      val = sMy[jy] * xs + sMx[ix] * ys;
-      if (f) val = T(f[o]) - val;
-    }
-    out[o] = val;
-    if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
-    if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
-    else if (dot == 2) acc += (double)val * (double)val;
-  }
-  if (dot) {
-    const double s = block_sum(acc, sred);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
-  }
+  apply_tile<T, TF, P>(dx, dy, u, f, out, dot, part, E, uout, pf, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
+                       smem_raw);
 }
 
 // Even-odd variant of the same operator.  The 1D element stiffness of GLL
@@ -271,7 +151,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
   const int Nx = dx.N, Ny = dy.N;
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
-  const double beta = fused_beta(pf);
+  const double beta = fused_beta(pf, blockIdx.y, gridDim.y);
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);

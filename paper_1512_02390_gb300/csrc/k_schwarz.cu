@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "level_ops.cuh"
 
 namespace sem {
 
@@ -87,214 +88,15 @@ __global__ void __launch_bounds__(256) k_sweep_simt(DirView<T> dx, DirView<T> dy
 }
 
 // ---- tensor-core FDM ---------------------------------------------------------
-// One warp per subdomain: the m x m window is padded to MP x MP (MP a multiple
-// of 16) in shared memory with zeros, and the four contractions of Eq. (FDM)
-// run as warp-level MMAs with FP32 accumulation:
-//   P1  Y[a][i] = sum_j S_y[j][a] X[j][i]          (A = S_y^T, B = X)
-//   P2  X[a][b] = sum_i Y[a][i] S_x[i][b] / (lam_y[a] + lam_x[b])
-//   P3  Y[j][b] = sum_a S_y[j][a] X[a][b]
-//   P4  E[j][i] = w_y[j] w_x[i] sum_b Y[j][b] S_x[i][b]
-// MODE 1: TF32 operands (mma m16n8k8), MODE 2: BF16 operands (mma m16n8k16).
-// Padding rows/columns of S are zero, so the padded products are exact
-// extensions of the m x m ones.
-
-__device__ __forceinline__ uint32_t f2tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// C (MP x MP) = A (MP x MP) * B (MP x MP), operands read from shared memory
-// through accessor functors (they carry the transposition), result handed to
-// an epilogue functor element by element.
-template <int MODE, int MP, typename LA, typename LB, typename EP>
-__device__ __forceinline__ void warp_gemm(LA la, LB lb, EP ep) {
-  constexpr int MT = MP / 16, NT = MP / 8;
-  constexpr int KS = MODE == 1 ? 8 : 16;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < MP; k0 += KS) {
-    uint32_t bf[NT][2];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int n = j * 8 + g;
-      if (MODE == 1) {
-        bf[j][0] = f2tf32(lb(k0 + t, n));
-        bf[j][1] = f2tf32(lb(k0 + t + 4, n));
-      } else {
-        bf[j][0] = pack_bf16(lb(k0 + 2 * t, n), lb(k0 + 2 * t + 1, n));
-        bf[j][1] = pack_bf16(lb(k0 + 2 * t + 8, n), lb(k0 + 2 * t + 9, n));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < MT; ++i) {
-      const int r = i * 16 + g;
-      uint32_t af[4];
-      if (MODE == 1) {
-        af[0] = f2tf32(la(r, k0 + t));
-        af[1] = f2tf32(la(r + 8, k0 + t));
-        af[2] = f2tf32(la(r, k0 + t + 4));
-        af[3] = f2tf32(la(r + 8, k0 + t + 4));
-      } else {
-        af[0] = pack_bf16(la(r, k0 + 2 * t), la(r, k0 + 2 * t + 1));
-        af[1] = pack_bf16(la(r + 8, k0 + 2 * t), la(r + 8, k0 + 2 * t + 1));
-        af[2] = pack_bf16(la(r, k0 + 2 * t + 8), la(r, k0 + 2 * t + 9));
-        af[3] = pack_bf16(la(r + 8, k0 + 2 * t + 8), la(r + 8, k0 + 2 * t + 9));
-      }
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        if (MODE == 1) mma_tf32(acc[i][j], af, bf[j]);
-        else mma_bf16(acc[i][j], af, bf[j]);
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int r = i * 16 + g, c = j * 8 + 2 * t;
-      ep(r, c, acc[i][j][0]);
-      ep(r, c + 1, acc[i][j][1]);
-      ep(r + 8, c, acc[i][j][2]);
-      ep(r + 8, c + 1, acc[i][j][3]);
-    }
-}
-
-constexpr int kMmaWarps = 4;
-
-template <int MP>
-struct MmaSmem {
-  static constexpr int SA = MP + 4;                    // row pitch (floats)
-  static constexpr int MAT = MP * SA;
-  static constexpr int PER_WARP = 4 * MAT + 4 * MP;    // X, Y, S_x, S_y, lam_x, lam_y, w_x, w_y
-};
-
 template <typename TIn, int MODE, int MP>
 __global__ void __launch_bounds__(32 * kMmaWarps) k_sweep_mma(DirView<float> dx, DirView<float> dy,
                                                               const TIn* __restrict__ r, float* __restrict__ E,
                                                               const float* __restrict__ nu_inv, int nsub) {
   pdl_enter();
-  using Q = MmaSmem<MP>;
-  constexpr int SA = Q::SA;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* base = reinterpret_cast<float*>(smem_raw) + warp * Q::PER_WARP;
-  float* X = base;
-  float* Y = X + Q::MAT;
-  float* Sx = Y + Q::MAT;
-  float* Sy = Sx + Q::MAT;
-  float* lx = Sy + Q::MAT;
-  float* ly = lx + MP;
-  float* wx = ly + MP;
-  float* wy = wx + MP;
-  const int m = dx.m, mm = m * m, p = dx.p, no = dx.n_o;
-  int cur_tx = -1, cur_ty = -1;  // tables currently in this warp's shared memory
-  for (int sidx = blockIdx.x * kMmaWarps + warp; sidx < nsub; sidx += gridDim.x * kMmaWarps) {
-    const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
-    const int tx = dx.tab[ex], ty = dy.tab[ey];
-    // window gather: every lane issues all its loads before the first store
-    constexpr int PER = (MP * MP + 31) / 32;
-    float xv[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = lane + 32 * q;
-      const int a = idx / MP, b = idx - a * MP;
-      float v = 0.f;
-      if (idx < MP * MP && a < m && b < m) {
-        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
-        const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
-        if (gx >= 0 && gy >= 0) v = (float)r[(long)gy * dx.N + gx];
-      }
-      xv[q] = v;
-    }
-    // tables: reloaded only when this subdomain's type differs from the last
-    if (tx != cur_tx) {
-      const float* gSx = dx.S + (long)tx * mm;
-      for (int idx = lane; idx < MP * MP; idx += 32) {
-        const int a = idx / MP, b = idx - a * MP;
-        Sx[a * SA + b] = (a < m && b < m) ? gSx[a * m + b] : 0.f;
-      }
-      for (int idx = lane; idx < MP; idx += 32) {
-        lx[idx] = idx < m ? dx.lam[tx * m + idx] : 1.f;
-        wx[idx] = idx < m ? dx.w[tx * m + idx] : 0.f;
-      }
-      cur_tx = tx;
-    }
-    if (ty != cur_ty) {
-      const float* gSy = dy.S + (long)ty * mm;
-      for (int idx = lane; idx < MP * MP; idx += 32) {
-        const int a = idx / MP, b = idx - a * MP;
-        Sy[a * SA + b] = (a < m && b < m) ? gSy[a * m + b] : 0.f;
-      }
-      for (int idx = lane; idx < MP; idx += 32) {
-        ly[idx] = idx < m ? dy.lam[ty * m + idx] : 1.f;
-        wy[idx] = idx < m ? dy.w[ty * m + idx] : 0.f;
-      }
-      cur_ty = ty;
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = lane + 32 * q;
-      if (idx < MP * MP) {
-        const int a = idx / MP, b = idx - a * MP;
-        X[a * SA + b] = xv[q];
-      }
-    }
-    __syncwarp();
-    // P1: Y = S_y^T X
-    warp_gemm<MODE, MP>([&](int row, int k) { return Sy[k * SA + row]; },
-                        [&](int k, int n) { return X[k * SA + n]; },
-                        [&](int row, int col, float v) { Y[row * SA + col] = v; });
-    __syncwarp();
-    // P2: X = (Y S_x) ./ (lam_y + lam_x)
-    warp_gemm<MODE, MP>([&](int row, int k) { return Y[row * SA + k]; },
-                        [&](int k, int n) { return Sx[k * SA + n]; },
-                        [&](int row, int col, float v) { X[row * SA + col] = v / (ly[row] + lx[col]); });
-    __syncwarp();
-    // P3: Y = S_y X
-    warp_gemm<MODE, MP>([&](int row, int k) { return Sy[row * SA + k]; },
-                        [&](int k, int n) { return X[k * SA + n]; },
-                        [&](int row, int col, float v) { Y[row * SA + col] = v; });
-    __syncwarp();
-    // P4: E = w_y w_x^T .* (Y S_x^T), written for the m x m window only
-    const float sc = nu_inv ? nu_inv[sidx] : 1.f;
-    float* Es = E + (long)sidx * mm;
-    warp_gemm<MODE, MP>([&](int row, int k) { return Y[row * SA + k]; },
-                        [&](int k, int n) { return Sx[n * SA + k]; },
-                        [&](int row, int col, float v) {
-                          if (row < m && col < m) Es[row * m + col] = wy[row] * wx[col] * v * sc;
-                        });
-    __syncwarp();
-  }
+  const int warp = threadIdx.x >> 5;
+  sweep_mma_warp<TIn, MODE, MP>(dx, dy, r, E, nu_inv, nsub, blockIdx.x * kMmaWarps + warp, gridDim.x * kMmaWarps,
+                                reinterpret_cast<float*>(smem_raw) + warp * MmaSmem<MP>::PER_WARP);
 }
 
 template <typename TIn, int MODE, int MP>

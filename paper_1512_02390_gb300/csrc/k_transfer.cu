@@ -20,141 +20,28 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "level_ops.cuh"
 
 namespace sem {
 
 namespace {
 
-template <int PF>
-struct TT {
-  static constexpr int PC = PF / 2;
-  static constexpr int TE = tile_elems(PF);            // elements per tile per direction
-  static constexpr int TNF = TE * PF;
-  static constexpr int TNC = TE * PC;
-  static constexpr int NPF = PF + 1, NPC = PC + 1;
-};
-
-// fc = I^T rf.  Fine nodes staged: [E0 pf - pf, E0 pf + TNF] per direction.
 template <typename T, int PF>
 __global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                   const T* __restrict__ J, const T* __restrict__ rf,
                                                   T* __restrict__ fc) {
   pdl_enter();
-  using Q = TT<PF>;
-  constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
-  constexpr int LN = TNF + PF + 1, LP = LN + 1, TP = TNC + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sr = reinterpret_cast<T*>(smem_raw);  // LN x LP fine residual
-  T* st = sr + LN * LP;                     // LN x TP  x-contracted
-  T* sJ = st + LN * TP;                     // NPF x NPC
-  const int E0x = blockIdx.x * TE, E0y = blockIdx.y * TE;
-  const int gx0 = E0x * PF - PF, gy0 = E0y * PF - PF;
-  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
-    const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, fx.N, fx.periodic, fx.segN);
-    const int gy = node_or_wall(gy0 + ly, fy.N, fy.periodic, fy.segN);
-    sr[ly * LP + lx] = (gx >= 0 && gy >= 0) ? rf[(long)gy * fx.N + gx] : T(0);
-  }
-  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
-  __syncthreads();
-  const bool lastx = E0x + TE >= cx.n, lasty = E0y + TE >= cy.n;
-  const int ownx = min(TE, cx.n - E0x) * PC + ((!cx.periodic && lastx) ? 1 : 0);
-  const int owny = min(TE, cy.n - E0y) * PC + ((!cy.periodic && lasty) ? 1 : 0);
-  // x contraction for every staged fine row
-  for (int idx = threadIdx.x; idx < LN * ownx; idx += blockDim.x) {
-    const int ly = idx / ownx, ic = idx - ly * ownx;
-    const int le = ic / PC, K = ic - le * PC;
-    const T* row = sr + ly * LP + le * PF + PF;  // fine local node 0 of element E0x + le
-    T t = T(0);
-    if (le < TE) {
-      if (K != 0) {
-#pragma unroll
-        for (int i = 1; i < PF; ++i) t += sJ[i * NPC + K] * row[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < PF; ++i) t += sJ[i * NPC] * row[i];
-#pragma unroll
-        for (int i = 1; i < PF; ++i) t += sJ[i * NPC + PC] * row[i - PF];
-      }
-    }
-    st[ly * TP + ic] = t;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
-    const int jc = idx / ownx, ic = idx - jc * ownx;
-    const int gI = E0x * PC + ic, gJ = E0y * PC + jc;
-    const bool wall = wall_node(gI, cx.N, cx.periodic, cx.segN) || wall_node(gJ, cy.N, cy.periodic, cy.segN);
-    T v = T(0);
-    if (!wall) {
-      const int le = jc / PC, K = jc - le * PC;
-      const T* col = st + (le * PF + PF) * TP + ic;
-      if (K != 0) {
-#pragma unroll
-        for (int j = 1; j < PF; ++j) v += sJ[j * NPC + K] * col[j * TP];
-      } else {
-#pragma unroll
-        for (int j = 0; j < PF; ++j) v += sJ[j * NPC] * col[j * TP];
-#pragma unroll
-        for (int j = 1; j < PF; ++j) v += sJ[j * NPC + PC] * col[(j - PF) * TP];
-      }
-    }
-    fc[(long)gJ * cx.N + gI] = v;
-  }
+  restrict_tile<T, PF>(fx, fy, cx, cy, J, rf, fc, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// out = in + I uc.  Coarse nodes staged: [E0 pc, E0 pc + TNC] per direction.
 template <typename T, typename TOut, int PF>
 __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                  const T* __restrict__ J, const T* __restrict__ uc,
                                                  const T* in, TOut* out) {
   pdl_enter();
-  using Q = TT<PF>;
-  constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
-  constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sc = reinterpret_cast<T*>(smem_raw);  // LC x LCP coarse values
-  T* st = sc + LC * LCP;                    // LC x TP  x-interpolated
-  T* sJ = st + LC * TP;
-  const int E0x = blockIdx.x * TE, E0y = blockIdx.y * TE;
-  for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
-    const int ly = idx / LC, lx = idx - ly * LC;
-    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
-    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic, cy.segN);
-    sc[ly * LCP + lx] = (gx >= 0 && gy >= 0) ? uc[(long)gy * cx.N + gx] : T(0);
-  }
-  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
-  __syncthreads();
-  const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
-  const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
-  const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
-  for (int idx = threadIdx.x; idx < LC * ownx; idx += blockDim.x) {
-    const int ly = idx / ownx, ix = idx - ly * ownx;
-    const int le = ix / PF, i = ix - le * PF;
-    T t = T(0);
-    if (le < TE) {
-      const T* row = sc + ly * LCP + le * PC;
-#pragma unroll
-      for (int k = 0; k < NPC; ++k) t += sJ[i * NPC + k] * row[k];
-    }
-    st[ly * TP + ix] = t;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
-    const int jy = idx / ownx, ix = idx - jy * ownx;
-    const int gi = E0x * PF + ix, gj = E0y * PF + jy;
-    const long o = (long)gj * fx.N + gi;
-    const bool wall = wall_node(gi, fx.N, fx.periodic, fx.segN) || wall_node(gj, fy.N, fy.periodic, fy.segN);
-    if (wall) {
-      out[o] = TOut(0);
-      continue;
-    }
-    const int le = jy / PF, j = jy - le * PF;
-    const T* col = st + (le * PC) * TP + ix;
-    T v = T(0);
-#pragma unroll
-    for (int k = 0; k < NPC; ++k) v += sJ[j * NPC + k] * col[k * TP];
-    out[o] = in ? TOut(in[o] + v) : TOut(v);
-  }
+  prolong_tile<T, TOut, PF>(fx, fy, cx, cy, J, uc, in, out, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Coarse solve as four small FP64 products over the unknowns (F: nuy x nux):
@@ -281,8 +168,7 @@ template <typename T, int PF>
 cudaError_t restrict_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,
                        const T* J, const T* rf, T* fc, cudaStream_t s) {
   using Q = TT<PF>;
-  constexpr int LN = Q::TNF + PF + 1;
-  const size_t sm = sizeof(T) * (LN * (LN + 1) + LN * (Q::TNC + 2) + (PF + 1) * Q::NPC);
+  const size_t sm = restrict_smem<T, PF>();
   cudaError_t e = allow_smem(k_restrict<T, PF>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((cx.n + Q::TE - 1) / Q::TE, (cy.n + Q::TE - 1) / Q::TE);
@@ -297,8 +183,7 @@ template <typename T, typename TOut, int PF>
 cudaError_t prolong_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,
                       const T* J, const T* uc, const T* in, TOut* out, cudaStream_t s) {
   using Q = TT<PF>;
-  constexpr int LC = Q::TNC + 1;
-  const size_t sm = sizeof(T) * (LC * (LC + 1) + LC * (Q::TNF + 2) + (PF + 1) * Q::NPC);
+  const size_t sm = prolong_smem<T, PF>();
   cudaError_t e = allow_smem(k_prolong<T, TOut, PF>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((fx.n + Q::TE - 1) / Q::TE, (fy.n + Q::TE - 1) / Q::TE);

@@ -114,6 +114,26 @@ inline int coarse_launches(const CoarseView& c, bool fp32) { return (fp32 && c.n
 template <typename T>
 cudaError_t launch_coarse_dense(const CoarseView& c, const double* Binv, const T* f0, T* u0, cudaStream_t s);
 
+// ---- persistent low-level V-cycle (Alg. 3 below the upper levels), k_lowcycle.cu
+struct LowLevel {
+  DirView<float> x, y;
+  const float* J;  // interpolation from level l-1 to l (l >= 1)
+  float *u, *f, *r, *E;
+};
+struct LowCycle {
+  int top;             // highest level handled, p_top in {2, 4, 8}
+  LowLevel lev[4];     // levels 0 .. top
+  CoarseView coarse;   // FP32 tables, at most 64 x 64 unknowns per problem
+  float* cw;           // coarse scratch, coarse.batch x 64 x 64
+  unsigned* bar;       // grid barrier [arrivals, generation]; arrivals 0 between launches
+  int* err;            // set to 1 when a barrier wait gave up
+};
+// Levels top .. 1: one Schwarz step from zero (mma.sync sweep, mode 1 TF32 /
+// 2 BF16, m <= 16), residual with the scatter fused, restriction; the coarse
+// solve; prolongations back to level top.  One cooperative launch; *grid
+// receives its CTA count.
+cudaError_t launch_low_cycle(const LowCycle& c, int mode, int top_p, int* grid, cudaStream_t s);
+
 // ---- Krylov vector kernels (Alg. 4), k_krylov.cu -------------------------
 // MGCG state of nb independent problems stacked in one node grid (nb = 1 for a
 // single solve).  Problem k owns nodes [k seg_len, (k+1) seg_len) (the last

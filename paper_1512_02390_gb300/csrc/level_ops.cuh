@@ -1,0 +1,507 @@
+// Bodies of the level operations of the V-cycle, one tile or one subdomain at
+// a time, shared by the one-kernel-per-step launches (k_operator.cu,
+// k_transfer.cu, k_schwarz.cu) and the persistent low-level cycle
+// (k_lowcycle.cu): the node-centric residual of Eq. (system matrix), the grid
+// transfers of Sec. 3.2 and the tensor-core (mma.sync) fast-diagonalisation
+// sweep of Alg. 2 / Eq. (FDM).
+#pragma once
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace sem {
+
+// ---- level residual (operator) ------------------------------------------------
+template <int P>
+struct Tile {
+  static constexpr int TE = tile_elems(P);           // elements per direction
+  static constexpr int TN = TE * P;                  // owned nodes per direction
+  static constexpr int LN = TN + P + 1;              // staged nodes per direction
+  static constexpr int LP = LN + 1;                  // padded row pitch
+  static constexpr int NP = P + 1;
+};
+
+// beta of this tile's problem for the fused MGCG direction (0 when unused)
+__device__ __forceinline__ double fused_beta(const PcgFuse& pf, int by, int gyd) {
+  if (!pf.z) return 0.0;
+  const int k = by / (gyd / pf.nb);
+  return pf.flags[2 * k] ? 0.0 : pf.beta[(long)k * pf.stride + pf.iter[1]];
+}
+
+// staged operand at node (gy, gx) (-1: wall, 0): u, the assembled Schwarz
+// correction (E), or the MGCG direction z + beta p
+template <typename T>
+__device__ __forceinline__ T stage_value(const T* __restrict__ u, const T* __restrict__ E, const DirView<T>& dx,
+                                         const DirView<T>& dy, const PcgFuse& pf, double beta, int gy, int gx) {
+  if (gx < 0 || gy < 0) return T(0);
+  if (E) return window_sum(dx, dy, E, gy, gx);
+  const long o = (long)gy * dx.N + gx;
+  if (pf.z) return T(fma(beta, (double)u[o], pf.z[o]));
+  return u[o];
+}
+
+template <typename T, int P>
+size_t apply_smem() {
+  using Tl = Tile<P>;
+  return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1)) +
+         sizeof(double) * kRedThreads;
+}
+
+// One tile (bx, by) of a (gxd x gyd) tile grid; smem: apply_smem<T, P>() bytes.
+template <typename T, typename TF, int P>
+__device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T>& dy, const T* __restrict__ u,
+                                           const TF* __restrict__ f, T* __restrict__ out, int dot,
+                                           double* __restrict__ part, const T* __restrict__ E,
+                                           T* __restrict__ uout, const PcgFuse& pf, int bx, int by, int gxd, int gyd,
+                                           unsigned char* smem_raw) {
+  using Tl = Tile<P>;
+  constexpr int TE = Tl::TE, TN = Tl::TN, LN = Tl::LN, LP = Tl::LP, NP = Tl::NP;
+  T* su = reinterpret_cast<T*>(smem_raw);          // LN x LP staged u
+  T* sLx = su + LN * LP;                           // (TE+1) x NP x NP
+  T* sLy = sLx + (TE + 1) * NP * NP;
+  T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
+  T* sMy = sMx + (TN + 1);
+  double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
+
+  const int ex0 = bx * TE, ey0 = by * TE;
+  const int Nx = dx.N, Ny = dy.N;
+  const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+  const double beta = fused_beta(pf, by, gyd);
+
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
+    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
+  }
+  // element stiffness of the tile and of its low-side neighbour (slot 0)
+  for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
+    const int le = idx / (NP * NP), ab = idx - le * NP * NP;
+    int exx = ex0 + le - 1, eyy = ey0 + le - 1;
+    if (dx.periodic) exx = (exx + dx.n) % dx.n;
+    if (dy.periodic) eyy = (eyy + dy.n) % dy.n;
+    sLx[idx] = (exx >= 0 && exx < dx.n) ? dx.Le[(long)exx * NP * NP + ab] : T(0);
+    sLy[idx] = (eyy >= 0 && eyy < dy.n) ? dy.Le[(long)eyy * NP * NP + ab] : T(0);
+  }
+  for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
+    const int gx = ex0 * P + idx, gy = ey0 * P + idx;
+    sMx[idx] = gx < Nx ? dx.Mg[gx] : T(0);
+    sMy[idx] = gy < Ny ? dy.Mg[gy] : T(0);
+  }
+  __syncthreads();
+
+  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
+  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
+    const int gi = ex0 * P + ix, gj = ey0 * P + jy;
+    const long o = (long)gj * Nx + gi;
+    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
+    T val = T(0);
+    if (!wall) {
+      const int lex = ix / P, a = ix - lex * P;
+      const int ley = jy / P, b = jy - ley * P;
+      const T* row = su + (jy + P) * LP;          // staged row of node (j, .)
+      // x direction: element row a of element lex (+ left neighbour's last row)
+      T xs = T(0), ys = T(0);
+      {
+        const T* L = sLx + (lex + 1) * NP * NP + a * NP;
+        const T* uu = row + lex * P + P;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) xs += L[k] * uu[k];
+        if (a == 0) {
+          const T* Ll = sLx + lex * NP * NP + P * NP;
+          const T* ul = row + lex * P;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) xs += Ll[k] * ul[k];
+        }
+      }
+      {
+        const T* L = sLy + (ley + 1) * NP * NP + b * NP;
+        const T* uu = su + (ley * P + P) * LP + ix + P;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ys += L[k] * uu[k * LP];
+        if (b == 0) {
+          const T* Ll = sLy + ley * NP * NP + P * NP;
+          const T* ul = su + (ley * P) * LP + ix + P;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) ys += Ll[k] * ul[k * LP];
+        }
+      }
+      val = sMy[jy] * xs + sMx[ix] * ys;
+      if (f) val = T(f[o]) - val;
+    }
+    out[o] = val;
+    if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
+    if (dot == 1) acc += (double)su[(jy + P) * LP + ix + P] * (double)val;
+    else if (dot == 2) acc += (double)val * (double)val;
+  }
+  if (dot) {
+    const double s = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[by * gxd + bx] = s;
+  }
+}
+
+
+// ---- grid transfer ------------------------------------------------------------
+template <int PF>
+struct TT {
+  static constexpr int PC = PF / 2;
+  static constexpr int TE = tile_elems(PF);            // elements per tile per direction
+  static constexpr int TNF = TE * PF;
+  static constexpr int TNC = TE * PC;
+  static constexpr int NPF = PF + 1, NPC = PC + 1;
+};
+
+// fc = I^T rf.  Fine nodes staged: [E0 pf - pf, E0 pf + TNF] per direction.
+// One coarse tile (bx, by); smem: restrict_smem<T, PF>() bytes.
+template <typename T, int PF>
+__device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                                              const DirView<T>& cy, const T* __restrict__ J,
+                                              const T* __restrict__ rf, T* __restrict__ fc, int bx, int by,
+                                              unsigned char* smem_raw) {
+  using Q = TT<PF>;
+  constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
+  constexpr int LN = TNF + PF + 1, LP = LN + 1, TP = TNC + 2;
+  T* sr = reinterpret_cast<T*>(smem_raw);  // LN x LP fine residual
+  T* st = sr + LN * LP;                     // LN x TP  x-contracted
+  T* sJ = st + LN * TP;                     // NPF x NPC
+  const int E0x = bx * TE, E0y = by * TE;
+  const int gx0 = E0x * PF - PF, gy0 = E0y * PF - PF;
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    const int gx = node_or_wall(gx0 + lx, fx.N, fx.periodic, fx.segN);
+    const int gy = node_or_wall(gy0 + ly, fy.N, fy.periodic, fy.segN);
+    sr[ly * LP + lx] = (gx >= 0 && gy >= 0) ? rf[(long)gy * fx.N + gx] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
+  __syncthreads();
+  const bool lastx = E0x + TE >= cx.n, lasty = E0y + TE >= cy.n;
+  const int ownx = min(TE, cx.n - E0x) * PC + ((!cx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, cy.n - E0y) * PC + ((!cy.periodic && lasty) ? 1 : 0);
+  // x contraction for every staged fine row
+  for (int idx = threadIdx.x; idx < LN * ownx; idx += blockDim.x) {
+    const int ly = idx / ownx, ic = idx - ly * ownx;
+    const int le = ic / PC, K = ic - le * PC;
+    const T* row = sr + ly * LP + le * PF + PF;  // fine local node 0 of element E0x + le
+    T t = T(0);
+    if (le < TE) {
+      if (K != 0) {
+#pragma unroll
+        for (int i = 1; i < PF; ++i) t += sJ[i * NPC + K] * row[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < PF; ++i) t += sJ[i * NPC] * row[i];
+#pragma unroll
+        for (int i = 1; i < PF; ++i) t += sJ[i * NPC + PC] * row[i - PF];
+      }
+    }
+    st[ly * TP + ic] = t;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
+    const int jc = idx / ownx, ic = idx - jc * ownx;
+    const int gI = E0x * PC + ic, gJ = E0y * PC + jc;
+    const bool wall = wall_node(gI, cx.N, cx.periodic, cx.segN) || wall_node(gJ, cy.N, cy.periodic, cy.segN);
+    T v = T(0);
+    if (!wall) {
+      const int le = jc / PC, K = jc - le * PC;
+      const T* col = st + (le * PF + PF) * TP + ic;
+      if (K != 0) {
+#pragma unroll
+        for (int j = 1; j < PF; ++j) v += sJ[j * NPC + K] * col[j * TP];
+      } else {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) v += sJ[j * NPC] * col[j * TP];
+#pragma unroll
+        for (int j = 1; j < PF; ++j) v += sJ[j * NPC + PC] * col[(j - PF) * TP];
+      }
+    }
+    fc[(long)gJ * cx.N + gI] = v;
+  }
+}
+
+// out = in + I uc.  Coarse nodes staged: [E0 pc, E0 pc + TNC] per direction.
+// One fine tile (bx, by); smem: prolong_smem<T, PF>() bytes.
+template <typename T, typename TOut, int PF>
+__device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                                             const DirView<T>& cy, const T* __restrict__ J,
+                                             const T* __restrict__ uc, const T* in, TOut* out, int bx, int by,
+                                             unsigned char* smem_raw) {
+  using Q = TT<PF>;
+  constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
+  constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
+  T* sc = reinterpret_cast<T*>(smem_raw);  // LC x LCP coarse values
+  T* st = sc + LC * LCP;                    // LC x TP  x-interpolated
+  T* sJ = st + LC * TP;
+  const int E0x = bx * TE, E0y = by * TE;
+  for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
+    const int ly = idx / LC, lx = idx - ly * LC;
+    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
+    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic, cy.segN);
+    sc[ly * LCP + lx] = (gx >= 0 && gy >= 0) ? uc[(long)gy * cx.N + gx] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
+  __syncthreads();
+  const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
+  const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
+  for (int idx = threadIdx.x; idx < LC * ownx; idx += blockDim.x) {
+    const int ly = idx / ownx, ix = idx - ly * ownx;
+    const int le = ix / PF, i = ix - le * PF;
+    T t = T(0);
+    if (le < TE) {
+      const T* row = sc + ly * LCP + le * PC;
+#pragma unroll
+      for (int k = 0; k < NPC; ++k) t += sJ[i * NPC + k] * row[k];
+    }
+    st[ly * TP + ix] = t;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
+    const int gi = E0x * PF + ix, gj = E0y * PF + jy;
+    const long o = (long)gj * fx.N + gi;
+    const bool wall = wall_node(gi, fx.N, fx.periodic, fx.segN) || wall_node(gj, fy.N, fy.periodic, fy.segN);
+    if (wall) {
+      out[o] = TOut(0);
+      continue;
+    }
+    const int le = jy / PF, j = jy - le * PF;
+    const T* col = st + (le * PC) * TP + ix;
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < NPC; ++k) v += sJ[j * NPC + k] * col[k * TP];
+    out[o] = in ? TOut(in[o] + v) : TOut(v);
+  }
+}
+
+template <typename T, int PF>
+constexpr size_t restrict_smem() {
+  using Q = TT<PF>;
+  constexpr int LN = Q::TNF + PF + 1;
+  return sizeof(T) * (LN * (LN + 1) + LN * (Q::TNC + 2) + (PF + 1) * Q::NPC);
+}
+
+template <typename T, int PF>
+constexpr size_t prolong_smem() {
+  using Q = TT<PF>;
+  constexpr int LC = Q::TNC + 1;
+  return sizeof(T) * (LC * (LC + 1) + LC * (Q::TNF + 2) + (PF + 1) * Q::NPC);
+}
+
+// ---- mma.sync sweep ---------------------------------------------------------------
+// One warp per subdomain: the m x m window is padded to MP x MP (MP a multiple
+// of 16) in shared memory with zeros, and the four contractions of Eq. (FDM)
+// run as warp-level MMAs with FP32 accumulation:
+//   P1  Y[a][i] = sum_j S_y[j][a] X[j][i]          (A = S_y^T, B = X)
+//   P2  X[a][b] = sum_i Y[a][i] S_x[i][b] / (lam_y[a] + lam_x[b])
+//   P3  Y[j][b] = sum_a S_y[j][a] X[a][b]
+//   P4  E[j][i] = w_y[j] w_x[i] sum_b Y[j][b] S_x[i][b]
+// MODE 1: TF32 operands (mma m16n8k8), MODE 2: BF16 operands (mma m16n8k16).
+// Padding rows/columns of S are zero, so the padded products are exact
+// extensions of the m x m ones.
+
+__device__ __forceinline__ uint32_t f2tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C (MP x MP) = A (MP x MP) * B (MP x MP), operands read from shared memory
+// through accessor functors (they carry the transposition), result handed to
+// an epilogue functor element by element.
+template <int MODE, int MP, typename LA, typename LB, typename EP>
+__device__ __forceinline__ void warp_gemm(LA la, LB lb, EP ep) {
+  constexpr int MT = MP / 16, NT = MP / 8;
+  constexpr int KS = MODE == 1 ? 8 : 16;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < MP; k0 += KS) {
+    uint32_t bf[NT][2];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int n = j * 8 + g;
+      if (MODE == 1) {
+        bf[j][0] = f2tf32(lb(k0 + t, n));
+        bf[j][1] = f2tf32(lb(k0 + t + 4, n));
+      } else {
+        bf[j][0] = pack_bf16(lb(k0 + 2 * t, n), lb(k0 + 2 * t + 1, n));
+        bf[j][1] = pack_bf16(lb(k0 + 2 * t + 8, n), lb(k0 + 2 * t + 9, n));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const int r = i * 16 + g;
+      uint32_t af[4];
+      if (MODE == 1) {
+        af[0] = f2tf32(la(r, k0 + t));
+        af[1] = f2tf32(la(r + 8, k0 + t));
+        af[2] = f2tf32(la(r, k0 + t + 4));
+        af[3] = f2tf32(la(r + 8, k0 + t + 4));
+      } else {
+        af[0] = pack_bf16(la(r, k0 + 2 * t), la(r, k0 + 2 * t + 1));
+        af[1] = pack_bf16(la(r + 8, k0 + 2 * t), la(r + 8, k0 + 2 * t + 1));
+        af[2] = pack_bf16(la(r, k0 + 2 * t + 8), la(r, k0 + 2 * t + 9));
+        af[3] = pack_bf16(la(r + 8, k0 + 2 * t + 8), la(r + 8, k0 + 2 * t + 9));
+      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        if (MODE == 1) mma_tf32(acc[i][j], af, bf[j]);
+        else mma_bf16(acc[i][j], af, bf[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int r = i * 16 + g, c = j * 8 + 2 * t;
+      ep(r, c, acc[i][j][0]);
+      ep(r, c + 1, acc[i][j][1]);
+      ep(r + 8, c, acc[i][j][2]);
+      ep(r + 8, c + 1, acc[i][j][3]);
+    }
+}
+
+constexpr int kMmaWarps = 4;
+
+template <int MP>
+struct MmaSmem {
+  static constexpr int SA = MP + 4;                    // row pitch (floats)
+  static constexpr int MAT = MP * SA;
+  static constexpr int PER_WARP = 4 * MAT + 4 * MP;    // X, Y, S_x, S_y, lam_x, lam_y, w_x, w_y
+};
+
+// Subdomains first, first + stride, ... of one level, each by one warp; smem:
+// this warp's MmaSmem<MP>::PER_WARP floats.
+template <typename TIn, int MODE, int MP>
+__device__ __forceinline__ void sweep_mma_warp(const DirView<float>& dx, const DirView<float>& dy,
+                                               const TIn* __restrict__ r, float* __restrict__ E,
+                                               const float* __restrict__ nu_inv, int nsub, int first, int stride,
+                                               float* base) {
+  using Q = MmaSmem<MP>;
+  constexpr int SA = Q::SA;
+  const int lane = threadIdx.x & 31;
+  float* X = base;
+  float* Y = X + Q::MAT;
+  float* Sx = Y + Q::MAT;
+  float* Sy = Sx + Q::MAT;
+  float* lx = Sy + Q::MAT;
+  float* ly = lx + MP;
+  float* wx = ly + MP;
+  float* wy = wx + MP;
+  const int m = dx.m, mm = m * m, p = dx.p, no = dx.n_o;
+  int cur_tx = -1, cur_ty = -1;  // tables currently in this warp's shared memory
+  for (int sidx = first; sidx < nsub; sidx += stride) {
+    const int ey = sidx / dx.n, ex = sidx - ey * dx.n;
+    const int tx = dx.tab[ex], ty = dy.tab[ey];
+    // window gather: every lane issues all its loads before the first store
+    constexpr int PER = (MP * MP + 31) / 32;
+    float xv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane + 32 * q;
+      const int a = idx / MP, b = idx - a * MP;
+      float v = 0.f;
+      if (idx < MP * MP && a < m && b < m) {
+        const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
+        const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
+        if (gx >= 0 && gy >= 0) v = (float)r[(long)gy * dx.N + gx];
+      }
+      xv[q] = v;
+    }
+    // tables: reloaded only when this subdomain's type differs from the last
+    if (tx != cur_tx) {
+      const float* gSx = dx.S + (long)tx * mm;
+      for (int idx = lane; idx < MP * MP; idx += 32) {
+        const int a = idx / MP, b = idx - a * MP;
+        Sx[a * SA + b] = (a < m && b < m) ? gSx[a * m + b] : 0.f;
+      }
+      for (int idx = lane; idx < MP; idx += 32) {
+        lx[idx] = idx < m ? dx.lam[tx * m + idx] : 1.f;
+        wx[idx] = idx < m ? dx.w[tx * m + idx] : 0.f;
+      }
+      cur_tx = tx;
+    }
+    if (ty != cur_ty) {
+      const float* gSy = dy.S + (long)ty * mm;
+      for (int idx = lane; idx < MP * MP; idx += 32) {
+        const int a = idx / MP, b = idx - a * MP;
+        Sy[a * SA + b] = (a < m && b < m) ? gSy[a * m + b] : 0.f;
+      }
+      for (int idx = lane; idx < MP; idx += 32) {
+        ly[idx] = idx < m ? dy.lam[ty * m + idx] : 1.f;
+        wy[idx] = idx < m ? dy.w[ty * m + idx] : 0.f;
+      }
+      cur_ty = ty;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx < MP * MP) {
+        const int a = idx / MP, b = idx - a * MP;
+        X[a * SA + b] = xv[q];
+      }
+    }
+    __syncwarp();
+    // P1: Y = S_y^T X
+    warp_gemm<MODE, MP>([&](int row, int k) { return Sy[k * SA + row]; },
+                        [&](int k, int n) { return X[k * SA + n]; },
+                        [&](int row, int col, float v) { Y[row * SA + col] = v; });
+    __syncwarp();
+    // P2: X = (Y S_x) ./ (lam_y + lam_x)
+    warp_gemm<MODE, MP>([&](int row, int k) { return Y[row * SA + k]; },
+                        [&](int k, int n) { return Sx[k * SA + n]; },
+                        [&](int row, int col, float v) { X[row * SA + col] = v / (ly[row] + lx[col]); });
+    __syncwarp();
+    // P3: Y = S_y X
+    warp_gemm<MODE, MP>([&](int row, int k) { return Sy[row * SA + k]; },
+                        [&](int k, int n) { return X[k * SA + n]; },
+                        [&](int row, int col, float v) { Y[row * SA + col] = v; });
+    __syncwarp();
+    // P4: E = w_y w_x^T .* (Y S_x^T), written for the m x m window only
+    const float sc = nu_inv ? nu_inv[sidx] : 1.f;
+    float* Es = E + (long)sidx * mm;
+    warp_gemm<MODE, MP>([&](int row, int k) { return Y[row * SA + k]; },
+                        [&](int k, int n) { return Sx[n * SA + k]; },
+                        [&](int row, int col, float v) {
+                          if (row < m && col < m) Es[row * m + col] = wy[row] * wx[col] * v * sc;
+                        });
+    __syncwarp();
+  }
+}
+
+}  // namespace sem

@@ -81,7 +81,10 @@ struct sem_handle {
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *r_old = nullptr;
   double* fi = nullptr;  // right side of the running MGCG solve (internal copy)
   double* Binv = nullptr;  // dense FP64 inverse of B_0(nu) (variable diffusivity)
-  int* tc_err = nullptr;   // device flag: a tcgen05 sweep gave up waiting
+  int* tc_err = nullptr;   // device flag: a tcgen05 sweep or a grid barrier gave up waiting
+  // levels p_l <= 8 and the coarse solve in one persistent kernel (mixed modes)
+  bool low_ok = false, low_on = false;
+  LowCycle lowc{};
   // the whole MGCG solve as one CUDA graph: prologue + WHILE node over one iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -340,7 +343,9 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
     KL(h, SEM_K_VECTOR, s, (launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
   T* uL = dbl ? reinterpret_cast<T*>(zout) : static_cast<T*>(lv[L].u);
   int rc;
-  for (int l = L; l >= 1; --l) {
+  // levels 1 .. low run in the persistent kernel (0: none)
+  const int low = (!dbl && h->low_ok && h->low_on) ? h->lowc.top : 0;
+  for (int l = L; l >= 1 && l > low; --l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     T* rl = static_cast<T*>(lv[l].r);
     const bool fuse = lv[l].tune.fuse && h->ns1[l] == 1 && !lv[l].var;
@@ -375,14 +380,17 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
        launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
                           static_cast<T*>(lv[l - 1].f), s));
   }
-  if (h->Binv)
+  if (low) {
+    KL(h, SEM_K_LOW_CYCLE, s, launch_low_cycle(h->lowc, h->sweep_mode, 1 << low, nullptr, s));
+  } else if (h->Binv) {
     KL(h, SEM_K_COARSE, s,
        launch_coarse_dense<T>(h->coarse, h->Binv, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
-  else
+  } else {
     KLN(h, SEM_K_COARSE, coarse_launches(h->coarse, !dbl), s,
         launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
+  }
   bool z_written = dbl;
-  for (int l = 1; l <= L; ++l) {
+  for (int l = low + 1; l <= L; ++l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
     if (l == L && !z_written && h->ns2[l] == 0) {
@@ -545,7 +553,10 @@ int take_tc_err(sem_handle* h, cudaStream_t s, bool& hit) {
   CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   hit = e != 0;
-  if (hit) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+  if (hit) {
+    CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+    if (h->lowc.bar) CK(cudaMemsetAsync(h->lowc.bar, 0, 2 * sizeof(unsigned), s));
+  }
   return SEM_OK;
 }
 
@@ -689,6 +700,43 @@ int autotune(sem_handle* h, const std::string& path, cudaStream_t s) {
     if (!rc && !path.empty()) {
       const std::string err = tune_cache_store(path, key, lv.tune);
       if (!err.empty()) rc = fail(SEM_BAD_ARG, err);
+    }
+  }
+  // the persistent low-level cycle against the per-level launches: whole
+  // V-cycles on the FP64 residual buffer, best of 3 x 10
+  if (!rc && h->low_ok) {
+    const std::string key = std::string(prop.name) + "|low-cycle|p=" + std::to_string(h->cfg.p) + "|n_o=" +
+                            std::to_string(h->lev[h->L].n_o) + "|prec=" + std::to_string(h->cfg.precision) +
+                            "|elems=" + std::to_string(h->lev[h->L].x64.n) + "x" + std::to_string(h->lev[h->L].y64.n);
+    TuneVal v;
+    if (!path.empty() && tune_cache_find(path, key, v)) {
+      h->low_on = v.fuse != 0;
+    } else {
+      double best_us[2] = {-1.0, -1.0};
+      for (int on = 0; on <= 1 && !rc; ++on) {
+        h->low_on = on != 0;
+        for (int w = 0; w < 2 && !rc; ++w) rc = precond(h, h->r, h->z, s);
+        for (int batch = 0; batch < 3 && !rc; ++batch) {
+          if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(SEM_CUDA_ERROR, "event");
+          for (int r = 0; r < 10 && !rc; ++r) rc = precond(h, h->r, h->z, s);
+          if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = fail(SEM_CUDA_ERROR, "event");
+          float ms = 0.f;
+          if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = fail(SEM_CUDA_ERROR, "event");
+          const double t = 100.0 * ms;  // microseconds per V-cycle
+          if (!rc && (best_us[on] < 0 || t < best_us[on])) best_us[on] = t;
+        }
+      }
+      if (!rc) {
+        h->low_on = best_us[1] < best_us[0];
+        v = TuneVal{};
+        v.fuse = h->low_on ? 1 : 0;
+        v.us = h->low_on ? best_us[1] : best_us[0];
+        if (!path.empty()) {
+          const std::string err = tune_cache_store(path, key, v);
+          if (!err.empty()) rc = fail(SEM_BAD_ARG, err);
+        }
+      }
     }
   }
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = fail(SEM_CUDA_ERROR, "autotune stream failed");
@@ -1088,6 +1136,31 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     }
     if ((rc = upload(h, &h->Binv, inv))) return bail(rc);
   }
+  // the persistent low-level cycle: mixed tensor-core V-cycle of the Poisson
+  // operator with one pre-smoothing step and none after on levels 1 .. top
+  // (p_top = min(p / 2, 8), windows m <= 16), coarse grid of at most 64 x 64
+  // unknowns per problem
+  if (h->mixed && h->sweep_mode != 0 && L >= 2 && !c.nu_kind && h->coarse.nux <= 64 && h->coarse.nuy <= 64) {
+    const int top_l = std::min(L - 1, 3);
+    bool ok = true;
+    for (int l = 1; l <= top_l; ++l)
+      ok = ok && h->lev[l].m <= 16 && h->ns1[l] == 1 && h->ns2[l] == 0;
+    if (ok) {
+      LowCycle& lc = h->lowc;
+      lc.top = top_l;
+      for (int l = 0; l <= top_l; ++l) {
+        Level& lv = h->lev[l];
+        lc.lev[l] = LowLevel{lv.x32, lv.y32, lv.J32, static_cast<float*>(lv.u), static_cast<float*>(lv.f),
+                             static_cast<float*>(lv.r), static_cast<float*>(lv.E)};
+      }
+      lc.coarse = h->coarse;
+      if ((rc = dev_alloc(h, &lc.cw, (size_t)std::max(1, nb) * 64 * 64)) || (rc = dev_alloc(h, &lc.bar, 2)))
+        return bail(rc);
+      CK(cudaMemset(lc.bar, 0, 2 * sizeof(unsigned)));
+      lc.err = h->tc_err;
+      h->low_ok = h->low_on = true;
+    }
+  }
   // MGCG vectors, partial sums, per-iteration scalars
   h->n = top(h).nodes;
   h->rows_top = c.ny * c.p;
@@ -1337,6 +1410,25 @@ int sem_autotune(sem_handle* h, const char* cache_path, void* stream) {
   return autotune(h, cache_path ? std::string(cache_path) : std::string(), as_stream(stream));
 }
 
+int sem_set_low_cycle(sem_handle* h, int32_t enable) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (enable != 0 && enable != 1) return fail(SEM_BAD_ARG, "enable must be 0 or 1");
+  if (enable && !h->low_ok) return fail(SEM_BAD_ARG, "no persistent low-level cycle for this configuration");
+  CK(cudaDeviceSynchronize());
+  h->low_on = enable != 0;
+  drop_graph(h);
+  return SEM_OK;
+}
+
+int sem_get_low_cycle(const sem_handle* h, int32_t* available, int32_t* enabled) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (available) *available = h->low_ok ? 1 : 0;
+  if (enabled) *enabled = (h->low_ok && h->low_on) ? 1 : 0;
+  return SEM_OK;
+}
+
 int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t) {
   int rc = check_handle(h);
   if (rc) return rc;
@@ -1498,6 +1590,11 @@ int sem_batch_create(const sem_config* cfgs, int32_t n, sem_batch** out) {
     sem_batch_destroy(b);
     return fail(SEM_OOM, "pointer tables");
   }
+  // groups run as concurrent branches of one graph: a grid-wide cooperative
+  // kernel per group could not be resident together, so with several groups
+  // the low levels stay on per-level launches
+  if (b->groups.size() > 1)
+    for (auto& g : b->groups) g.h->low_ok = g.h->low_on = false;
   *out = b;
   return SEM_OK;
 }

@@ -104,6 +104,13 @@ class Solver:
     def get_tune(self, level):
         return B.sem_get_tune(self.h, level)
 
+    def set_low_cycle(self, enable):
+        B.sem_set_low_cycle(self.h, enable)
+
+    def low_cycle(self):
+        """(available, enabled) of the persistent low-level cycle."""
+        return B.sem_get_low_cycle(self.h)
+
     def set_tune_from(self, other):
         """Copy the launch shapes of a handle with the same levels."""
         for l in range(1, self.levels + 1):
