@@ -88,8 +88,10 @@ def test_autotune_cache_roundtrip(tmp_path):
         assert t["fuse"] in (0, 1) and t["spw"] in (1, 2, 4) and t["tc"] in (0, 1) and t["us"] > 0
         assert t["tc"] <= t["tc_available"]
     lines = [json.loads(l) for l in open(path).read().splitlines()]
-    assert len(lines) == S.levels
-    assert len({d["key"] for d in lines}) == S.levels
+    low = [d for d in lines if "|low-cycle|" in d["key"]]
+    assert len(low) == (1 if S.low_cycle()[0] else 0)
+    assert len(lines) == S.levels + len(low)
+    assert len({d["key"] for d in lines}) == len(lines)
     ref = _solves(S, b)
     for it, st, u in ref:
         assert st == P.SEM_OK
@@ -102,7 +104,8 @@ def test_autotune_cache_roundtrip(tmp_path):
         for k in ("fuse", "spw", "tc", "eo"):
             assert again[l][k] == tuned[l][k]
         assert abs(again[l]["us"] - round(tuned[l]["us"], 3)) < 1e-9
-    assert len(open(path).read().splitlines()) == S.levels
+    assert len(open(path).read().splitlines()) == len(lines)
+    assert S2.low_cycle() == S.low_cycle()
     for it, st, u in _solves(S2, b):
         assert (it, st) == ref[0][:2]
         assert np.array_equal(u, ref[0][2])

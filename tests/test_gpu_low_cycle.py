@@ -1,9 +1,8 @@
 """The persistent low-level cycle (levels p_l <= 8 and the coarse solve in one
 cooperative kernel) against the per-level launches and against the FP64
-oracle's V-cycle (Alg. 3), and inside MGCG (Alg. 4): same bodies, so the
-V-cycle corrections agree to FP32 rounding (the coarse solve sums in another
-order); the solve reaches 1e-10 and the FP64 solution; the graph replays the
-first solve bitwise."""
+oracle's V-cycle (Alg. 3), and inside MGCG (Alg. 4): the V-cycle corrections
+agree to the rounding of the reduced-precision sweeps; the solve reaches 1e-10
+and the FP64 solution; the graph replays the first solve bitwise."""
 import numpy as np
 import pytest
 
@@ -60,8 +59,10 @@ def test_low_cycle_matches_launches_and_oracle(case):
     if periodic:
         got_on, got_off, want = got_on - got_on.mean(), got_off - got_off.mean(), want - want.mean()
     scale = np.abs(want).max()
-    assert np.abs(got_on - got_off).max() <= 1e-4 * scale
     u_in = 2.0**-11 if case["precision"] == "tf32" else 2.0**-8
+    # off: the low levels default to the tcgen05 sweep, which rounds its
+    # reduced-precision products in another order than the mma.sync one
+    assert np.abs(got_on - got_off).max() <= 16 * u_in * scale
     assert np.abs(got_on - want).max() <= 64 * u_in * scale
 
 
