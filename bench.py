@@ -259,6 +259,26 @@ def run_learned(args, stream):
     return out
 
 
+def replica_seed(rank):
+    """Seed of the right side rank `rank` solves (independent replicas)."""
+    return SEED + rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the job ends when the last replica does."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, unknowns_per_rank, ms):
+    """Whole-job DOF/s: every rank solved its own problem in at most ms."""
+    return world * unknowns_per_rank / (ms * 1e-3)
+
+
 def run_high_order(args, stream):
     """32 x 32 elements, p = 32 (1,046,529 unknowns), n_o in {1, 2, 3}: BF16
     tensor-core sweeps inside the FP64 MGCG.  Per iteration i the relative
@@ -339,7 +359,7 @@ def run_ours(args):
         S = P.Solver(nx=NX, ny=NY, p=P_ORDER, overlap=n_o, weight=5, precision=prec, tol=TOL, i_max=100)
         # launch shapes per level, timed on this GPU (or read from --tune-cache)
         S.tune = S.autotune(args.tune_cache)
-        fn = SI.uniform_nodal(SEED + rank, S.shape)  # each replica solves its own problem
+        fn = SI.uniform_nodal(replica_seed(rank), S.shape)  # each replica solves its own problem
         b = torch.empty(S.nx_nodes * S.ny_nodes, dtype=torch.float64, device="cuda")
         S.mass(torch.from_numpy(fn.ravel()).cuda(), b)
         return S, b
@@ -393,10 +413,7 @@ def run_ours(args):
         if not is_head:
             _, _, vprof = timed(S, b, 2, 0, profile=True)
             S.profile(False)
-        if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         # solution error against the FP64 solve of the same problem (the FP64
         # path matches the CPU oracle to 1e-12 in the tests)
         u_chk = torch.zeros_like(b)
@@ -405,7 +422,7 @@ def run_ours(args):
             fp64_solution[n_o] = u_chk
         ref = fp64_solution.get(n_o)
         err = (u_chk - ref).norm().item() / ref.norm().item() if ref is not None else None
-        variants[key] = {"dof_per_s": world * S.n_unknowns / (ms * 1e-3), "ms_per_solve": ms,
+        variants[key] = {"dof_per_s": job_throughput(world, S.n_unknowns, ms), "ms_per_solve": ms,
                          "iterations": res.iterations, "status": res.status,
                          "final_rel_residual": res.res / res.res0 if res.res0 else 0.0,
                          "rel_error_vs_fp64": err,
@@ -442,7 +459,7 @@ def run_ours(args):
         e1.synchronize()
         if k >= args.warmup:
             e2e_t.append(e0.elapsed_time(e1))
-    e2e_ms = float(np.mean(e2e_t))
+    e2e_ms = max_over_ranks(float(np.mean(e2e_t)), dist, "cuda")
 
     # roofline of the dominant kernel class, from a profiled pass (same steps)
     _, _, kprof = timed(S, b, args.steps, 1, profile=True)
@@ -495,7 +512,7 @@ def run_ours(args):
         "variants": variants,
         "fp64_value": variants["fp64_no%d" % N_O]["dof_per_s"],
         "speedup_vs_fp64": variants["%s_no%d" % (HEADLINE, N_O)]["dof_per_s"] / variants["fp64_no%d" % N_O]["dof_per_s"],
-        "e2e": {"value": world * S.n_unknowns / (e2e_ms * 1e-3), "unit": "DOF/s",
+        "e2e": {"value": job_throughput(world, S.n_unknowns, e2e_ms), "unit": "DOF/s",
                 "h2d_bytes_per_step": int(b.numel() * 8), "d2h_bytes_per_step": int(b.numel() * 8)},
         "gpu_launches": gpu_launches,
         "roofline": roof,

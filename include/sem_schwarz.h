@@ -269,8 +269,10 @@ int sem_autotune(sem_handle* h, const char* cache_path, void* stream);
  * FP32 coarse solve and the prolongations, with grid barriers instead of kernel
  * boundaries.  Available for the TF32 / BF16 modes of the Poisson operator with
  * one pre-smoothing step and no post-smoothing, windows m <= 16 and coarse
- * grids of at most 64 x 64 unknowns; on by default where available, and
- * sem_autotune keeps it only where it is faster than the per-level launches.
+ * grids of at most 64 x 64 unknowns.  Off by default: measured on one GB300 it
+ * loses to the per-level kernels replayed from the solve graph (64 x 64, p = 16:
+ * 2.69 against 2.31 ms per solve; 14 grid barriers at 2 CTAs per SM cost more
+ * than the launch gaps they remove); sem_autotune turns it on where it wins.
  * A grid barrier that waits more than about a second makes the next
  * synchronous solve return SEM_TIMEOUT.  sem_set_low_cycle(h, 1) fails with
  * SEM_BAD_ARG where it is not available; both calls discard the captured graph. */

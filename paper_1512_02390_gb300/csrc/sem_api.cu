@@ -1158,7 +1158,7 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
         return bail(rc);
       CK(cudaMemset(lc.bar, 0, 2 * sizeof(unsigned)));
       lc.err = h->tc_err;
-      h->low_ok = h->low_on = true;
+      h->low_ok = true;  // off until sem_set_low_cycle or sem_autotune turns it on
     }
   }
   // MGCG vectors, partial sums, per-iteration scalars

@@ -43,8 +43,9 @@ def _vcycle(S, u0, f):
 @pytest.mark.parametrize("case", CASES, ids=_ids)
 def test_low_cycle_matches_launches_and_oracle(case):
     S = P.Solver(**case)
-    avail, on = S.low_cycle()
-    assert avail and on
+    assert S.low_cycle() == (True, False)
+    S.set_low_cycle(True)
+    assert S.low_cycle() == (True, True)
     periodic = case.get("periodic", False)
     H = O.Hierarchy(O.Mesh1D.uniform(case["nx"], 1.0, periodic), O.Mesh1D.uniform(case["ny"], 1.0, periodic),
                     case["p"], overlap=case["overlap"], weight=5)
@@ -69,6 +70,7 @@ def test_low_cycle_matches_launches_and_oracle(case):
 @pytest.mark.parametrize("case", CASES[:3], ids=_ids)
 def test_low_cycle_inside_mgcg(case):
     S = P.Solver(**case)
+    S.set_low_cycle(True)
     S64 = P.Solver(**dict(case, precision="fp64"))
     fn = torch.from_numpy(SI.uniform_nodal(9, S.shape).ravel()).cuda()
     b = torch.empty_like(fn)
