@@ -227,8 +227,8 @@ def run_learned(args, stream):
 
     out = {}
     params, _ = LW.load_model()
-    for p_, no, c in ((16, 2, 10.0), (16, 2, 100.0), (8, 1, 100.0)):
-        kw = dict(nx=64, ny=64, p=p_, overlap=no, x_edges=SI.geometric_edges(64, 1.0 / 64 / 32), nu=("contrast", c),
+    for p_, no, c, n in ((16, 2, 10.0, 64), (16, 2, 100.0, 64), (8, 1, 100.0, 64), (8, 1, 100.0, 16)):
+        kw = dict(nx=n, ny=n, p=p_, overlap=no, x_edges=SI.geometric_edges(n, 1.0 / n / 32), nu=("contrast", c),
                   tol=TOL, i_max=400, precision=HEADLINE)
         px, py = LW.predict(params, **kw)
         row = {}
@@ -253,9 +253,10 @@ def run_learned(args, stream):
             row[name] = {"iterations": res.iterations, "status": res.status, "rbar": res.rbar, "ms": ms,
                          "dof_per_s": (S.n_unknowns / (ms * 1e-3)) if res.status == 0 else 0.0}
             S.close()
-        out["p%d_no%d_contrast%d" % (p_, no, int(c))] = row
-    out["workload"] = ("64x64 elements, p=16 (n_o=2) and p=8 (n_o=1), x geometric 1:32 (first width = h_y/32), "
-                       "nu = 1 + (c-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y), TF32 V-cycle, MGCG to 1e-10")
+        out["%dx%d_p%d_no%d_contrast%d" % (n, n, p_, no, int(c))] = row
+    out["workload"] = ("64x64 (and 16x16) elements, p=16 (n_o=2) and p=8 (n_o=1), x geometric 1:32 (first width = "
+                       "h_y/32), nu = 1 + (c-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y), TF32 V-cycle, MGCG to 1e-10, "
+                       "i_max 400")
     return out
 
 
