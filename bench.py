@@ -339,6 +339,49 @@ def run_high_order(args, stream):
     return out
 
 
+def run_large(args, stream):
+    """256 x 256 elements, p = 16 (16,769,025 unknowns, 134 MB per FP64
+    vector): a working set beyond the 129 MB L2, where the level kernels meet
+    HBM.  TF32 and FP64 V-cycles, MGCG to 1e-10."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    out = {}
+    b = None
+    for prec in ("fp64", HEADLINE):
+        S = P.Solver(nx=256, ny=256, p=16, overlap=2, weight=5, precision=prec, tol=TOL, i_max=100)
+        S.autotune(args.tune_cache)
+        if b is None:
+            fn = torch.from_numpy(SI.uniform_nodal(SEED, S.shape).ravel()).cuda()
+            b = torch.empty_like(fn)
+            S.mass(fn, b)
+            del fn
+        u = torch.zeros_like(b)
+        S.pcg_solve(u, b)
+        times = []
+        for _ in range(3):
+            u.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, _ = S.pcg_solve(u, b)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.mean(times))
+        S.profile(True)
+        u.zero_()
+        S.pcg_solve(u, b)
+        prof = S.profile_read()
+        S.profile(False)
+        out[prec] = {"ms_per_solve": ms, "dof_per_s": S.n_unknowns / (ms * 1e-3), "iterations": res.iterations,
+                     "status": res.status, "class_ms_per_solve": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+        S.close()
+    out["workload"] = "256x256 elements, p=16, n_o=2, Dirichlet, b = M f, f ~ U[-1,1] seed 1, MGCG(1,0) w_5 to 1e-10"
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -523,6 +566,7 @@ def run_ours(args):
         line["batched"] = run_batched(args, flush, stream)
         line["learned"] = run_learned(args, stream)
         line["high_order_bf16"] = run_high_order(args, stream)
+        line["large"] = run_large(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
         line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",
