@@ -263,7 +263,7 @@ template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) k_convert(long n, const TA* __restrict__ a, TB* __restrict__ b) {
   pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    b[i] = TB(a[i]);
+    b[i] = convert_to<TB>(a[i]);
 }
 
 __global__ void __launch_bounds__(256) k_axpy(long n, double alpha, const double* __restrict__ x,

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
       T ys = yc[b * TN];
       if (b == 0) ys += yc[(P - NP) * TN];
       val = sMy[jy] * xs + sMx[ix] * ys;
-      if (f) val = T(f[o]) - val;
+      if (f) val = convert_to<T>(f[o]) - val;
     }
     out[o] = val;
     if (uout) uout[o] = wall ? T(0) : own[q];

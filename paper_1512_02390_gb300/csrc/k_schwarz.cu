@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_scatter(DirView<T> dx, DirView<T> dy, c
         s += E[(long)(ey * dx.n + ex) * mm + a * m + b];
       }
     }
-    u[idx] = accum ? TOut(u[idx] + s) : TOut(s);
+    u[idx] = accum ? TOut(u[idx] + convert_to<TOut>(s)) : convert_to<TOut>(s);
   }
 }
 

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
               gy = node_or_wall(gy, dy.N, dy.periodic, dy.segN);
               gx = node_or_wall(gx, Nx, dx.periodic, dx.segN);
             }
-            if (gx >= 0 && gy >= 0) xv[q] = (float)r[(long)gy * Nx + gx];
+            if (gx >= 0 && gy >= 0) xv[q] = convert_to<float>(r[(long)gy * Nx + gx]);
           }
           a += kTcThreads / 32;
           while (a >= m) a -= m, ++s;
@@ -327,10 +327,10 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(DirView<float> dx, DirV
         for (int b = lane; b < m; b += 32) {
           float x = 0.f;
           if (fl == 1) {
-            x = (float)r[(long)gy * Nx + ox + b];
+            x = convert_to<float>(r[(long)gy * Nx + ox + b]);
           } else if (fl == 2 && gy >= 0) {
             const int gx = node_or_wall(ox + b, Nx, dx.periodic, dx.segN);
-            if (gx >= 0) x = (float)r[(long)gy * Nx + gx];
+            if (gx >= 0) x = convert_to<float>(r[(long)gy * Nx + gx]);
           }
           op_put<MODE>(sA, ro + k_off<MODE>(b), x);
         }

@@ -132,7 +132,7 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
         }
       }
       val = sMy[jy] * xs + sMx[ix] * ys;
-      if (f) val = T(f[o]) - val;
+      if (f) val = convert_to<T>(f[o]) - val;
     }
     out[o] = val;
     if (uout) uout[o] = wall ? T(0) : su[(jy + P) * LP + ix + P];
@@ -275,7 +275,7 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     T v = T(0);
 #pragma unroll
     for (int k = 0; k < NPC; ++k) v += sJ[j * NPC + k] * col[k * TP];
-    out[o] = in ? TOut(in[o] + v) : TOut(v);
+    out[o] = in ? convert_to<TOut>(in[o] + v) : convert_to<TOut>(v);
   }
 }
 
@@ -439,7 +439,7 @@ __device__ __forceinline__ void sweep_mma_warp(const DirView<float>& dx, const D
       if (idx < MP * MP && a < m && b < m) {
         const int gy = node_or_wall(ey * p + a - no, dy.N, dy.periodic, dy.segN);
         const int gx = node_or_wall(ex * p + b - no, dx.N, dx.periodic, dx.segN);
-        if (gx >= 0 && gy >= 0) v = (float)r[(long)gy * dx.N + gx];
+        if (gx >= 0 && gy >= 0) v = convert_to<float>(r[(long)gy * dx.N + gx]);
       }
       xv[q] = v;
     }
