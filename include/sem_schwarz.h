@@ -378,14 +378,6 @@ int sem_batch_launches(const sem_batch* b, int64_t* launches);
  * captures a new batch graph. */
 int sem_batch_autotune(sem_batch* b, const char* cache_path, void* stream);
 
-/* Precision conversion of n values (DEVICE arrays), the one the mixed-precision
- * V-cycle uses on the FP64 residual and the FP64 correction: direction 0
- * binary64 -> binary32 (IEEE 754 round to nearest, ties to even), 1 binary32 ->
- * binary64 (exact).  Bit-identical to the hardware conversion; done with
- * integer operations because the conversion instruction shares GB300's
- * cut-down FP64 pipe. */
-int sem_convert(const void* in, void* out, int64_t n, int32_t direction, void* stream);
-
 /* Name of a status code. */
 const char* sem_status_string(int32_t status);
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
-    "sem_convert", "sem_status_string", "sem_last_error",
+    "sem_status_string", "sem_last_error",
 ]
 SEM_MLP_PARAMS = 4610
 # sem_kernel_class
@@ -128,7 +128,6 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_batch_autotune": (i32, [vp, ctypes.c_char_p, vp]),
         "sem_set_low_cycle": (i32, [vp, i32]),
         "sem_get_low_cycle": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
-        "sem_convert": (i32, [vp, vp, ctypes.c_int64, i32, vp]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -396,16 +395,3 @@ def sem_get_low_cycle(h):
     _check(load_library().sem_get_low_cycle(h, ctypes.byref(a), ctypes.byref(e)))
     return bool(a.value), bool(e.value)
 
-
-def sem_convert(x, out, stream=None) -> None:
-    """out = x in out's precision (float64 <-> float32 CUDA tensors of equal length)."""
-    import torch
-    if x.numel() != out.numel() or not (x.is_cuda and out.is_cuda and x.is_contiguous() and out.is_contiguous()):
-        raise ValueError("expected contiguous CUDA tensors of equal length")
-    if x.dtype == torch.float64 and out.dtype == torch.float32:
-        d = 0
-    elif x.dtype == torch.float32 and out.dtype == torch.float64:
-        d = 1
-    else:
-        raise ValueError("float64 -> float32 or float32 -> float64")
-    _check(load_library().sem_convert(x.data_ptr(), out.data_ptr(), x.numel(), d, _stream(stream)))

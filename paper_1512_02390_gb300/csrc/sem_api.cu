@@ -785,15 +785,6 @@ const char* sem_status_string(int32_t s) {
 
 const char* sem_last_error(void) { return g_err.c_str(); }
 
-int sem_convert(const void* in, void* out, int64_t n, int32_t direction, void* stream) {
-  if (n < 0 || (n > 0 && (!in || !out)) || direction < 0 || direction > 1) return fail(SEM_BAD_ARG, "invalid argument");
-  if (n == 0) return SEM_OK;
-  cudaStream_t s = as_stream(stream);
-  if (direction == 0) CK((launch_convert<double, float>(n, static_cast<const double*>(in), static_cast<float*>(out), s)));
-  else CK((launch_convert<float, double>(n, static_cast<const float*>(in), static_cast<double*>(out), s)));
-  return SEM_OK;
-}
-
 void sem_destroy(sem_handle* h) {
   if (!h) return;
   int prev = -1;
