@@ -190,15 +190,16 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
   // staged values of this thread's owned nodes, kept for the dot product and
   // the assembled-correction output (the y products overwrite the tile)
-  // owned nodes in rows of the widest width W (compile-time divisions)
-  constexpr int W = TN + 1;
-  constexpr int KOWN = (W * W + 255) / 256;
+  constexpr int KOWN = ((TN + 1) * (TN + 1) + 255) / 256;
   T own[KOWN];
 #pragma unroll
   for (int q = 0; q < KOWN; ++q) {
     const int idx = threadIdx.x + 256 * q;
-    const int jy = idx / W, ix = idx - jy * W;
-    own[q] = (jy < owny && ix < ownx) ? su[(jy + P) * LP + ix + P] : T(0);
+    own[q] = T(0);
+    if (idx < ownx * owny) {
+      const int jy = idx / ownx, ix = idx - jy * ownx;
+      own[q] = su[(jy + P) * LP + ix + P];
+    }
   }
   form_eo<T, P, true>(su, ev);
   __syncthreads();
@@ -213,9 +214,8 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
 #pragma unroll
   for (int q = 0; q < KOWN; ++q) {
     const int idx = threadIdx.x + 256 * q;
-    const int jy = idx / W, ix = idx - jy * W;
-    if (jy >= owny) break;
-    if (ix >= ownx) continue;
+    if (idx >= ownx * owny) break;
+    const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
     const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);

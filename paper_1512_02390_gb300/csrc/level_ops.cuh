@@ -95,12 +95,8 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
   double acc = 0.0;
-  // rows of the widest owned width W (compile-time: no integer division by a
-  // runtime value per node)
-  constexpr int W = TN + 1;
-  for (int idx = threadIdx.x; idx < W * owny; idx += blockDim.x) {
-    const int jy = idx / W, ix = idx - jy * W;
-    if (ix >= ownx) continue;
+  for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
     const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
@@ -187,10 +183,8 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
   const int ownx = min(TE, cx.n - E0x) * PC + ((!cx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, cy.n - E0y) * PC + ((!cy.periodic && lasty) ? 1 : 0);
   // x contraction for every staged fine row
-  constexpr int WC = TNC + 1;  // widest owned coarse row (compile-time divisions)
-  for (int idx = threadIdx.x; idx < LN * WC; idx += blockDim.x) {
-    const int ly = idx / WC, ic = idx - ly * WC;
-    if (ic >= ownx) continue;
+  for (int idx = threadIdx.x; idx < LN * ownx; idx += blockDim.x) {
+    const int ly = idx / ownx, ic = idx - ly * ownx;
     const int le = ic / PC, K = ic - le * PC;
     const T* row = sr + ly * LP + le * PF + PF;  // fine local node 0 of element E0x + le
     T t = T(0);
@@ -208,9 +202,8 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
     st[ly * TP + ic] = t;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < owny * WC; idx += blockDim.x) {
-    const int jc = idx / WC, ic = idx - jc * WC;
-    if (ic >= ownx) continue;
+  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
+    const int jc = idx / ownx, ic = idx - jc * ownx;
     const int gI = E0x * PC + ic, gJ = E0y * PC + jc;
     const bool wall = wall_node(gI, cx.N, cx.periodic, cx.segN) || wall_node(gJ, cy.N, cy.periodic, cy.segN);
     T v = T(0);
@@ -256,10 +249,8 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
   const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
   const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
-  constexpr int WF = TNF + 1;  // widest owned fine row (compile-time divisions)
-  for (int idx = threadIdx.x; idx < LC * WF; idx += blockDim.x) {
-    const int ly = idx / WF, ix = idx - ly * WF;
-    if (ix >= ownx) continue;
+  for (int idx = threadIdx.x; idx < LC * ownx; idx += blockDim.x) {
+    const int ly = idx / ownx, ix = idx - ly * ownx;
     const int le = ix / PF, i = ix - le * PF;
     T t = T(0);
     if (le < TE) {
@@ -270,9 +261,8 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     st[ly * TP + ix] = t;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < owny * WF; idx += blockDim.x) {
-    const int jy = idx / WF, ix = idx - jy * WF;
-    if (ix >= ownx) continue;
+  for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
+    const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = E0x * PF + ix, gj = E0y * PF + jy;
     const long o = (long)gj * fx.N + gi;
     const bool wall = wall_node(gi, fx.N, fx.periodic, fx.segN) || wall_node(gj, fy.N, fy.periodic, fy.segN);
