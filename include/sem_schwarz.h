@@ -202,6 +202,17 @@ typedef struct sem_level_info {
 int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info, int32_t* tab_x,
                       double* S_x, double* lam_x, double* w_x, double* coords_x);
 
+/* Host-only: the 1D GLL set of order p that every level is built from
+ * (Sec. 2): nodes xi[p+1] and quadrature weights w[p+1] on [-1, 1], the
+ * differentiation matrix D[(p+1)^2] (row-major, D[i*(p+1) + j] = phi_j'(xi_i))
+ * and the reference stiffness L_ref[(p+1)^2], L_ref_ij = sum_q w_q D_qi D_qj
+ * (an element of width h has stiffness (2/h) L_ref and mass (h/2) w).  Each
+ * entry is the correctly rounded double of its exact value: the set is
+ * computed in double-double arithmetic and rounded once.  Caller-owned HOST
+ * arrays; any pointer may be NULL.  No device work (works without a GPU).
+ * Errors: SEM_BAD_ARG for p < 1 or p > 64. */
+int sem_gll_tables(int32_t p, double* xi, double* w, double* D, double* L_ref);
+
 /* Kernel classes of the tracing counters. */
 typedef enum sem_kernel_class {
   SEM_K_APPLY_FP64 = 0, /* FP64 operator / residual on the finest level (Eq. (system matrix)) */

@@ -52,10 +52,20 @@ design notes of the repository):
      convex blend of the two neighbouring odd-degree shape functions.
   R18 variable diffusivity: B(nu) is the weak form with nu sampled at the GLL
      nodes inside the GLL quadrature of each element.
+  R19 the 1D GLL set (nodes, weights, D and the reference stiffness
+     Lhat = D^T W D of Sec. 2) is taken as the correctly rounded doubles of
+     the exact values: computed in 50-digit decimal arithmetic and rounded
+     once.  The assembled operator is ill-conditioned enough that the
+     discrete solution at 64 x 64 elements, p = 16, moves by ~1e-11 between
+     two double-precision evaluations of Lhat in different summation orders;
+     the exact values are the one reading two independent FP64 codes can
+     share.
 """
 from __future__ import annotations
 
+import functools
 import math
+from decimal import Decimal, localcontext
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -68,29 +78,92 @@ from numpy.polynomial import legendre as npleg
 # ---------------------------------------------------------------------------
 
 
-def gll(p: int):
-    """GLL nodes xi_0..xi_p and quadrature weights on [-1, 1] (Sec. 2).
+_DIGITS = 50  # decimal working precision of the 1D set-up
 
-    Nodes: -1, +1 and the roots of P_p'; weights 2 / (p (p+1) P_p(xi)^2).
-    The interior roots come from numpy's Legendre root finder and are polished
-    by Newton steps on P_p'.
+
+def _legendre_decimal(p: int, x: Decimal):
+    """P_p(x), P_p'(x), P_p''(x) in decimal arithmetic.
+
+    (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1};  differentiating the identity
+    (2k+1) P_k = P'_{k+1} - P'_{k-1} once more gives the derivative recurrences
+    P'_{k+1} = P'_{k-1} + (2k+1) P_k and P''_{k+1} = P''_{k-1} + (2k+1) P'_k.
+    """
+    P0, P1 = Decimal(1), x
+    d0, d1 = Decimal(0), Decimal(1)
+    s0, s1 = Decimal(0), Decimal(0)
+    for k in range(1, p):
+        P0, P1 = P1, ((2 * k + 1) * x * P1 - k * P0) / (k + 1)
+        d0, d1 = d1, d0 + (2 * k + 1) * P0
+        s0, s1 = s1, s0 + (2 * k + 1) * d0
+    return P1, d1, s1
+
+
+@functools.lru_cache(maxsize=None)
+def _gll_exact(p: int):
+    """GLL nodes, weights and differentiation matrix of order p to 50 digits (Sec. 2).
+
+    Nodes: -1, +1 and the roots of P_p', from numpy's Legendre root finder
+    refined by Newton steps on P_p' in decimal arithmetic until a step falls
+    below 1e-45.  Weights: w_j = 2 / (p (p+1) P_p(xi_j)^2).  Differentiation
+    matrix D_ij = phi_j'(xi_i), in the closed form for GLL nodes:
+    P_p(xi_i) / (P_p(xi_j) (xi_i - xi_j)) off the diagonal, -p(p+1)/4 and
+    p(p+1)/4 at the two end points, 0 at the interior diagonal entries.
     """
     if p < 1:
         raise ValueError("p >= 1 required")
-    c = np.zeros(p + 1)
-    c[p] = 1.0
-    dc = npleg.legder(c)
-    if p >= 2:
-        x = np.sort(np.real(npleg.legroots(dc)))
-        ddc = npleg.legder(dc)
-        for _ in range(4):
-            x = x - npleg.legval(x, dc) / npleg.legval(x, ddc)
-        xi = np.concatenate([[-1.0], x, [1.0]])
-    else:
-        xi = np.array([-1.0, 1.0])
-    xi = 0.5 * (xi - xi[::-1])  # exact symmetry xi_{p-i} = -xi_i
-    w = 2.0 / (p * (p + 1) * npleg.legval(xi, c) ** 2)
-    return xi, w
+    with localcontext() as ctx:
+        ctx.prec = _DIGITS
+        x = [Decimal(-1)]
+        if p >= 2:
+            c = np.zeros(p + 1)
+            c[p] = 1.0
+            for x0 in np.sort(np.real(npleg.legroots(npleg.legder(c)))):
+                t = Decimal(float(x0))
+                for _ in range(100):
+                    _, d, s2 = _legendre_decimal(p, t)
+                    step = d / s2
+                    t -= step
+                    if abs(step) < Decimal("1e-45"):
+                        break
+                x.append(t)
+        x.append(Decimal(1))
+        for j in range(p // 2 + 1):  # exact symmetry xi_{p-j} = -xi_j
+            h = (x[p - j] - x[j]) / 2
+            x[j], x[p - j] = -h, h
+        if p % 2 == 0:
+            x[p // 2] = Decimal(0)
+        P = [_legendre_decimal(p, t)[0] for t in x]
+        w = [Decimal(2) / (p * (p + 1) * Pj * Pj) for Pj in P]
+        n = p + 1
+        D = [[Decimal(0)] * n for _ in range(n)]
+        for i in range(n):
+            for j in range(n):
+                if i != j:
+                    D[i][j] = P[i] / (P[j] * (x[i] - x[j]))
+        D[0][0] = Decimal(-p * (p + 1)) / 4
+        D[p][p] = Decimal(p * (p + 1)) / 4
+        # reference stiffness Lhat_ij = sum_q w_q D_qi D_qj (GLL quadrature)
+        L = [[sum(w[q] * D[q][i] * D[q][j] for q in range(n)) for j in range(n)] for i in range(n)]
+        # float(Decimal) is correctly rounded
+        xi = np.array([float(t) for t in x])
+        wf = np.array([float(t) for t in w])
+        Df = np.array([[float(t) for t in row] for row in D])
+        Lf = np.array([[float(t) for t in row] for row in L])
+    for a in (xi, wf, Df, Lf):
+        a.setflags(write=False)
+    return xi, wf, Df, Lf
+
+
+def gll(p: int):
+    """GLL nodes xi_0..xi_p and quadrature weights on [-1, 1] (Sec. 2),
+    each the correctly rounded double of its exact value."""
+    xi, w, _, _ = _gll_exact(p)
+    return xi.copy(), w.copy()
+
+
+def gll_diff(p: int) -> np.ndarray:
+    """D[i, j] = phi_j'(xi_i) on the GLL nodes of order p, correctly rounded."""
+    return _gll_exact(p)[2].copy()
 
 
 def lagrange_matrix(xi: np.ndarray, x: np.ndarray) -> np.ndarray:
@@ -105,7 +178,8 @@ def lagrange_matrix(xi: np.ndarray, x: np.ndarray) -> np.ndarray:
 
 
 def diff_matrix(xi: np.ndarray) -> np.ndarray:
-    """D[i, j] = phi_j'(xi_i), the derivative of the Lagrange basis at the nodes."""
+    """D[i, j] = phi_j'(xi_i) for arbitrary distinct nodes, in double
+    arithmetic (barycentric form; the GLL set uses gll_diff)."""
     n = len(xi)
     c = np.array([np.prod([xi[i] - xi[k] for k in range(n) if k != i]) for i in range(n)])
     D = np.zeros((n, n))
@@ -118,11 +192,14 @@ def diff_matrix(xi: np.ndarray) -> np.ndarray:
 
 
 def element_matrices(p: int, h: float):
-    """1D element mass (diagonal, GLL quadrature) and stiffness on width h (Sec. 2, R1)."""
-    xi, w = gll(p)
-    D = diff_matrix(xi)
+    """1D element mass (diagonal, GLL quadrature) and stiffness on width h (Sec. 2, R1).
+
+    M = (h/2) w and L = (2/h) Lhat with Lhat = D^T W D evaluated exactly and
+    rounded once (reading R19), then scaled by one double multiplication.
+    """
+    _, w, _, Lhat = _gll_exact(p)
     M = 0.5 * h * w
-    L = (2.0 / h) * (D.T @ (w[:, None] * D))
+    L = (2.0 / h) * Lhat
     return M, L
 
 
@@ -297,7 +374,7 @@ class Level:
     def _setup_variable(self, nu):
         """Variable diffusivity nu(x, y) sampled at the GLL nodes (Sec. 4.3)."""
         xi, w = gll(self.p)
-        self.D = diff_matrix(xi)
+        self.D = gll_diff(self.p)
         self.wq = w
         X = self.mx.coords(self.p)
         Y = self.my.coords(self.p)

@@ -29,7 +29,7 @@ SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_TF32, SEM_PREC_BF16 = range(4)
 EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
-    "sem_inspect_level", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
+    "sem_inspect_level", "sem_gll_tables", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
     "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_pcg_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), dp, i32, vp]),
         "sem_inspect_level": (i32, [ctypes.POINTER(sem_config), i32, ctypes.POINTER(sem_level_info),
                                     ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]),
+        "sem_gll_tables": (i32, [i32, dp, dp, dp, dp]),
         "sem_profile": (i32, [vp, i32]),
         "sem_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "sem_schwarz_correction_noalloc": (i32, [ctypes.POINTER(sem_sweep_tables), ctypes.POINTER(sem_sweep_tables),
@@ -266,6 +267,15 @@ def sem_inspect_level(cfg: sem_config, level: int):
                                  tab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), d(S), d(lam), d(w), d(xc)))
     return dict(p=info.p, n_o=info.n_o, m=m, tab=tab, S=S.reshape(nt, m, m), lam=lam.reshape(nt, m),
                 w=w.reshape(nt, m), coords=xc)
+
+
+def sem_gll_tables(p: int):
+    """(xi, w, D, L_ref) of order p as the library builds them; needs no GPU."""
+    n = int(p) + 1
+    xi, w, D, L = np.zeros(n), np.zeros(n), np.zeros((n, n)), np.zeros((n, n))
+    d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(load_library().sem_gll_tables(int(p), d(xi), d(w), d(D), d(L)))
+    return xi, w, D, L
 
 
 def sem_profile(h, enable: bool) -> None:

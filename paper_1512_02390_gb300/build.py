@@ -58,7 +58,9 @@ def build(verbose: bool = False) -> str:
         if _stale(src, obj, deps):
             cmd = [nvcc] + ARCH + common + ["-c", src, "-o", obj]
             if src.endswith(".cpp"):
-                cmd = [nvcc] + common + ["-x", "c++", "-c", src, "-o", obj]
+                # host set-up: no contraction into fused multiply-adds, so that
+                # x86-64 and aarch64 hosts compute the same tables
+                cmd = [nvcc] + common + ["-Xcompiler", "-ffp-contract=off", "-x", "c++", "-c", src, "-o", obj]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

@@ -247,9 +247,11 @@ const T* NUI(const Level& l) {
 // out = A_l u (f null) or f - A_l u on level l; B_l(nu) when nu varies.
 // With E, u is assembled from the Schwarz corrections (fused scatter) and
 // written to uout (Poisson operator only).
+// eo: -2 = the level's tuned form, else the form to use (see launch_apply).
 template <typename T, typename TF = T>
 int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f, T* out, int dot, double* part,
-                int* np, cudaStream_t s, const T* E = nullptr, T* uout = nullptr, PcgFuse pf = PcgFuse()) {
+                int* np, cudaStream_t s, const T* E = nullptr, T* uout = nullptr, PcgFuse pf = PcgFuse(),
+                int eo = -2) {
   if (l.var) {
     if constexpr (std::is_same<T, TF>::value) {
       if (E) return fail(SEM_BAD_ARG, "fused scatter needs the Poisson operator");
@@ -259,7 +261,8 @@ int level_apply(sem_handle* h, const Level& l, int cls, const T* u, const TF* f,
       return fail(SEM_BAD_ARG, "variable operator needs a right side of its own type");
     }
   }
-  KL(h, cls, s, (launch_apply<T, TF>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s, E, uout, pf, l.tune.eo)));
+  KL(h, cls, s, (launch_apply<T, TF>(DX<T>(l), DY<T>(l), u, f, out, dot, part, np, s, E, uout, pf,
+                                     eo == -2 ? l.tune.eo : eo)));
   return SEM_OK;
 }
 
@@ -421,10 +424,16 @@ int precond(sem_handle* h, const double* r, double* z, cudaStream_t s) {
 
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
 
+// The FP64 operator of the outer iteration: it defines the discrete problem.
+// In FP64 mode it applies the element matrices as stored (eo = 0): the
+// even-odd form folds them into (L_ak +- L_a,p-k) / 2, whose roundings move
+// the coefficients by up to half an ulp, and the exact discrete solution with
+// them (by about 1e-11 relative at 64 x 64 elements, p = 16).  The mixed
+// modes, whose solution bar is 1e-9, keep the even-odd form.
 int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s,
             double* part = nullptr, PcgFuse pf = PcgFuse()) {
   return level_apply<double>(h, top(h), SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s, nullptr,
-                             nullptr, pf);
+                             nullptr, pf, h->mixed ? -2 : 0);
 }
 
 // The direction update p = z + beta p of Alg. 4 fused into the FP64 operator
@@ -846,6 +855,21 @@ static bool make_mesh(int n, double len, const double* edges, bool periodic, Mes
   for (int i = 0; i < n; ++i)
     if (!(m.edges[i + 1] > m.edges[i])) return false;
   return true;
+}
+
+int sem_gll_tables(int32_t p, double* xi, double* w, double* D, double* L_ref) {
+  g_err.clear();
+  if (p < 1 || p > 64) return fail(SEM_BAD_ARG, "need 1 <= p <= 64");
+  std::vector<double> x, wq, Dm, M, L;
+  gll(p, x, wq);
+  gll_deriv(p, Dm);
+  element_matrices(p, 2.0, M, L);  // h = 2: the reference element [-1, 1]
+  const size_t n = p + 1;
+  if (xi) std::memcpy(xi, x.data(), n * sizeof(double));
+  if (w) std::memcpy(w, wq.data(), n * sizeof(double));
+  if (D) std::memcpy(D, Dm.data(), n * n * sizeof(double));
+  if (L_ref) std::memcpy(L_ref, L.data(), n * n * sizeof(double));
+  return SEM_OK;
 }
 
 int sem_inspect_level(const sem_config* cfg, int32_t level, sem_level_info* info, int32_t* tab_x, double* S_x,

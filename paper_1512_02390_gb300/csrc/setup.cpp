@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <tuple>
 
@@ -11,12 +12,58 @@ namespace sem {
 
 namespace {
 
-// Legendre P_p(x) and P_{p-1}(x) by the three-term recurrence.
-void legendre(int p, double x, double& Pp, double& Pm1) {
-  double a = 1.0, b = x;  // P_0, P_1
-  if (p == 0) { Pp = 1.0; Pm1 = 0.0; return; }
+// ---- double-double arithmetic ------------------------------------------------
+// A value is the unevaluated sum hi + lo with |lo| <= ulp(hi) / 2 (about 106
+// significant bits).  Built from the error-free transformations of Knuth
+// (two-sum) and Dekker (two-product, here with one fused multiply-add); the
+// 1D matrices below are computed in it and rounded once to double, so that
+// they are the correctly rounded values of their exact definitions.
+struct DD {
+  double hi = 0.0, lo = 0.0;
+  DD() = default;
+  DD(double h) : hi(h) {}  // NOLINT: implicit from double on purpose
+  DD(double h, double l) : hi(h), lo(l) {}
+};
+
+DD two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return DD(s, (a - (s - bb)) + (b - bb));
+}
+DD fast_two_sum(double a, double b) {  // |a| >= |b|
+  const double s = a + b;
+  return DD(s, b - (s - a));
+}
+DD operator+(const DD& a, const DD& b) {
+  DD s = two_sum(a.hi, b.hi);
+  const DD t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(s.hi, s.lo + t.lo);
+}
+DD operator-(const DD& a) { return DD(-a.hi, -a.lo); }
+DD operator-(const DD& a, const DD& b) { return a + (-b); }
+DD operator*(const DD& a, const DD& b) {
+  const double p = a.hi * b.hi;
+  const double e = std::fma(a.hi, b.hi, -p);
+  const double c = a.hi * b.lo;
+  const double d = a.lo * b.hi;
+  return fast_two_sum(p, e + (c + d));
+}
+DD operator/(const DD& a, const DD& b) {  // long division, three partial quotients
+  const double q1 = a.hi / b.hi;
+  DD r = a - b * DD(q1);
+  const double q2 = r.hi / b.hi;
+  r = r - b * DD(q2);
+  const double q3 = r.hi / b.hi;
+  return fast_two_sum(q1, q2) + DD(q3);
+}
+double fabs_dd(const DD& a) { return std::fabs(a.hi); }
+
+// P_p(x) and P_{p-1}(x) by the three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}.
+void legendre_dd(int p, const DD& x, DD& Pp, DD& Pm1) {
+  DD a(1.0), b = x;
+  if (p == 0) { Pp = DD(1.0); Pm1 = DD(0.0); return; }
   for (int k = 1; k < p; ++k) {
-    double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+    const DD c = (DD(2.0 * k + 1.0) * x * b - DD((double)k) * a) / DD(k + 1.0);
     a = b;
     b = c;
   }
@@ -24,59 +71,105 @@ void legendre(int p, double x, double& Pp, double& Pm1) {
   Pm1 = a;
 }
 
-}  // namespace
-
-void gll(int p, std::vector<double>& xi, std::vector<double>& w) {
-  xi.assign(p + 1, 0.0);
-  w.assign(p + 1, 0.0);
-  xi[0] = -1.0;
-  xi[p] = 1.0;
-  // interior nodes: roots of P_p'.  Newton on P_p' with P_p'' from the
-  // Legendre equation (1-x^2) P'' = 2x P' - p(p+1) P, started at the
-  // Chebyshev-Gauss-Lobatto points.
+// GLL nodes and weights in double-double: interior nodes are the roots of
+// P_p'; Newton on P_p' with P_p' = p (x P_p - P_{p-1}) / (x^2 - 1) and P_p''
+// from the Legendre equation (1 - x^2) P'' = 2x P' - p(p+1) P, started at the
+// Chebyshev-Gauss-Lobatto points (quadratic convergence; the loop stops once
+// a step is below 1e-30).  Weights w_j = 2 / (p (p+1) P_p(xi_j)^2).
+void gll_dd(int p, std::vector<DD>& xi, std::vector<DD>& w) {
+  xi.assign(p + 1, DD(0.0));
+  w.assign(p + 1, DD(0.0));
+  xi[0] = DD(-1.0);
+  xi[p] = DD(1.0);
+  const DD pp1(p * (p + 1.0));
   for (int j = 1; j < p; ++j) {
-    double x = -std::cos(M_PI * j / p);
-    for (int it = 0; it < 100; ++it) {
-      double P, Pm;
-      legendre(p, x, P, Pm);
-      double dP = p * (x * P - Pm) / (x * x - 1.0);
-      double d2P = (2.0 * x * dP - p * (p + 1.0) * P) / (1.0 - x * x);
-      double dx = dP / d2P;
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
+    DD x(-std::cos(M_PI * j / p));
+    for (int it = 0; it < 200; ++it) {
+      DD P, Pm;
+      legendre_dd(p, x, P, Pm);
+      const DD x2m1 = x * x - DD(1.0);
+      const DD dP = DD((double)p) * (x * P - Pm) / x2m1;
+      const DD d2P = (DD(2.0) * x * dP - pp1 * P) / (-x2m1);
+      const DD dx = dP / d2P;
+      x = x - dx;
+      if (fabs_dd(dx) < 1e-30) break;
     }
     xi[j] = x;
   }
-  for (int j = 0; j <= p / 2; ++j) {  // exact symmetry
-    double s = 0.5 * (xi[p - j] - xi[j]);
+  for (int j = 0; j <= p / 2; ++j) {  // exact symmetry xi_{p-j} = -xi_j
+    const DD s = (xi[p - j] - xi[j]) * DD(0.5);
     xi[j] = -s;
     xi[p - j] = s;
   }
-  if (p % 2 == 0) xi[p / 2] = 0.0;
+  if (p % 2 == 0) xi[p / 2] = DD(0.0);
   for (int j = 0; j <= p; ++j) {
-    double P, Pm;
-    legendre(p, xi[j], P, Pm);
-    w[j] = 2.0 / (p * (p + 1.0) * P * P);
+    DD P, Pm;
+    legendre_dd(p, xi[j], P, Pm);
+    w[j] = DD(2.0) / (pp1 * P * P);
   }
 }
 
-void deriv_matrix(const std::vector<double>& xi, std::vector<double>& D) {
-  const int n = (int)xi.size();
-  std::vector<double> c(n, 1.0);  // c_i = prod_{k != i} (xi_i - xi_k)
+// D_ij = phi_j'(xi_i) on the GLL nodes in double-double: off the diagonal the
+// barycentric form c_i / (c_j (xi_i - xi_j)), c_i = prod_{k != i} (xi_i - xi_k);
+// on it the GLL values -p(p+1)/4, p(p+1)/4 at the end points and 0 inside.
+void gll_deriv_dd(int p, const std::vector<DD>& xi, std::vector<DD>& D) {
+  const int n = p + 1;
+  std::vector<DD> c(n, DD(1.0));
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k)
-      if (k != i) c[i] *= xi[i] - xi[k];
-  D.assign(n * n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double diag = 0.0;
-    for (int j = 0; j < n; ++j) {
-      if (j == i) continue;
-      D[i * n + j] = c[i] / (c[j] * (xi[i] - xi[j]));
-      diag += 1.0 / (xi[i] - xi[j]);
-    }
-    D[i * n + i] = diag;
-  }
+      if (k != i) c[i] = c[i] * (xi[i] - xi[k]);
+  D.assign(n * n, DD(0.0));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (j != i) D[i * n + j] = c[i] / (c[j] * (xi[i] - xi[j]));
+  D[0] = DD(-0.25 * p * (p + 1.0));
+  D[n * n - 1] = DD(0.25 * p * (p + 1.0));
 }
+
+// The correctly rounded 1D set of order p (computed once per order).
+struct GllSet {
+  std::vector<double> xi, w, D, Lhat;
+};
+
+const GllSet& gll_set(int p) {
+  static std::map<int, GllSet> cache;  // entries are never erased: references stay valid
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(p);
+  if (it != cache.end()) return it->second;
+  std::vector<DD> x, w, D;
+  gll_dd(p, x, w);
+  gll_deriv_dd(p, x, D);
+  const int n = p + 1;
+  GllSet g;
+  g.xi.resize(n);
+  g.w.resize(n);
+  g.D.resize(n * n);
+  g.Lhat.resize(n * n);
+  for (int i = 0; i < n; ++i) {
+    g.xi[i] = x[i].hi;
+    g.w[i] = w[i].hi;
+  }
+  for (int i = 0; i < n * n; ++i) g.D[i] = D[i].hi;
+  // reference stiffness Lhat_ij = sum_q w_q D_qi D_qj (Sec. 2, GLL quadrature)
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      DD s(0.0);
+      for (int q = 0; q < n; ++q) s = s + w[q] * D[q * n + i] * D[q * n + j];
+      g.Lhat[i * n + j] = s.hi;
+    }
+  return cache.emplace(p, std::move(g)).first->second;
+}
+
+}  // namespace
+
+void gll(int p, std::vector<double>& xi, std::vector<double>& w) {
+  const GllSet& g = gll_set(p);
+  xi = g.xi;
+  w = g.w;
+}
+
+void gll_deriv(int p, std::vector<double>& D) { D = gll_set(p).D; }
 
 void lagrange_eval(const std::vector<double>& xi, const std::vector<double>& x,
                    std::vector<double>& out) {
@@ -89,20 +182,14 @@ void lagrange_eval(const std::vector<double>& xi, const std::vector<double>& x,
 }
 
 void element_matrices(int p, double h, std::vector<double>& M, std::vector<double>& L) {
-  std::vector<double> xi, w, D;
-  gll(p, xi, w);
-  deriv_matrix(xi, D);
+  const GllSet& g = gll_set(p);
   const int n = p + 1;
   M.resize(n);
-  L.assign(n * n, 0.0);
-  for (int i = 0; i < n; ++i) M[i] = 0.5 * h * w[i];
-  // L_ij = (2/h) sum_q w_q D_qi D_qj
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      double s = 0.0;
-      for (int q = 0; q < n; ++q) s += w[q] * D[q * n + i] * D[q * n + j];
-      L[i * n + j] = (2.0 / h) * s;
-    }
+  L.resize(n * n);
+  for (int i = 0; i < n; ++i) M[i] = 0.5 * h * g.w[i];
+  // L = (2/h) Lhat, Lhat correctly rounded: one rounding of the scaled value
+  const double s = 2.0 / h;
+  for (int i = 0; i < n * n; ++i) L[i] = s * g.Lhat[i];
 }
 
 bool gen_eig_diag(int n, const std::vector<double>& A, const std::vector<double>& b,
@@ -376,7 +463,7 @@ double nu_value(int kind, double a, double b, double x, double y) {
 void build_var(const Mesh1D& mx, const Mesh1D& my, int p, int kind, double a, double b, VarData& o) {
   std::vector<double> xi, w;
   gll(p, xi, w);
-  deriv_matrix(xi, o.D);
+  gll_deriv(p, o.D);
   const int np1 = p + 1, nn = np1 * np1;
   o.Gx.assign((size_t)mx.n * my.n * nn, 0.0);
   o.Gy.assign((size_t)mx.n * my.n * nn, 0.0);

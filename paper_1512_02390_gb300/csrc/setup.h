@@ -31,14 +31,17 @@ struct Mesh1D {
   }
 };
 
-// GLL nodes and weights on [-1, 1] (Newton iteration on the Legendre recurrence).
+// GLL nodes and weights on [-1, 1] (Sec. 2), computed in double-double
+// arithmetic and rounded once: the correctly rounded values.
 void gll(int p, std::vector<double>& xi, std::vector<double>& w);
-// D[i*(p+1) + j] = phi_j'(xi_i).
-void deriv_matrix(const std::vector<double>& xi, std::vector<double>& D);
+// The GLL differentiation matrix D[i*(p+1) + j] = phi_j'(xi_i), correctly rounded.
+void gll_deriv(int p, std::vector<double>& D);
 // Lagrange basis on nodes xi evaluated at points x: out[i*n + k] = phi_k(x_i).
 void lagrange_eval(const std::vector<double>& xi, const std::vector<double>& x,
                    std::vector<double>& out);
-// 1D element mass (GLL diagonal, p+1) and stiffness ((p+1)^2) of width h.
+// 1D element mass (GLL diagonal, p+1) and stiffness ((p+1)^2) of width h:
+// M = (h/2) w and L = (2/h) Lhat, Lhat_ij = sum_q w_q D_qi D_qj correctly
+// rounded, each scaled with one double multiplication.
 void element_matrices(int p, double h, std::vector<double>& M, std::vector<double>& L);
 // Symmetric-definite eigenproblem A s = lambda diag(b) s by cyclic Jacobi on
 // diag(b)^{-1/2} A diag(b)^{-1/2}.  S (n x n, row-major, columns = vectors with

@@ -86,3 +86,21 @@ def test_host_tables_match_oracle(lib, periodic, nx, p, overlap, weight, edges):
         # padding: zero rows outside the window, unit eigenvalue slots
         pad = np.setdiff1d(np.arange(m), slots)
         assert np.all(t["S"][tid][pad] == 0) and np.all(t["lam"][tid][mv:] == 1.0)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 8, 16, 32, 64])
+def test_gll_tables_equal_the_oracle_bitwise(lib, p):
+    """The library's 1D set (double-double arithmetic, rounded once) and the
+    oracle's (50-digit decimal, rounded once) are both the correctly rounded
+    values, so they agree bit for bit although no code is shared."""
+    xi, w, D, L = P.sem_gll_tables(p)
+    oxi, ow = O.gll(p)
+    _, oL = O.element_matrices(p, 2.0)
+    for a, b in ((xi, oxi), (w, ow), (D, O.gll_diff(p)), (L, oL)):
+        assert np.array_equal(a, b)
+
+
+def test_gll_tables_reject_bad_order(lib):
+    for p in (0, 65):
+        with pytest.raises(P.SemError):
+            P.sem_gll_tables(p)

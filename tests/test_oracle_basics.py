@@ -23,6 +23,60 @@ def test_gll_closed_form_p4():
     np.testing.assert_allclose(w, [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10], atol=1e-15)
 
 
+def _cr_sqrt(num, den):
+    """Correctly rounded sqrt(num / den) (60-digit decimal square root)."""
+    from decimal import Decimal, localcontext
+    with localcontext() as c:
+        c.prec = 60
+        return float((Decimal(num) / Decimal(den)).sqrt())
+
+
+def test_gll_closed_forms_are_correctly_rounded():
+    """Reading R19: nodes, weights, D and Lhat equal, bit for bit, the
+    correctly rounded closed forms (Python's rational division and the
+    decimal square root round correctly)."""
+    cases = {
+        1: ([-1.0, 1.0], [1.0, 1.0]),
+        2: ([-1.0, 0.0, 1.0], [1 / 3, 4 / 3, 1 / 3]),
+        3: ([-1.0, -_cr_sqrt(1, 5), _cr_sqrt(1, 5), 1.0], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+        4: ([-1.0, -_cr_sqrt(3, 7), 0.0, _cr_sqrt(3, 7), 1.0], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+    }
+    for p, (x, w) in cases.items():
+        xi, wq = O.gll(p)
+        assert np.array_equal(xi, np.array(x)) and np.array_equal(wq, np.array(w)), p
+    # p = 2 on [-1, 1]: phi_j' at the nodes and the exact stiffness (1/6)[7 -8 1; -8 16 -8; 1 -8 7]
+    assert np.array_equal(O.gll_diff(2), np.array([[-1.5, 2.0, -0.5], [-0.5, 0.0, 0.5], [0.5, -2.0, 1.5]]))
+    _, L2 = O.element_matrices(2, 2.0)
+    assert np.array_equal(L2, np.array([[7 / 6, -4 / 3, 1 / 6], [-4 / 3, 8 / 3, -4 / 3], [1 / 6, -4 / 3, 7 / 6]]))
+    _, L1 = O.element_matrices(1, 2.0)
+    assert np.array_equal(L1, np.array([[0.5, -0.5], [-0.5, 0.5]]))
+
+
+@pytest.mark.parametrize("p", [3, 5, 8, 13, 16, 24, 32])
+def test_reference_stiffness_is_correctly_rounded(p):
+    """Lhat (h = 2) keeps the exact identities bit for bit (symmetry,
+    centro-symmetry of the GLL nodes) and its rows, whose exact sums vanish
+    (constants have zero derivative), sum exactly to at most half an ulp per
+    entry: a bound that a correctly rounded matrix meets and a plain double
+    evaluation of D^T W D (tens of ulps off at p = 16) does not."""
+    import math as m
+    _, L = O.element_matrices(p, 2.0)
+    assert np.array_equal(L, L.T)
+    assert np.array_equal(L, L[::-1, ::-1])
+    for row in L:
+        assert abs(m.fsum(row)) <= 0.5 * sum(np.spacing(np.abs(row)))
+    # the same bound fails for the double-precision evaluation at this size
+    if p == 16:
+        xi, w = O.gll(p)
+        D = O.diff_matrix(xi)
+        Ld = D.T @ (w[:, None] * D)
+        assert any(abs(m.fsum(r)) > 0.5 * sum(np.spacing(np.abs(r))) for r in Ld)
+    # interior diagonal of D is exactly zero, the end points -p(p+1)/4, p(p+1)/4
+    D = O.gll_diff(p)
+    assert D[0, 0] == -p * (p + 1) / 4 and D[p, p] == p * (p + 1) / 4
+    assert np.all(np.diag(D)[1:-1] == 0.0)
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 5, 8, 13, 16, 32])
 def test_gll_quadrature_exact_to_degree_2p_minus_1(p):
     xi, w = O.gll(p)
