@@ -32,6 +32,9 @@ CASES = [
     dict(nx=16, ny=12, p=8, overlap=2, periodic=True),      # m = 13, one table class
     dict(nx=12, ny=10, p=16, overlap=2),                    # m = 21, the bench's window
     dict(nx=12, ny=9, p=16, overlap=1),                     # m = 19
+    dict(nx=10, ny=8, p=16, overlap=3, periodic=True),      # m = 23, periodic wrap of every window
+    dict(nx=12, ny=12, p=16, overlap=2, stretch=True),      # m = 21, a table per column (tables change mid-range)
+    dict(nx=12, ny=10, p=16, overlap=1, nu=("contrast", 10.0)),  # m = 19, 1 / nu_bar per subdomain
     dict(nx=7, ny=6, p=32, overlap=2),                      # m = 37, three per stack, 48-column accumulator
     dict(nx=24, ny=24, p=8, overlap=1, stretch=True),       # x geometric: a table per column
     dict(nx=16, ny=16, p=8, overlap=1, nu=("contrast", 10.0)),  # 1 / nu_bar per subdomain
