@@ -459,8 +459,12 @@ struct TcGeo {
   static constexpr uint32_t LBO_B = NP * 16 + 16;
   static constexpr uint32_t A_BYTES = KC * LBO_A;
   static constexpr uint32_t B_BYTES = KC * LBO_B;
+  // the stack buffer also stages the G output blocks of M x M floats
+  static constexpr uint32_t STAGE_BYTES = (uint32_t)(G * M * M * sizeof(float));
+  static constexpr uint32_t A_REGION = ((A_BYTES > STAGE_BYTES ? A_BYTES : STAGE_BYTES) + 15u) / 16u * 16u;
+  static constexpr int PAD_CHUNK = M / EPC;  // first K chunk that holds padding columns
   static constexpr int COLS = NP <= 32 ? 32 : 64;
-  static constexpr size_t SMEM = A_BYTES + 4 * (size_t)B_BYTES + (size_t)(M * M + 64) * sizeof(float);
+  static constexpr size_t SMEM = A_REGION + 4 * (size_t)B_BYTES + (size_t)(M * M + M) * sizeof(float);
   static_assert(M <= 32 && ROWS <= kTcThreads && KP >= M, "window size outside the row-linear kernel");
   __host__ __device__ static constexpr uint32_t off_a(int r, int k) {
     return (uint32_t)(k / EPC) * LBO_A + (uint32_t)r * 16u + (uint32_t)(k % EPC) * ES;
@@ -517,17 +521,19 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
   pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
-  unsigned char* sB = smem + Q::A_BYTES;  // B1 = S_x^T, B2 = S_y^T, B3 = S_y, B4 = diag(w_x) S_x (N x K rows)
+  unsigned char* sB = smem + Q::A_REGION;  // B1 = S_x^T, B2 = S_y^T, B3 = S_y, B4 = diag(w_x) S_x (N x K rows)
   float* inv = reinterpret_cast<float*>(sB + 4 * Q::B_BYTES);  // [ah * M + bh] = 1 / (lambda_y[ah] + lambda_x[bh])
   float* wys = inv + M * M;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
   __shared__ int s_flag;
-  // the stack's subdomains and their 1 / nu_bar_s (1 for the Poisson operator),
-  // double-buffered by stack parity: the next stack writes them while the
-  // last epilogue of the previous one may still read
-  __shared__ int s_sub[2][Q::G];
-  __shared__ float s_scale[2][Q::G];
+  // metadata of kChunk stacks at a time, loaded once per chunk: the slots'
+  // subdomains [gi * G + s], their 1 / nu_bar_s (1 for the Poisson
+  // operator) and each stack's table pair tx | ty << 16
+  constexpr int kChunk = 16;
+  __shared__ int s_sub[kChunk * Q::G];
+  __shared__ float s_scale[kChunk * Q::G];
+  __shared__ int s_tab[kChunk];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t bar = smem_addr(&mbar);
   if (t == 0) {
@@ -556,29 +562,68 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
   const int g0 = blockIdx.x * per, g1 = min(wk.ngroups, g0 + per);
   int cur_tx = -1, cur_ty = -1;
   uint32_t phase = 0;
-  for (int g = g0; g < g1 && ok; ++g) {
-    const int* sub = wk.sub + (long)g * Q::G;
-    const int first = sub[0];
-    const int tx = dx.tab[first % dx.n], ty = dy.tab[first / dx.n];
+  for (int c0 = g0; c0 < g1 && ok; c0 += kChunk) {
+  const int cn = min(kChunk, g1 - c0);
+  __syncthreads();  // the previous chunk's last epilogue has read s_sub / s_scale
+  for (int i = t; i < cn * Q::G; i += kTcThreads) s_sub[i] = wk.sub[(long)c0 * Q::G + i];
+  __syncthreads();
+  for (int i = t; i < cn * Q::G; i += kTcThreads) {
+    const int v = s_sub[i];
+    s_scale[i] = (v >= 0 && nu_inv) ? nu_inv[v] : 1.f;
+  }
+  for (int i = t; i < cn; i += kTcThreads) {
+    const int first = s_sub[i * Q::G];  // slot 0 of a stack is never empty
+    s_tab[i] = dx.tab[first % dx.n] | (dy.tab[first / dx.n] << 16);
+  }
+  __syncthreads();
+  for (int gi = 0; gi < cn && ok; ++gi) {
+    const int* sub = s_sub + gi * Q::G;
+    const int tx = s_tab[gi] & 0xffff, ty = s_tab[gi] >> 16;
     if (tx != cur_tx || ty != cur_ty) {
       __syncthreads();  // the previous stack's epilogues have read inv / wys
       const float* Sx = dx.S + (long)tx * M * M;
       const float* Sy = dy.S + (long)ty * M * M;
       const float* wx = dx.w + (long)tx * M;
-      for (int idx = t; idx < Q::NP * Q::KP; idx += kTcThreads) {
+      // every load of this thread first, then the stores: one memory latency
+      constexpr int TI = (Q::NP * Q::KP + kTcThreads - 1) / kTcThreads;
+      constexpr int LI = (M * M + kTcThreads - 1) / kTcThreads;
+      float b1[TI], b2[TI], b3[TI], b4[TI], ly[LI], lx[LI];
+#pragma unroll
+      for (int q = 0; q < TI; ++q) {
+        const int idx = t + q * kTcThreads;
         const int n = idx / Q::KP, k = idx - n * Q::KP;
-        const bool in = n < M && k < M;
-        const uint32_t o = Q::off_b(n, k);
-        op_put<MODE>(sB, o, in ? Sx[k * M + n] : 0.f);
-        op_put<MODE>(sB + Q::B_BYTES, o, in ? Sy[k * M + n] : 0.f);
-        op_put<MODE>(sB + 2 * Q::B_BYTES, o, in ? Sy[n * M + k] : 0.f);
-        op_put<MODE>(sB + 3 * Q::B_BYTES, o, in ? wx[n] * Sx[n * M + k] : 0.f);
+        const bool in = idx < Q::NP * Q::KP && n < M && k < M;
+        b1[q] = in ? Sx[k * M + n] : 0.f;
+        b2[q] = in ? Sy[k * M + n] : 0.f;
+        b3[q] = in ? Sy[n * M + k] : 0.f;
+        b4[q] = in ? wx[n] * Sx[n * M + k] : 0.f;
       }
-      for (int i = t; i < M * M; i += kTcThreads) {
+#pragma unroll
+      for (int q = 0; q < LI; ++q) {
+        const int i = t + q * kTcThreads;
         const int ah = i / M, bh = i - ah * M;
-        inv[i] = 1.f / (dy.lam[(long)ty * M + ah] + dx.lam[(long)tx * M + bh]);
+        ly[q] = i < M * M ? dy.lam[(long)ty * M + ah] : 1.f;
+        lx[q] = i < M * M ? dx.lam[(long)tx * M + bh] : 0.f;
       }
-      for (int i = t; i < M; i += kTcThreads) wys[i] = dy.w[(long)ty * M + i];
+      const float wy_t = t < M ? dy.w[(long)ty * M + t] : 0.f;
+#pragma unroll
+      for (int q = 0; q < TI; ++q) {
+        const int idx = t + q * kTcThreads;
+        if (idx < Q::NP * Q::KP) {
+          const int n = idx / Q::KP, k = idx - n * Q::KP;
+          const uint32_t o = Q::off_b(n, k);
+          op_put<MODE>(sB, o, b1[q]);
+          op_put<MODE>(sB + Q::B_BYTES, o, b2[q]);
+          op_put<MODE>(sB + 2 * Q::B_BYTES, o, b3[q]);
+          op_put<MODE>(sB + 3 * Q::B_BYTES, o, b4[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < LI; ++q) {
+        const int i = t + q * kTcThreads;
+        if (i < M * M) inv[i] = 1.f / (ly[q] + lx[q]);
+      }
+      if (t < M) wys[t] = wy_t;
       cur_tx = tx;
       cur_ty = ty;
     }
@@ -598,11 +643,6 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
                           (dx.segN == 0 || (ox_l - 1) / dx.segN == (ox_l + M - 1) / dx.segN);
         fl_l = (in_x && in_y && !dx.periodic && !dy.periodic) ? 1 : 2;
       }
-    }
-    if (warp == 0 && lane < Q::G) {  // for the last epilogue
-      const int sidx = sub[lane];
-      s_sub[g & 1][lane] = sidx;
-      s_scale[g & 1][lane] = (sidx >= 0 && nu_inv) ? nu_inv[sidx] : 1.f;
     }
     // gather R_s r: warp w takes window rows w, w + 4, ... of every slot, lane
     // b node b of the row; the loads of SB slots at a time are all issued
@@ -719,21 +759,42 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
     // G4: E_s[a][b] = w_y[a] / nu_bar_s * sum_bh A4[(s, a)][bh] w_x[b] S_x[b][bh]
     ok = tcm_step<Q, MODE>(tmem, a_s, b_s + 3 * Q::B_BYTES, bar, phase, &s_flag);
     if (ok) {
-      const int sidx = row_ok ? s_sub[g & 1][s_me] : -1;
-      const float f = sidx >= 0 ? wys[j_me] * s_scale[g & 1][s_me] : 0.f;
-      float* Es = E + (long)max(sidx, 0) * (M * M) + j_me * M;
+      // the weighted rows go to the free stack buffer as the E blocks
+      // [s][a][b]; warp w then copies blocks w, w + 4, ... to E with
+      // consecutive lanes on consecutive floats
+      float* stage = reinterpret_cast<float*>(sA);
+      const float f = row_ok ? wys[j_me] * s_scale[gi * Q::G + s_me] : 0.f;
 #pragma unroll
       for (int c = 0; c < Q::NPC; ++c) {
         float v[16];
         tmem_ld16(taddr + c * 16, v);
         tmem_wait_ld();
-        if (sidx >= 0) {
+        if (row_ok) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (c * 16 + i < M) Es[c * 16 + i] = v[i] * f;
+            if (c * 16 + i < M) stage[t * M + c * 16 + i] = v[i] * f;
         }
       }
+      __syncthreads();
+#pragma unroll
+      for (int sl = warp; sl < Q::G; sl += kTcThreads / 32) {
+        const int sidx = sub[sl];
+        if (sidx >= 0) {
+          float* Es = E + (long)sidx * (M * M);
+          const float* src = stage + sl * (M * M);
+#pragma unroll
+          for (int i = lane; i < M * M; i += 32) Es[i] = src[i];
+        }
+      }
+      __syncthreads();
+      // the staged floats overwrote the zero K padding of the stack operand
+      // (as BF16 pairs they can read as NaN); the next gather's barrier
+      // orders this before the next product
+      for (int i = t; i < (Q::KC - Q::PAD_CHUNK) * kTcThreads; i += kTcThreads)
+        *reinterpret_cast<uint4*>(sA + (uint32_t)(Q::PAD_CHUNK + i / kTcThreads) * Q::LBO_A +
+                                  (uint32_t)(i % kTcThreads) * 16u) = make_uint4(0, 0, 0, 0);
     }
+  }
   }
   if (!ok && t == 0) {
     atomicExch(wk.err, 1);
