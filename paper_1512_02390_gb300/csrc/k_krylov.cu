@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
                                                          const double* __restrict__ part_pq, int npq, PcgState st,
                                                          double* __restrict__ part_rr, int i_max,
                                                          cudaGraphConditionalHandle cond, int use_cond,
-                                                         const double* __restrict__ z) {
+                                                         const double* __restrict__ z, float* __restrict__ r32) {
   pdl_enter();
   __shared__ double sred[kRedThreads];
   __shared__ int am_last;
@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
         u[i] += alpha * pi;
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         acc += ri * ri;
       }
     } else {
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
         u[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         acc += ri * ri;
       }
     }
@@ -351,10 +353,10 @@ int chunk_grid(const PcgState& st) {
 cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
                                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
-                                       const double* z) {
+                                       const double* z, float* r32) {
   dim3 grid(chunk_grid(st), st.nb);
   {
-    const cudaError_t e_ = launch_pdl(k_update_ur_check, dim3(grid), dim3(256), 0, s, n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z);
+    const cudaError_t e_ = launch_pdl(k_update_ur_check, dim3(grid), dim3(256), 0, s, n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z, r32);
     if (e_ != cudaSuccess) return e_;
   }
   return cudaGetLastError();

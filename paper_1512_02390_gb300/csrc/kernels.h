@@ -157,11 +157,13 @@ struct PcgState {
 int elementwise_grid(long n);
 // CTAs per problem of the batched vector kernels (grid = (chunks, nb))
 int chunk_grid(const PcgState& st);
-// z != nullptr: first p = z + beta_i p (beta_i from launch_dot2_beta), stored
+// z != nullptr: first p = z + beta_i p (beta_i from launch_dot2_beta), stored;
+// r32 != nullptr: the updated residual is also written rounded to FP32 (the
+// right side of a mixed-precision V-cycle)
 cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, const double* q,
                                        const double* part_pq, int npq, PcgState st, double* part_rr, int i_max,
                                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
-                                       const double* z = nullptr);
+                                       const double* z = nullptr, float* r32 = nullptr);
 // i = iter[1]: per problem beta_i = z^T (r - r_old) / delta_{i-1} with
 // r - r_old = -alpha_i q (r_old = 0 at i = 1) and delta_i = z^T r, reduced by
 // the last CTA and stored in the scalar histories

@@ -333,16 +333,18 @@ int level_down_fused(sem_handle* h, const Level& l, const TF* f, T* u, cudaStrea
 }
 
 // z = MultigridCycle(0, rtop), Alg. 3, with the level vectors in type T.  In
-// the mixed mode the finest level reads the FP64 residual directly.
+// the mixed mode the finest level's right side is rtop rounded to FP32 in
+// lv[L].f: written here, or already by the residual update of the outer
+// iteration (r32_ready).  Every finest-level kernel rounds its right side to
+// FP32 on reading, so the copy changes no result; it halves their reads and
+// takes the conversions out of them.
 template <typename T>
-int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
+int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bool r32_ready = false) {
   const int L = h->L;
   auto& lv = h->lev;
   constexpr bool dbl = std::is_same<T, double>::value;
-  // the finest right side: FP64 in both modes, except the variable operator in
-  // the mixed mode (converted once)
-  const bool convert_top = !dbl && lv[L].var;
-  if (convert_top)
+  const bool convert_top = !dbl;
+  if (convert_top && !r32_ready)
     KL(h, SEM_K_VECTOR, s, (launch_convert<double, float>(lv[L].nodes, rtop, static_cast<float*>(lv[L].f), s)));
   T* uL = dbl ? reinterpret_cast<T*>(zout) : static_cast<T*>(lv[L].u);
   int rc;
@@ -418,8 +420,9 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s) {
   return SEM_OK;
 }
 
-int precond(sem_handle* h, const double* r, double* z, cudaStream_t s) {
-  return h->mixed ? vcycle_z<float>(h, r, z, s) : vcycle_z<double>(h, r, z, s);
+// r32_ready: the FP32 copy of r sits in the finest level's f (mixed mode)
+int precond(sem_handle* h, const double* r, double* z, cudaStream_t s, bool r32_ready = false) {
+  return h->mixed ? vcycle_z<float>(h, r, z, s, r32_ready) : vcycle_z<double>(h, r, z, s);
 }
 
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
@@ -462,7 +465,8 @@ int pcg_tail(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int
   if ((rc = apply64(h, h->p, nullptr, h->q, 1, &np, s, nullptr, pf))) return rc;
   KL(h, SEM_K_VECTOR, s,
      launch_pcg_update_ur_check(h->n, h->u, h->r, h->p, h->q, h->part, np / h->nb, h->st, h->part + kMaxPartials,
-                                h->cfg.i_max, cond, use_cond, s, fused ? h->z : nullptr));
+                                h->cfg.i_max, cond, use_cond, s, fused ? h->z : nullptr,
+                                h->mixed ? static_cast<float*>(top(h).f) : nullptr));
   return SEM_OK;
 }
 
@@ -483,7 +487,8 @@ int pcg_prologue(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond,
 int pcg_body(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const long n = h->n;
   int rc;
-  if ((rc = precond(h, h->r, h->z, s))) return rc;
+  // the previous body's (or the prologue's) update kernel wrote r's FP32 copy
+  if ((rc = precond(h, h->r, h->z, s, true))) return rc;
   if (fused_direction(h)) {
     KL(h, SEM_K_VECTOR, s, launch_dot2_beta(n, h->z, h->r, h->q, h->part, h->st, s));
     return pcg_tail(h, s, cond, use_cond, true);
