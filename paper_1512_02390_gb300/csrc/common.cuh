@@ -120,6 +120,49 @@ __device__ __forceinline__ T window_sum(const DirView<T>& dx, const DirView<T>& 
   return s;
 }
 
+// window_sum for a compile-time order P: node g = e P + j (0 <= j < P) lies in
+// the windows of elements e - 1 (when j <= n_o), e and e + 1 (when
+// j >= P - n_o), at window index (e - e') P + j + n_o; the same windows in
+// the same (ascending y, then x) order as window_sum, so the same sum.
+template <int P, typename T>
+__device__ __forceinline__ T window_sum_p(const DirView<T>& dx, const DirView<T>& dy, const T* __restrict__ E, int gj,
+                                          int gi) {
+  const int no = dx.n_o, m = P + 1 + 2 * no, mm = m * m;
+  int ex[3], bx[3], nxc = 0, ey[3], by[3], nyc = 0;
+  {
+    const int e = gi / P, j = gi - e * P;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+      if ((d < 0 && j > no) || (d > 0 && j < P - no)) continue;
+      int ee = e + d;
+      if (dx.periodic) ee = ee < 0 ? ee + dx.n : (ee >= dx.n ? ee - dx.n : ee);
+      else if (ee < 0 || ee >= dx.n) continue;
+      ex[nxc] = ee;
+      bx[nxc] = j - d * P + no;
+      ++nxc;
+    }
+  }
+  {
+    const int e = gj / P, j = gj - e * P;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+      if ((d < 0 && j > no) || (d > 0 && j < P - no)) continue;
+      int ee = e + d;
+      if (dy.periodic) ee = ee < 0 ? ee + dy.n : (ee >= dy.n ? ee - dy.n : ee);
+      else if (ee < 0 || ee >= dy.n) continue;
+      ey[nyc] = ee;
+      by[nyc] = j - d * P + no;
+      ++nyc;
+    }
+  }
+  T s = T(0);
+  for (int iy = 0; iy < nyc; ++iy) {
+    const T* Er = E + (long)ey[iy] * dx.n * mm + by[iy] * m;
+    for (int ix = 0; ix < nxc; ++ix) s += Er[(long)ex[ix] * mm + bx[ix]];
+  }
+  return s;
+}
+
 }  // namespace sem
 
 namespace sem {

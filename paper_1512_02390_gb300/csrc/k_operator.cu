@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
     const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
+    su[ly * LP + lx] = stage_value<P>(u, E, dx, dy, pf, beta, gy, gx);
   }
   // E/O tables of slot s = element ex0 + s - 1 (slot 0: low-side neighbour)
   for (int idx = threadIdx.x; idx < 2 * (TE + 1) * EO; idx += blockDim.x) {

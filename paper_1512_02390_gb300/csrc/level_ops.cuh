@@ -31,21 +31,29 @@ __device__ __forceinline__ double fused_beta(const PcgFuse& pf, int by, int gyd)
 
 // staged operand at node (gy, gx) (-1: wall, 0): u, the assembled Schwarz
 // correction (E), or the MGCG direction z + beta p
-template <typename T>
+template <int P, typename T>
 __device__ __forceinline__ T stage_value(const T* __restrict__ u, const T* __restrict__ E, const DirView<T>& dx,
                                          const DirView<T>& dy, const PcgFuse& pf, double beta, int gy, int gx) {
   if (gx < 0 || gy < 0) return T(0);
-  if (E) return window_sum(dx, dy, E, gy, gx);
+  if (E) return window_sum_p<P>(dx, dy, E, gy, gx);
   const long o = (long)gy * dx.N + gx;
   if (pf.z) return T(fma(beta, (double)u[o], pf.z[o]));
   return u[o];
 }
 
+// per staged column (and row): its node (-1: wall) and the up to 3 windows
+// holding it (count, E offset of the column / row)
+template <int P>
+struct StageTab {
+  static constexpr int LN = Tile<P>::LN;
+  static constexpr size_t BYTES = 2 * LN * (sizeof(long) * 3 + sizeof(int) * 2);
+};
+
 template <typename T, int P>
 size_t apply_smem() {
   using Tl = Tile<P>;
   return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1)) +
-         sizeof(double) * kRedThreads;
+         sizeof(double) * kRedThreads + StageTab<P>::BYTES;
 }
 
 // One tile (bx, by) of a (gxd x gyd) tile grid; smem: apply_smem<T, P>() bytes.
@@ -63,17 +71,59 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
   T* sMy = sMx + (TN + 1);
   double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
+  long* woff = reinterpret_cast<long*>(sred + kRedThreads);  // [2 LN][3] E offsets (columns, then rows)
+  int* gnode = reinterpret_cast<int*>(woff + 2 * 3 * LN);    // [2 LN] node or -1
+  int* wcnt = gnode + 2 * LN;                                // [2 LN] windows holding it
 
   const int ex0 = bx * TE, ey0 = by * TE;
   const int Nx = dx.N, Ny = dy.N;
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
   const double beta = fused_beta(pf, by, gyd);
 
+  // staged columns and rows: node or wall, and for the assembled correction
+  // the windows of Eq. (correction:global) that hold the node, in ascending
+  // element order (node g = e P + j lies in the windows of e - 1 when
+  // j <= n_o, of e, and of e + 1 when j >= P - n_o; index (e - e') P + j + n_o)
+  for (int i = threadIdx.x; i < 2 * LN; i += blockDim.x) {
+    const bool is_row = i >= LN;
+    const DirView<T>& d = is_row ? dy : dx;
+    const int g = node_or_wall((is_row ? gy0 - LN : gx0) + i, d.N, d.periodic, d.segN);
+    gnode[i] = g;
+    int n = 0;
+    if (E && g >= 0) {
+      const int no = dx.n_o, m = P + 1 + 2 * no;
+      const long mm = (long)m * m;
+      const int e = g / P, j = g - e * P;
+#pragma unroll
+      for (int dd = -1; dd <= 1; ++dd) {
+        if ((dd < 0 && j > no) || (dd > 0 && j < P - no)) continue;
+        int ee = e + dd;
+        if (d.periodic) ee = ee < 0 ? ee + d.n : (ee >= d.n ? ee - d.n : ee);
+        else if (ee < 0 || ee >= d.n) continue;
+        const int b = j - dd * P + no;
+        woff[i * 3 + n] = is_row ? (long)ee * dx.n * mm + (long)b * m : (long)ee * mm + b;
+        ++n;
+      }
+    }
+    wcnt[i] = n;
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
-    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    su[ly * LP + lx] = stage_value(u, E, dx, dy, pf, beta, gy, gx);
+    const int gx = gnode[lx], gy = gnode[LN + ly];
+    T v = T(0);
+    if (gx >= 0 && gy >= 0) {
+      if (E) {
+        const int ny = wcnt[LN + ly], nx = wcnt[lx];
+        for (int iy = 0; iy < ny; ++iy) {
+          const T* Er = E + woff[(LN + ly) * 3 + iy];
+          for (int ix = 0; ix < nx; ++ix) v += Er[woff[lx * 3 + ix]];
+        }
+      } else {
+        v = stage_value<P>(u, E, dx, dy, pf, beta, gy, gx);  // E is null here
+      }
+    }
+    su[ly * LP + lx] = v;
   }
   // element stiffness of the tile and of its low-side neighbour (slot 0)
   for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {
@@ -96,10 +146,12 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
   double acc = 0.0;
   for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
-    const int jy = idx / ownx, ix = idx - jy * ownx;
+    // full tiles (TN or TN + 1 owned columns) divide by a constant
+    const int jy = ownx == TN ? idx / TN : (ownx == TN + 1 ? idx / (TN + 1) : idx / ownx);
+    const int ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
     const long o = (long)gj * Nx + gi;
-    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
+    const bool wall = gnode[ix + P] < 0 || gnode[LN + jy + P] < 0;
     T val = T(0);
     if (!wall) {
       const int lex = ix / P, a = ix - lex * P;
