@@ -219,7 +219,9 @@ def run_batched(args, flush, stream):
 
 
 def run_learned(args, stream):
-    """C4: 64x64, p=16, x stretched to 1:32, nu contrast 100: learned weights vs w_5."""
+    """C4: 64x64, p=16, x stretched to 1:32, nu contrast 100: learned weights vs w_5 (both with the
+    reduced-precision V-cycle) and the plain FP64 method (w_5, FP64 V-cycle) on the same problem;
+    the reduced-precision solutions' max-norm error against the FP64 one."""
     import torch
     import paper_1512_02390_gb300 as P
     from paper_1512_02390_gb300 import learned as LW
@@ -232,9 +234,10 @@ def run_learned(args, stream):
                   tol=TOL, i_max=400, precision=HEADLINE)
         px, py = LW.predict(params, **kw)
         row = {}
-        for name, extra in (("w5", dict(weight=5)),
+        u64 = None
+        for name, extra in (("fp64_w5", dict(weight=5, precision="fp64")), ("w5", dict(weight=5)),
                             ("learned", dict(weight="learned", learned_x=px.ravel(), learned_y=py.ravel()))):
-            S = P.Solver(**kw, **extra)
+            S = P.Solver(**dict(kw, **extra))
             fn = torch.from_numpy(SI.uniform_nodal(SEED, S.shape).ravel()).cuda()
             b = torch.empty_like(fn)
             S.mass(fn, b)
@@ -252,11 +255,15 @@ def run_learned(args, stream):
             ms = e0.elapsed_time(e1)
             row[name] = {"iterations": res.iterations, "status": res.status, "rbar": res.rbar, "ms": ms,
                          "dof_per_s": (S.n_unknowns / (ms * 1e-3)) if res.status == 0 else 0.0}
+            if name == "fp64_w5":
+                u64 = u.clone() if res.status == 0 else None
+            elif u64 is not None and res.status == 0:
+                row[name]["rel_error_vs_fp64"] = float((u - u64).abs().max() / u64.abs().max())
             S.close()
         out["%dx%d_p%d_no%d_contrast%d" % (n, n, p_, no, int(c))] = row
     out["workload"] = ("64x64 (and 16x16) elements, p=16 (n_o=2) and p=8 (n_o=1), x geometric 1:32 (first width = "
-                       "h_y/32), nu = 1 + (c-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y), TF32 V-cycle, MGCG to 1e-10, "
-                       "i_max 400")
+                       "h_y/32), nu = 1 + (c-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y), MGCG to 1e-10, i_max 400; "
+                       "fp64_w5: plain FP64 method; w5 / learned: TF32 V-cycle")
     return out
 
 
