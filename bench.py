@@ -54,8 +54,69 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read every 2 ms through NVML (ctypes on
+    libnvidia-ml, read-only queries) while the timed region runs."""
+
+    # nvmlClocksEventReasons bits of the NVML API
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        # NVML numbers every GPU of the machine: find this process's CUDA device by its PCI address
+        rc = -1
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            bus = ("%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)).encode()
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h))
+        except Exception:
+            rc = -1
+        if rc != 0 and self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = (getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or
+                           getattr(self.lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+        self.sm, self.smax, self.bits = [], [], 0
+        self.stop = threading.Event()
+
+    def _poll(self):
+        ct = self.ct
+        mhz, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0:  # NVML_CLOCK_SM
+                self.sm.append(mhz.value)
+            if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0:
+                self.smax.append(mx.value)
+            if self.reasons_fn is not None and self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.bits |= rs.value
+            time.sleep(0.002)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._poll, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=1)
+
+    def summary(self):
+        if not self.sm:
+            return None
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": max(self.smax) if self.smax else None,
+                "reasons": sorted(n for b, n in self.REASONS.items() if self.bits & b), "samples": len(self.sm),
+                "source": "nvml, 2 ms"}
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """Clock / throttle sampling during the timed region: NVML every 2 ms where
+    it loads, else nvidia-smi every 200 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -64,9 +125,15 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.lines = []
 
     def __enter__(self):
+        try:
+            self.nvml = NvmlSampler(self.index).__enter__()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -82,6 +149,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.nvml:
+            self.nvml.__exit__()
         if self.proc:
             self.proc.terminate()
             try:
@@ -90,6 +159,10 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml:
+            got = self.nvml.summary()
+            if got:
+                return got
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
@@ -107,7 +180,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def _oracle_job(nx, ny, p, n_o, seed, tol, reps):
