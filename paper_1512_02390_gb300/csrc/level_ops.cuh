@@ -52,8 +52,10 @@ struct StageTab {
 template <typename T, int P>
 size_t apply_smem() {
   using Tl = Tile<P>;
-  return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1)) +
-         sizeof(double) * kRedThreads + StageTab<P>::BYTES;
+  // + 16: the double / long tables start on a 16-byte boundary
+  return sizeof(T) * (Tl::LN * Tl::LP + 2 * (Tl::TE + 1) * Tl::NP * Tl::NP + 2 * (Tl::TN + 1) +
+                      (Tl::TN + 1) * Tl::TE) +
+         16 + sizeof(double) * kRedThreads + StageTab<P>::BYTES;
 }
 
 // One tile (bx, by) of a (gxd x gyd) tile grid; smem: apply_smem<T, P>() bytes.
@@ -70,7 +72,9 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   T* sLy = sLx + (TE + 1) * NP * NP;
   T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
   T* sMy = sMx + (TN + 1);
-  double* sred = reinterpret_cast<double*>(sMy + (TN + 1));
+  T* sbx = sMy + (TN + 1);                                    // [(TN + 1) x TE] left-edge x sums
+  double* sred = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(sbx + (TN + 1) * TE) + 15) & ~static_cast<uintptr_t>(15));
   long* woff = reinterpret_cast<long*>(sred + kRedThreads);  // [2 LN][3] E offsets (columns, then rows)
   int* gnode = reinterpret_cast<int*>(woff + 2 * 3 * LN);    // [2 LN] node or -1
   int* wcnt = gnode + 2 * LN;                                // [2 LN] windows holding it
@@ -144,6 +148,20 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
   const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  // x part of a node on an element's left edge (a = 0) from the element on
+  // its left (that element's last stiffness row), one thread per (row,
+  // element): in the node loop only two lanes of a warp need it, and the
+  // whole warp would issue the 17-term sum
+  for (int idx = threadIdx.x; idx < owny * TE; idx += blockDim.x) {
+    const int jy = idx / TE, lex = idx - jy * TE;
+    const T* Ll = sLx + lex * NP * NP + P * NP;
+    const T* ul = su + (jy + P) * LP + lex * P;
+    T t = T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) t += Ll[k] * ul[k];
+    sbx[idx] = t;
+  }
+  __syncthreads();
   double acc = 0.0;
   for (int idx = threadIdx.x; idx < ownx * owny; idx += blockDim.x) {
     // full tiles (TN or TN + 1 owned columns) divide by a constant
@@ -164,12 +182,7 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
         const T* uu = row + lex * P + P;
 #pragma unroll
         for (int k = 0; k < NP; ++k) xs += L[k] * uu[k];
-        if (a == 0) {
-          const T* Ll = sLx + lex * NP * NP + P * NP;
-          const T* ul = row + lex * P;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) xs += Ll[k] * ul[k];
-        }
+        if (a == 0 && lex < TE) xs += sbx[jy * TE + lex];
       }
       {
         const T* L = sLy + (ley + 1) * NP * NP + b * NP;
