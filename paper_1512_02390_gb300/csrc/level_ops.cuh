@@ -234,6 +234,8 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
   T* sr = reinterpret_cast<T*>(smem_raw);  // LN x LP fine residual
   T* st = sr + LN * LP;                     // LN x TP  x-contracted
   T* sJ = st + LN * TP;                     // NPF x NPC
+  T* sbx = sJ + (PF + 1) * NPC;             // LN x TE: x sums from the element on the left
+  T* sby = sbx + LN * TE;                   // TE x (TNC + 1): y sums from the element below
   const int E0x = bx * TE, E0y = by * TE;
   const int gx0 = E0x * PF - PF, gy0 = E0y * PF - PF;
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
@@ -247,6 +249,26 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
   const bool lastx = E0x + TE >= cx.n, lasty = E0y + TE >= cy.n;
   const int ownx = min(TE, cx.n - E0x) * PC + ((!cx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, cy.n - E0y) * PC + ((!cy.periodic && lasty) ? 1 : 0);
+  // A coarse node on an element's left (lower) edge, K = 0, also collects the
+  // element on that side through its last coarse basis function PC.  In FP64
+  // those sums come from one thread per (row, element) (in the contraction
+  // loops every warp would issue them for its few K = 0 lanes, on the narrow
+  // FP64 pipe), and the element's own part runs over i = 0 .. PF-1 for every
+  // K: J[0][K] = 0 for K != 0 (fine node 0 is coarse node 0).  In FP32 the
+  // extra passes and barriers cost more than the divergence they remove
+  // (measured), so the K = 0 lanes sum both parts in place.
+  constexpr bool kPass = std::is_same<T, double>::value;
+  if (kPass) {
+  for (int idx = threadIdx.x; idx < LN * TE; idx += blockDim.x) {
+    const int ly = idx / TE, le = idx - ly * TE;
+    const T* row = sr + ly * LP + le * PF + PF;
+    T t = T(0);
+#pragma unroll
+    for (int i = 1; i < PF; ++i) t += sJ[i * NPC + PC] * row[i - PF];
+    sbx[idx] = t;
+  }
+  __syncthreads();
+  }
   // x contraction for every staged fine row
   for (int idx = threadIdx.x; idx < LN * ownx; idx += blockDim.x) {
     const int ly = idx / ownx, ic = idx - ly * ownx;
@@ -254,7 +276,11 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
     const T* row = sr + ly * LP + le * PF + PF;  // fine local node 0 of element E0x + le
     T t = T(0);
     if (le < TE) {
-      if (K != 0) {
+      if (kPass) {
+#pragma unroll
+        for (int i = 0; i < PF; ++i) t += sJ[i * NPC + K] * row[i];
+        if (K == 0) t += sbx[ly * TE + le];
+      } else if (K != 0) {
 #pragma unroll
         for (int i = 1; i < PF; ++i) t += sJ[i * NPC + K] * row[i];
       } else {
@@ -267,6 +293,17 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
     st[ly * TP + ic] = t;
   }
   __syncthreads();
+  if (kPass) {
+  for (int idx = threadIdx.x; idx < TE * ownx; idx += blockDim.x) {
+    const int le = idx / ownx, ic = idx - le * ownx;
+    const T* col = st + (le * PF + PF) * TP + ic;
+    T t = T(0);
+#pragma unroll
+    for (int j = 1; j < PF; ++j) t += sJ[j * NPC + PC] * col[(j - PF) * TP];
+    sby[le * (TNC + 1) + ic] = t;
+  }
+  __syncthreads();
+  }
   for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
     const int jc = idx / ownx, ic = idx - jc * ownx;
     const int gI = E0x * PC + ic, gJ = E0y * PC + jc;
@@ -275,7 +312,11 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
     if (!wall) {
       const int le = jc / PC, K = jc - le * PC;
       const T* col = st + (le * PF + PF) * TP + ic;
-      if (K != 0) {
+      if (kPass) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) v += sJ[j * NPC + K] * col[j * TP];
+        if (K == 0 && le < TE) v += sby[le * (TNC + 1) + ic];
+      } else if (K != 0) {
 #pragma unroll
         for (int j = 1; j < PF; ++j) v += sJ[j * NPC + K] * col[j * TP];
       } else {
@@ -348,7 +389,8 @@ template <typename T, int PF>
 constexpr size_t restrict_smem() {
   using Q = TT<PF>;
   constexpr int LN = Q::TNF + PF + 1;
-  return sizeof(T) * (LN * (LN + 1) + LN * (Q::TNC + 2) + (PF + 1) * Q::NPC);
+  constexpr int extra = std::is_same<T, double>::value ? LN * Q::TE + Q::TE * (Q::TNC + 1) : 0;  // FP64 passes
+  return sizeof(T) * (LN * (LN + 1) + LN * (Q::TNC + 2) + (PF + 1) * Q::NPC + extra);
 }
 
 template <typename T, int PF>
