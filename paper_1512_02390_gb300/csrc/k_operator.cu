@@ -111,9 +111,10 @@ __device__ __forceinline__ void eo_products(const T* eo, const T* ev, T* dst_bas
     T ye = T(0), yo = T(0);
 #pragma unroll
     for (int k = 0; k <= H; ++k) ye += E[k] * e[k * TN];
+    if (a < H) {  // the odd part of the middle row is zero (a is uniform across a warp: w = lane)
 #pragma unroll
-    for (int k = 0; k < H; ++k) yo += O[k] * o[k * TN];
-    if (a == H) yo = T(0);
+      for (int k = 0; k < H; ++k) yo += O[k] * o[k * TN];
+    }
     if (XDIR) {
       T* dst = dst_base + (w * (TE + 1) + sl) * NP;  // [row][slot][a]
       if (a < H) dst[P - a] = ye - yo;
