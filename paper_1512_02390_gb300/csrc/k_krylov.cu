@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
                                                          const double* __restrict__ z, float* __restrict__ r32) {
   pdl_enter();
   __shared__ double sred[kRedThreads];
+  __shared__ double s_alpha;
   __shared__ int am_last;
   if (*st.active == 0) {  // nothing left (zero or invalid start of every problem)
     if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -56,11 +57,17 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
   double acc = 0.0;
   if (live) {
     const double pq = sum_partials(part_pq + (long)k * npq, npq, sred);
-    const double alpha = st.delta[(long)k * st.stride + it - 1] / pq;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st.pq[(long)k * st.stride + it] = pq;
-      st.alpha[(long)k * st.stride + it] = alpha;
+    // one division per CTA: a double division is a sequence of FP64-pipe
+    // operations, and this kernel is bound by that pipe
+    if (threadIdx.x == 0) {
+      s_alpha = st.delta[(long)k * st.stride + it - 1] / pq;
+      if (blockIdx.x == 0) {
+        st.pq[(long)k * st.stride + it] = pq;
+        st.alpha[(long)k * st.stride + it] = s_alpha;
+      }
     }
+    __syncthreads();
+    const double alpha = s_alpha;
     long lo, hi;
     segment(st, n, k, lo, hi);
     if (z) {
@@ -203,16 +210,21 @@ __global__ void __launch_bounds__(256) k_update_p(long n, const double* __restri
                                                   const double* __restrict__ part, int np, PcgState st) {
   pdl_enter();
   __shared__ double sred[kRedThreads];
+  __shared__ double s_beta;
   const int k = blockIdx.y;
   if (st.flags[2 * k]) return;
   const int it = st.iter[1];
   const double zd = sum_partials(part + (long)k * np, np, sred);
   const double zr = sum_partials(part + (long)(st.nb + k) * np, np, sred);
-  const double beta = zd / st.delta[(long)k * st.stride + it - 1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st.beta[(long)k * st.stride + it] = beta;
-    st.delta[(long)k * st.stride + it] = zr;
+  if (threadIdx.x == 0) {  // one division per CTA (FP64-pipe bound kernel)
+    s_beta = zd / st.delta[(long)k * st.stride + it - 1];
+    if (blockIdx.x == 0) {
+      st.beta[(long)k * st.stride + it] = s_beta;
+      st.delta[(long)k * st.stride + it] = zr;
+    }
   }
+  __syncthreads();
+  const double beta = s_beta;
   long lo, hi;
   segment(st, n, k, lo, hi);
   for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
@@ -279,7 +291,11 @@ __global__ void __launch_bounds__(256) k_sub_mean(long n, double* __restrict__ b
                                                   int np, double count) {
   pdl_enter();
   __shared__ double sred[kRedThreads];
-  const double mu = sum_partials(part, np, sred) / count;
+  __shared__ double s_mu;
+  const double sum = sum_partials(part, np, sred);
+  if (threadIdx.x == 0) s_mu = sum / count;  // one division per CTA
+  __syncthreads();
+  const double mu = s_mu;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] -= mu;
 }
 
