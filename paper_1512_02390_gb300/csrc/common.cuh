@@ -66,11 +66,39 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf) {
   return r;
 }
 
+// The same sum with its FP64 adds in one warp, for kernels bound by the
+// narrow FP64 pipe (a butterfly in every warp issues nw times the adds): lane
+// l of warp 0 adds the values of threads l, l + 32, l + 64, ... in that
+// order, then a butterfly over the 32 lane sums.  sbuf: blockDim.x doubles
+// (a multiple of 32).
+__device__ __forceinline__ double block_sum_w0(double v, double* sbuf) {
+  __shared__ double s_total;
+  sbuf[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double r = sbuf[threadIdx.x];
+    for (int i = threadIdx.x + 32; i < (int)blockDim.x; i += 32) r += sbuf[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (threadIdx.x == 0) s_total = r;
+  }
+  __syncthreads();
+  return s_total;
+}
+
+// Sum of n partials written by other CTAs of the same launch (read through
+// L2, fixed order): used by the last CTA of a launch.
+__device__ __forceinline__ double sum_partials_cg(const double* part, int n, double* sbuf) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+  return block_sum_w0(v, sbuf);
+}
+
 // Sum of n partials in a fixed order, identical in every block that calls it.
 __device__ __forceinline__ double sum_partials(const double* part, int n, double* sbuf) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
-  return block_sum(v, sbuf);
+  return block_sum_w0(v, sbuf);
 }
 
 }  // namespace sem

@@ -14,15 +14,18 @@ namespace {
 
 constexpr int kElemGrid = 4 * 152;
 
-__device__ __forceinline__ bool bad(double x) { return !(fabs(x) <= 1.7976931348623157e308); }
+// Elements per thread and pass of the MGCG vector loops (CTAs of kB =
+// kRedThreads threads, the block size of every launch below): thread t of
+// CTA c takes elements base + j kB (j < kU) with base = lo + c kU kB + t,
+// and issues the loads of all kU before using any (the loops are
+// latency-bound; one pass of kU costs one memory round trip).
+constexpr int kU = 4;
+constexpr int kB = kRedThreads;
 
-// Sum of n partials written by other CTAs of the same launch (read through
-// L2, fixed order): used by the last CTA of a launch.
-__device__ __forceinline__ double sum_partials_cg(const double* part, int n, double* sbuf) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
-  return block_sum(v, sbuf);
-}
+__device__ __forceinline__ long pass_base(long lo) { return lo + (long)blockIdx.x * (kB * kU) + threadIdx.x; }
+__device__ __forceinline__ long pass_step() { return (long)gridDim.x * (kB * kU); }
+
+__device__ __forceinline__ bool bad(double x) { return !(fabs(x) <= 1.7976931348623157e308); }
 
 __device__ __forceinline__ void segment(const PcgState& st, long n, int k, long& lo, long& hi) {
   lo = (long)k * st.seg_len;
@@ -70,28 +73,38 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
     const double alpha = s_alpha;
     long lo, hi;
     segment(st, n, k, lo, hi);
-    if (z) {
-      const double beta = st.beta[(long)k * st.stride + st.iter[1]];
-      for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-        const double pi = fma(beta, p[i], z[i]);  // the operator staged the same value
-        p[i] = pi;
-        u[i] += alpha * pi;
-        const double ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        if (r32) r32[i] = (float)ri;
-        acc += ri * ri;
+    const double beta = z ? st.beta[(long)k * st.stride + st.iter[1]] : 0.0;
+    for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
+      double pv[kU], zv[kU], uv[kU], rv[kU], qv[kU];
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        const long i = i0 + j * kB;
+        const bool in = i < hi;
+        pv[j] = in ? p[i] : 0.0;
+        zv[j] = (in && z) ? z[i] : 0.0;
+        uv[j] = in ? u[i] : 0.0;
+        rv[j] = in ? r[i] : 0.0;
+        qv[j] = in ? q[i] : 0.0;
       }
-    } else {
-      for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-        u[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        if (r32) r32[i] = (float)ri;
-        acc += ri * ri;
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        const long i = i0 + j * kB;
+        if (i < hi) {
+          double pi = pv[j];
+          if (z) {
+            pi = fma(beta, pv[j], zv[j]);  // the operator staged the same value
+            p[i] = pi;
+          }
+          u[i] = uv[j] + alpha * pi;
+          const double ri = rv[j] - alpha * qv[j];
+          r[i] = ri;
+          if (r32) r32[i] = (float)ri;
+          acc += ri * ri;
+        }
       }
     }
   }
-  const double s = block_sum(acc, sred);
+  const double s = block_sum_w0(acc, sred);
   if (threadIdx.x == 0) {
     part_rr[(long)k * gridDim.x + blockIdx.x] = s;
     __threadfence();
@@ -148,14 +161,25 @@ __global__ void __launch_bounds__(256) k_dot2_beta(long n, const double* __restr
   if (st.flags[2 * k] == 0) {
     long lo, hi;
     segment(st, n, k, lo, hi);
-    for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-      const double zi = z[i];
-      a += zi * q[i];
-      b += zi * r[i];
+    for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
+      double zv[kU], qv[kU], rv[kU];
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        const long i = i0 + j * kB;
+        const bool in = i < hi;
+        zv[j] = in ? z[i] : 0.0;
+        qv[j] = in ? q[i] : 0.0;
+        rv[j] = in ? r[i] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        a += zv[j] * qv[j];
+        b += zv[j] * rv[j];
+      }
     }
   }
-  const double sa = block_sum(a, sred);
-  const double sb = block_sum(b, sred);
+  const double sa = block_sum_w0(a, sred);
+  const double sb = block_sum_w0(b, sred);
   if (threadIdx.x == 0) {
     part[(long)k * gridDim.x + blockIdx.x] = sa;
     part[(long)(st.nb + k) * gridDim.x + blockIdx.x] = sb;
@@ -166,18 +190,7 @@ __global__ void __launch_bounds__(256) k_dot2_beta(long n, const double* __restr
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  const int it = st.iter[1];
-  for (int kk = 0; kk < st.nb; ++kk) {
-    const double zq = sum_partials_cg(part + (long)kk * gridDim.x, gridDim.x, sred);
-    const double zr = sum_partials_cg(part + (long)(st.nb + kk) * gridDim.x, gridDim.x, sred);
-    if (threadIdx.x == 0 && st.flags[2 * kk] == 0) {
-      const long o = (long)kk * st.stride + it;
-      const double num = it == 1 ? zr : -st.alpha[o] * zq;
-      st.beta[o] = num / st.delta[o - 1];
-      st.delta[o] = zr;
-    }
-  }
-  if (threadIdx.x == 0) *st.ticket = 0u;
+  pcg_beta_finish(part, gridDim.x, st, sred);
 }
 
 // per problem k: part[k G + c] = sum z.(r - r_old), part[(nb + k) G + c] = sum z.r
@@ -190,13 +203,24 @@ __global__ void __launch_bounds__(256) k_dot2(long n, const double* __restrict__
   long lo, hi;
   segment(st, n, k, lo, hi);
   double a = 0.0, b = 0.0;
-  for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-    const double zi = z[i], ri = r[i];
-    a += zi * (ri - r_old[i]);
-    b += zi * ri;
+  for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
+    double zv[kU], rv[kU], ov[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const long i = i0 + j * kB;
+      const bool in = i < hi;
+      zv[j] = in ? z[i] : 0.0;
+      rv[j] = in ? r[i] : 0.0;
+      ov[j] = in ? r_old[i] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      a += zv[j] * (rv[j] - ov[j]);
+      b += zv[j] * rv[j];
+    }
   }
-  const double sa = block_sum(a, sred);
-  const double sb = block_sum(b, sred);
+  const double sa = block_sum_w0(a, sred);
+  const double sb = block_sum_w0(b, sred);
   if (threadIdx.x == 0) {
     part[(long)k * gridDim.x + blockIdx.x] = sa;
     part[(long)(st.nb + k) * gridDim.x + blockIdx.x] = sb;
@@ -227,9 +251,24 @@ __global__ void __launch_bounds__(256) k_update_p(long n, const double* __restri
   const double beta = s_beta;
   long lo, hi;
   segment(st, n, k, lo, hi);
-  for (long i = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; i < hi; i += (long)gridDim.x * blockDim.x) {
-    p[i] = z[i] + beta * p[i];
-    r_old[i] = r[i];
+  for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
+    double zv[kU], pv[kU], rv[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const long i = i0 + j * kB;
+      const bool in = i < hi;
+      zv[j] = in ? z[i] : 0.0;
+      pv[j] = in ? p[i] : 0.0;
+      rv[j] = in ? r[i] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const long i = i0 + j * kB;
+      if (i < hi) {
+        p[i] = zv[j] + beta * pv[j];
+        r_old[i] = rv[j];
+      }
+    }
   }
 }
 
@@ -305,7 +344,7 @@ __global__ void __launch_bounds__(256) k_norm2(long n, const double* __restrict_
   double a = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     a += x[i] * x[i];
-  const double s = block_sum(a, sred);
+  const double s = block_sum_w0(a, sred);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -372,7 +411,7 @@ cudaError_t launch_pcg_update_ur_check(long n, double* u, double* r, double* p, 
                                        const double* z, float* r32) {
   dim3 grid(chunk_grid(st), st.nb);
   {
-    const cudaError_t e_ = launch_pdl(k_update_ur_check, dim3(grid), dim3(256), 0, s, n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z, r32);
+    const cudaError_t e_ = launch_pdl(k_update_ur_check, dim3(grid), dim3(kB), 0, s, n, u, r, p, q, part_pq, npq, st, part_rr, i_max, cond, use_cond, z, r32);
     if (e_ != cudaSuccess) return e_;
   }
   return cudaGetLastError();
@@ -382,7 +421,7 @@ cudaError_t launch_dot2_beta(long n, const double* z, const double* r, const dou
                              cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
   {
-    const cudaError_t e_ = launch_pdl(k_dot2_beta, dim3(grid), dim3(256), 0, s, n, z, r, q, part, st);
+    const cudaError_t e_ = launch_pdl(k_dot2_beta, dim3(grid), dim3(kB), 0, s, n, z, r, q, part, st);
     if (e_ != cudaSuccess) return e_;
   }
   return cudaGetLastError();
@@ -392,7 +431,7 @@ cudaError_t launch_dot2(long n, const double* z, const double* r, const double* 
                         cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
   {
-    const cudaError_t e_ = launch_pdl(k_dot2, dim3(grid), dim3(256), 0, s, n, z, r, r_old, part, st);
+    const cudaError_t e_ = launch_pdl(k_dot2, dim3(grid), dim3(kB), 0, s, n, z, r, r_old, part, st);
     if (e_ != cudaSuccess) return e_;
   }
   return cudaGetLastError();
@@ -402,7 +441,7 @@ cudaError_t launch_pcg_update_p(long n, const double* z, double* p, const double
                                 const double* part, PcgState st, cudaStream_t s) {
   dim3 grid(chunk_grid(st), st.nb);
   {
-    const cudaError_t e_ = launch_pdl(k_update_p, dim3(grid), dim3(256), 0, s, n, z, p, r, r_old, part, grid.x, st);
+    const cudaError_t e_ = launch_pdl(k_update_p, dim3(grid), dim3(kB), 0, s, n, z, p, r, r_old, part, grid.x, st);
     if (e_ != cudaSuccess) return e_;
   }
   return cudaGetLastError();

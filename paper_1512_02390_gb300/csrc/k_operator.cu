@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_apply_eo(DirView<T> dx, DirView<T> dy, 
     else if (dot == 2) acc += (double)val * (double)val;
   }
   if (dot) {
-    const double s = block_sum(acc, sred);
+    const double s = block_sum_w0(acc, sred);
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }

@@ -44,6 +44,16 @@ __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, D
   prolong_tile<T, TOut, PF>(fx, fy, cx, cy, J, uc, in, out, blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// the finest prolongation of the V-cycle writing z, with z.q, z.r and beta
+template <typename T, int PF>
+__global__ void __launch_bounds__(256) k_prolong_dot(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
+                                                     const T* __restrict__ J, const T* __restrict__ uc,
+                                                     const T* in, double* out, PcgDot dot) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  prolong_tile<T, double, PF, true>(fx, fy, cx, cy, J, uc, in, out, blockIdx.x, blockIdx.y, smem_raw, &dot);
+}
+
 // Coarse solve as four small FP64 products over the unknowns (F: nuy x nux):
 //   T1 = S_y^T (F - mu),  T2 = (T1 S_x) ./ (lam_y + lam_x^T),  T3 = S_y T2,
 //   U  = T3 S_x^T - mean(U)
@@ -194,7 +204,60 @@ cudaError_t prolong_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<
   return cudaGetLastError();
 }
 
+template <typename T, int PF>
+cudaError_t prolong_dot_p(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,
+                          const T* J, const T* uc, const T* in, double* out, const PcgDot& dot, cudaStream_t s) {
+  using Q = TT<PF>;
+  const size_t sm = prolong_smem<T, PF>();
+  cudaError_t e = allow_smem(k_prolong_dot<T, PF>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((fx.n + Q::TE - 1) / Q::TE, (fy.n + Q::TE - 1) / Q::TE);
+  if (2L * grid.x * grid.y > kMaxPartials) return cudaErrorInvalidConfiguration;
+  {
+    const cudaError_t e_ = launch_pdl(k_prolong_dot<T, PF>, dim3(grid), dim3(256), sm, s, fx, fy, cx, cy, J, uc, in, out, dot);
+    if (e_ != cudaSuccess) return e_;
+  }
+  return cudaGetLastError();
+}
+
+template <int PF>
+long prolong_ctas_p(int nx, int ny) {
+  constexpr int TE = TT<PF>::TE;
+  return (long)((nx + TE - 1) / TE) * ((ny + TE - 1) / TE);
+}
+
 }  // namespace
+
+long prolong_ctas(int p, int nx, int ny) {
+  switch (p) {
+    case 2: return prolong_ctas_p<2>(nx, ny);
+    case 4: return prolong_ctas_p<4>(nx, ny);
+    case 8: return prolong_ctas_p<8>(nx, ny);
+    case 16: return prolong_ctas_p<16>(nx, ny);
+    case 32: return prolong_ctas_p<32>(nx, ny);
+    default: return -1;
+  }
+}
+
+template <typename T>
+cudaError_t launch_prolong_dot(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                               const DirView<T>& cy, const T* J, const T* uc, const T* in, double* out,
+                               const PcgDot& dot, cudaStream_t s) {
+  switch (fx.p) {
+    case 2: return prolong_dot_p<T, 2>(fx, fy, cx, cy, J, uc, in, out, dot, s);
+    case 4: return prolong_dot_p<T, 4>(fx, fy, cx, cy, J, uc, in, out, dot, s);
+    case 8: return prolong_dot_p<T, 8>(fx, fy, cx, cy, J, uc, in, out, dot, s);
+    case 16: return prolong_dot_p<T, 16>(fx, fy, cx, cy, J, uc, in, out, dot, s);
+    case 32: return prolong_dot_p<T, 32>(fx, fy, cx, cy, J, uc, in, out, dot, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_prolong_dot<float>(const DirView<float>&, const DirView<float>&, const DirView<float>&,
+                                               const DirView<float>&, const float*, const float*, const float*,
+                                               double*, const PcgDot&, cudaStream_t);
+template cudaError_t launch_prolong_dot<double>(const DirView<double>&, const DirView<double>&,
+                                                const DirView<double>&, const DirView<double>&, const double*,
+                                                const double*, const double*, double*, const PcgDot&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_restrict(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,
@@ -231,8 +294,12 @@ cudaError_t launch_prolong(const DirView<T>& fx, const DirView<T>& fy, const Dir
 // reads from its peers' shared memory (distributed shared memory) after a
 // cluster barrier.
 constexpr int kC32 = 64, kC32P = 65, kCl = 8, kClRows = kC32 / kCl;  // tile, pitch, cluster, rows per CTA
+constexpr int kClThreads = kClRows * 32;  // threads per CTA: one warp per owned row
+// Tile passes per thread.  The tile loads (global, and peer shared memory in
+// the gather) are all issued before the first store, one round trip each.
+constexpr int kClPass = kC32 * kC32 / kClThreads;
 
-__global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
+__global__ void __launch_bounds__(kClThreads) k_coarse_fdm32(CoarseView c, const float* __restrict__ f0,
                                                      float* __restrict__ u0) {
   pdl_enter();
   namespace cg = cooperative_groups;
@@ -249,11 +316,22 @@ __global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float*
   const int nux = c.nux, nuy = c.nuy, t = threadIdx.x;
   const int r0 = rank * kClRows;
   const int fy0 = c.firsty + (blockIdx.x / kCl) * c.block_rows;
-  for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
-    const int a = idx / kC32, b = idx - a * kC32;
-    Sx[a * kC32P + b] = (a < nux && b < nux) ? c.Sx32[a * nux + b] : 0.f;
-    Sy[a * kC32P + b] = (a < nuy && b < nuy) ? c.Sy32[a * nuy + b] : 0.f;
-    F[a * kC32P + b] = (a < nuy && b < nux) ? f0[(long)(fy0 + a) * c.Nx + c.firstx + b] : 0.f;
+  {
+    float vx[kClPass], vy[kClPass], vf[kClPass];
+#pragma unroll
+    for (int j = 0; j < kClPass; ++j) {
+      const int idx = t + j * kClThreads, a = idx / kC32, b = idx - a * kC32;
+      vx[j] = (a < nux && b < nux) ? c.Sx32[a * nux + b] : 0.f;
+      vy[j] = (a < nuy && b < nuy) ? c.Sy32[a * nuy + b] : 0.f;
+      vf[j] = (a < nuy && b < nux) ? f0[(long)(fy0 + a) * c.Nx + c.firstx + b] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kClPass; ++j) {
+      const int idx = t + j * kClThreads, a = idx / kC32, b = idx - a * kC32;
+      Sx[a * kC32P + b] = vx[j];
+      Sy[a * kC32P + b] = vy[j];
+      F[a * kC32P + b] = vf[j];
+    }
   }
   for (int i = t; i < kC32; i += blockDim.x) {
     lx[i] = i < nux ? c.lx32[i] : 1.f;
@@ -293,10 +371,18 @@ __global__ void __launch_bounds__(256) k_coarse_fdm32(CoarseView c, const float*
   }
   cluster.sync();
   // gather every CTA's rows of W1 (over the right side, no longer needed)
-  for (int idx = t; idx < kC32 * kC32; idx += blockDim.x) {
-    const int a = idx / kC32, b = idx - a * kC32;
-    const float* peer = cluster.map_shared_rank(Wb, a / kClRows);
-    F[a * kC32P + b] = peer[(a % kClRows) * kC32P + b];
+  {
+    float vw[kClPass];
+#pragma unroll
+    for (int j = 0; j < kClPass; ++j) {
+      const int idx = t + j * kClThreads, a = idx / kC32, b = idx - a * kC32;
+      vw[j] = cluster.map_shared_rank(Wb, a / kClRows)[(a % kClRows) * kC32P + b];
+    }
+#pragma unroll
+    for (int j = 0; j < kClPass; ++j) {
+      const int idx = t + j * kClThreads, a = idx / kC32, b = idx - a * kC32;
+      F[a * kC32P + b] = vw[j];
+    }
   }
   cluster.sync();  // peers are done reading this CTA's rows
   float mean_u = 0.f;
@@ -343,7 +429,7 @@ cudaError_t launch_coarse(const CoarseView& c, const T* f0, T* u0, cudaStream_t 
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(kCl * std::max(1, c.batch));
-      cfg.blockDim = dim3(256);
+      cfg.blockDim = dim3(kClThreads);
       cfg.dynamicSmemBytes = sm;
       cfg.stream = s;
       cudaLaunchAttribute attr[2];

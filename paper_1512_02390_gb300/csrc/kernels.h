@@ -154,6 +154,47 @@ struct PcgState {
   unsigned* ticket;  // CTA completion counter of the fused update / check
   int* active;       // problems still iterating
 };
+
+// Polak-Ribiere step of Alg. 4 for every live problem k, from G partials of
+// z.q (part[k G ..]) and of z.r (part[(nb + k) G ..]) per problem, by the last
+// CTA of the launch that wrote them: beta_i = z.(r - r_old) / delta_{i-1}
+// with r - r_old = -alpha_i q (z.r itself at i = 1, where r_old = 0), and
+// delta_i = z.r; then the CTA counter is reset for the next launch.
+__device__ __forceinline__ void pcg_beta_finish(const double* part, int G, const PcgState& st, double* sred) {
+  const int it = st.iter[1];
+  for (int kk = 0; kk < st.nb; ++kk) {
+    const double zq = sum_partials_cg(part + (long)kk * G, G, sred);
+    const double zr = sum_partials_cg(part + (long)(st.nb + kk) * G, G, sred);
+    if (threadIdx.x == 0 && st.flags[2 * kk] == 0) {
+      const long o = (long)kk * st.stride + it;
+      const double num = it == 1 ? zr : -st.alpha[o] * zq;
+      st.beta[o] = num / st.delta[o - 1];
+      st.delta[o] = zr;
+    }
+  }
+  if (threadIdx.x == 0) *st.ticket = 0u;
+}
+
+// z.q and z.r of Alg. 4's direction update, fused into the kernel that writes
+// z = MG(r) for one problem: CTA c of G writes part[c] and part[G + c]; the
+// last CTA to finish runs pcg_beta_finish (2 G <= kMaxPartials).
+struct PcgDot {
+  const double* q;
+  const double* r;
+  double* part;
+  PcgState st;
+};
+
+// out = in + I uc as launch_prolong (double z; in may alias out), plus the
+// fused z.q, z.r and beta of `dot`.  cudaErrorInvalidConfiguration when the
+// tile grid needs more than kMaxPartials / 2 partials.
+// CTAs (tiles) of the prolongation to order p of an nx x ny element mesh
+long prolong_ctas(int p, int nx, int ny);
+template <typename T>
+cudaError_t launch_prolong_dot(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                               const DirView<T>& cy, const T* J, const T* uc, const T* in, double* out,
+                               const PcgDot& dot, cudaStream_t s);
+
 int elementwise_grid(long n);
 // CTAs per problem of the batched vector kernels (grid = (chunks, nb))
 int chunk_grid(const PcgState& st);

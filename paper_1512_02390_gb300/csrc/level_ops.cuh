@@ -206,7 +206,7 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
     else if (dot == 2) acc += (double)val * (double)val;
   }
   if (dot) {
-    const double s = block_sum(acc, sred);
+    const double s = block_sum_w0(acc, sred);
     if (threadIdx.x == 0) part[by * gxd + bx] = s;
   }
 }
@@ -333,11 +333,14 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
 
 // out = in + I uc.  Coarse nodes staged: [E0 pc, E0 pc + TNC] per direction.
 // One fine tile (bx, by); smem: prolong_smem<T, PF>() bytes.
-template <typename T, typename TOut, int PF>
+// DOT (TOut double): also the z.q and z.r partials of the written values z
+// (this tile's CTA c = by gridDim.x + bx) and, in the last CTA, beta and delta
+// (PcgDot); every CTA of the launch runs it.
+template <typename T, typename TOut, int PF, bool DOT = false>
 __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
                                              const DirView<T>& cy, const T* __restrict__ J,
                                              const T* __restrict__ uc, const T* in, TOut* out, int bx, int by,
-                                             unsigned char* smem_raw) {
+                                             unsigned char* smem_raw, const PcgDot* dot = nullptr) {
   using Q = TT<PF>;
   constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
   constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
@@ -345,6 +348,9 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
   T* st = sc + LC * LCP;                    // LC x TP  x-interpolated
   T* sJ = st + LC * TP;
   const int E0x = bx * TE, E0y = by * TE;
+  const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
+  const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
   for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
     const int ly = idx / LC, lx = idx - ly * LC;
     const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
@@ -353,9 +359,6 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
   }
   for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
   __syncthreads();
-  const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
-  const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
-  const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
   for (int idx = threadIdx.x; idx < LC * ownx; idx += blockDim.x) {
     const int ly = idx / ownx, ix = idx - ly * ownx;
     const int le = ix / PF, i = ix - le * PF;
@@ -368,6 +371,7 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     st[ly * TP + ix] = t;
   }
   __syncthreads();
+  double zq = 0.0, zr = 0.0;  // DOT: this thread's part of z.q, z.r (wall nodes: z = 0)
   for (int idx = threadIdx.x; idx < owny * ownx; idx += blockDim.x) {
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = E0x * PF + ix, gj = E0y * PF + jy;
@@ -382,7 +386,30 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     T v = T(0);
 #pragma unroll
     for (int k = 0; k < NPC; ++k) v += sJ[j * NPC + k] * col[k * TP];
-    out[o] = in ? convert_to<TOut>(in[o] + v) : convert_to<TOut>(v);
+    const TOut z = in ? convert_to<TOut>(in[o] + v) : convert_to<TOut>(v);
+    out[o] = z;
+    if constexpr (DOT) {
+      zq += z * dot->q[o];
+      zr += z * dot->r[o];
+    }
+  }
+  if constexpr (DOT) {
+    static_assert(std::is_same<TOut, double>::value, "the fused dot products take the FP64 z");
+    __shared__ double sred[kRedThreads];
+    __shared__ int am_last;
+    const double sq = block_sum_w0(zq, sred);
+    const double sr = block_sum_w0(zr, sred);
+    const int G = gridDim.x * gridDim.y, c = by * gridDim.x + bx;
+    if (threadIdx.x == 0) {
+      dot->part[c] = sq;
+      dot->part[G + c] = sr;
+      __threadfence();
+      am_last = atomicAdd(dot->st.ticket, 1u) == (unsigned)(G - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    pcg_beta_finish(dot->part, G, dot->st, sred);
   }
 }
 

@@ -338,8 +338,12 @@ int level_down_fused(sem_handle* h, const Level& l, const TF* f, T* u, cudaStrea
 // iteration (r32_ready).  Every finest-level kernel rounds its right side to
 // FP32 on reading, so the copy changes no result; it halves their reads and
 // takes the conversions out of them.
+// dot != null: the launch that writes the final z also forms z.q, z.r and
+// beta (PcgDot) where it can (the finest prolongation, when no
+// post-smoothing follows); *dotted tells whether it did.
 template <typename T>
-int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bool r32_ready = false) {
+int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bool r32_ready = false,
+             const PcgDot* dot = nullptr, bool* dotted = nullptr) {
   const int L = h->L;
   auto& lv = h->lev;
   constexpr bool dbl = std::is_same<T, double>::value;
@@ -398,6 +402,16 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
   for (int l = low + 1; l <= L; ++l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
+    const long nct = dot ? prolong_ctas(DX<T>(lv[l]).p, DX<T>(lv[l]).n, DY<T>(lv[l]).n) : -1;
+    if (dot && l == L && h->ns2[l] == 0 && nct > 0 && 2 * nct <= kMaxPartials) {
+      // z = (dbl: ul +) I uc, with the dot products
+      KL(h, SEM_K_PROLONG, s,
+         (launch_prolong_dot<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc,
+                                ul, zout, *dot, s)));
+      z_written = true;
+      *dotted = true;
+      continue;
+    }
     if (l == L && !z_written && h->ns2[l] == 0) {
       KL(h, SEM_K_PROLONG, s,
          (launch_prolong<T, double>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]),
@@ -421,8 +435,11 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
 }
 
 // r32_ready: the FP32 copy of r sits in the finest level's f (mixed mode)
-int precond(sem_handle* h, const double* r, double* z, cudaStream_t s, bool r32_ready = false) {
-  return h->mixed ? vcycle_z<float>(h, r, z, s, r32_ready) : vcycle_z<double>(h, r, z, s);
+int precond(sem_handle* h, const double* r, double* z, cudaStream_t s, bool r32_ready = false,
+            const PcgDot* dot = nullptr, bool* dotted = nullptr) {
+  if (dotted) *dotted = false;
+  return h->mixed ? vcycle_z<float>(h, r, z, s, r32_ready, dot, dotted)
+                  : vcycle_z<double>(h, r, z, s, false, dot, dotted);
 }
 
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
@@ -488,11 +505,15 @@ int pcg_body(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int
   const long n = h->n;
   int rc;
   // the previous body's (or the prologue's) update kernel wrote r's FP32 copy
-  if ((rc = precond(h, h->r, h->z, s, true))) return rc;
   if (fused_direction(h)) {
-    KL(h, SEM_K_VECTOR, s, launch_dot2_beta(n, h->z, h->r, h->q, h->part, h->st, s));
+    // one problem: the V-cycle's last launch forms z.q, z.r and beta
+    const PcgDot dot = {h->q, h->r, h->part, h->st};
+    bool dotted = false;
+    if ((rc = precond(h, h->r, h->z, s, true, h->nb == 1 ? &dot : nullptr, &dotted))) return rc;
+    if (!dotted) KL(h, SEM_K_VECTOR, s, launch_dot2_beta(n, h->z, h->r, h->q, h->part, h->st, s));
     return pcg_tail(h, s, cond, use_cond, true);
   }
+  if ((rc = precond(h, h->r, h->z, s, true))) return rc;
   KL(h, SEM_K_VECTOR, s, launch_dot2(n, h->z, h->r, h->r_old, h->part, h->st, s));
   KL(h, SEM_K_VECTOR, s, launch_pcg_update_p(n, h->z, h->p, h->r, h->r_old, h->part, h->st, s));
   return pcg_tail(h, s, cond, use_cond, false);
