@@ -26,8 +26,11 @@ namespace sem {
 
 namespace {
 
+// The finest level's transfer launches have one CTA per 2 x 2 elements (1024
+// at 64 x 64, p = 16): at 32 registers 8 CTAs fit an SM and they run in one
+// wave instead of two.  FP64 and p = 32 restrictions would spill at 32.
 template <typename T, int PF>
-__global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF <= 16) ? 8 : 1) k_restrict(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                   const T* __restrict__ J, const T* __restrict__ rf,
                                                   T* __restrict__ fc) {
   pdl_enter();
@@ -36,7 +39,7 @@ __global__ void __launch_bounds__(256) k_restrict(DirView<T> fx, DirView<T> fy, 
 }
 
 template <typename T, typename TOut, int PF>
-__global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
+__global__ void __launch_bounds__(256, 8) k_prolong(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                  const T* __restrict__ J, const T* __restrict__ uc,
                                                  const T* in, TOut* out) {
   pdl_enter();
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(256) k_prolong(DirView<T> fx, DirView<T> fy, D
 
 // the finest prolongation of the V-cycle writing z, with z.q, z.r and beta
 template <typename T, int PF>
-__global__ void __launch_bounds__(256) k_prolong_dot(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
+__global__ void __launch_bounds__(256, 8) k_prolong_dot(DirView<T> fx, DirView<T> fy, DirView<T> cx, DirView<T> cy,
                                                      const T* __restrict__ J, const T* __restrict__ uc,
                                                      const T* in, double* out, PcgDot dot) {
   pdl_enter();
