@@ -6,6 +6,7 @@
 // delta) without an extra launch or atomics.  Per-iteration scalars are kept
 // in history arrays indexed by the iteration count, so a kernel that reads
 // delta_{i-1} never races with the one that writes delta_i.
+#include "f32_round.h"
 #include "kernels.h"
 
 namespace sem {
@@ -32,6 +33,47 @@ __device__ __forceinline__ void segment(const PcgState& st, long n, int k, long&
   hi = (k == st.nb - 1) ? n : lo + st.seg_len;
 }
 
+// The vector part of k_update_ur_check over nodes [lo, hi): [HAS_Z: p = z +
+// beta p, stored]; u += alpha p; r -= alpha q; [HAS_R32: FP32 copy of r];
+// returns this thread's part of ||r||^2
+template <bool HAS_Z, bool HAS_R32>
+__device__ __forceinline__ double update_ur(long lo, long hi, double alpha, double beta, double* __restrict__ u,
+                                            double* __restrict__ r, double* __restrict__ p,
+                                            const double* __restrict__ q, const double* __restrict__ z,
+                                            float* __restrict__ r32) {
+  double acc = 0.0;
+  for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
+    double pv[kU], zv[kU], uv[kU], rv[kU], qv[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const long i = i0 + j * kB;
+      const bool in = i < hi;
+      pv[j] = in ? p[i] : 0.0;
+      zv[j] = (HAS_Z && in) ? z[i] : 0.0;
+      uv[j] = in ? u[i] : 0.0;
+      rv[j] = in ? r[i] : 0.0;
+      qv[j] = in ? q[i] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const long i = i0 + j * kB;
+      if (i < hi) {
+        double pi = pv[j];
+        if constexpr (HAS_Z) {
+          pi = fma(beta, pv[j], zv[j]);  // the operator staged the same value
+          p[i] = pi;
+        }
+        u[i] = uv[j] + alpha * pi;
+        const double ri = rv[j] - alpha * qv[j];
+        r[i] = ri;
+        if constexpr (HAS_R32) r32[i] = f32_from_f64_rn(ri);  // integer ALU, not the FP64 pipe
+        acc += ri * ri;
+      }
+    }
+  }
+  return acc;
+}
+
 // Iteration i = iter[0], problem k = blockIdx.y (skipped once done):
 // [z != null: p = z + beta p with beta = beta_k,iter[1], the direction update
 // of Alg. 4 fused here and into the operator that formed q]
@@ -40,7 +82,8 @@ __device__ __forceinline__ void segment(const PcgState& st, long n, int k, long&
 // scalars, sets done / status (convergence ||r|| <= r_max, breakdown, i_max),
 // advances the counter and, inside a graph, sets the WHILE condition to
 // "some problem still iterating".  npq: partials of p.q per problem.
-__global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restrict__ u, double* __restrict__ r,
+// (256, 4): at most 64 registers, so the 4 x 152 CTAs of the grid are resident at once
+__global__ void __launch_bounds__(256, 4) k_update_ur_check(long n, double* __restrict__ u, double* __restrict__ r,
                                                          double* __restrict__ p, const double* __restrict__ q,
                                                          const double* __restrict__ part_pq, int npq, PcgState st,
                                                          double* __restrict__ part_rr, int i_max,
@@ -74,34 +117,12 @@ __global__ void __launch_bounds__(256) k_update_ur_check(long n, double* __restr
     long lo, hi;
     segment(st, n, k, lo, hi);
     const double beta = z ? st.beta[(long)k * st.stride + st.iter[1]] : 0.0;
-    for (long i0 = pass_base(lo); i0 < hi; i0 += pass_step()) {
-      double pv[kU], zv[kU], uv[kU], rv[kU], qv[kU];
-#pragma unroll
-      for (int j = 0; j < kU; ++j) {
-        const long i = i0 + j * kB;
-        const bool in = i < hi;
-        pv[j] = in ? p[i] : 0.0;
-        zv[j] = (in && z) ? z[i] : 0.0;
-        uv[j] = in ? u[i] : 0.0;
-        rv[j] = in ? r[i] : 0.0;
-        qv[j] = in ? q[i] : 0.0;
-      }
-#pragma unroll
-      for (int j = 0; j < kU; ++j) {
-        const long i = i0 + j * kB;
-        if (i < hi) {
-          double pi = pv[j];
-          if (z) {
-            pi = fma(beta, pv[j], zv[j]);  // the operator staged the same value
-            p[i] = pi;
-          }
-          u[i] = uv[j] + alpha * pi;
-          const double ri = rv[j] - alpha * qv[j];
-          r[i] = ri;
-          if (r32) r32[i] = (float)ri;
-          acc += ri * ri;
-        }
-      }
+    if (z) {
+      acc = r32 ? update_ur<true, true>(lo, hi, alpha, beta, u, r, p, q, z, r32)
+                : update_ur<true, false>(lo, hi, alpha, beta, u, r, p, q, z, r32);
+    } else {
+      acc = r32 ? update_ur<false, true>(lo, hi, alpha, beta, u, r, p, q, z, r32)
+                : update_ur<false, false>(lo, hi, alpha, beta, u, r, p, q, z, r32);
     }
   }
   const double s = block_sum_w0(acc, sred);

@@ -104,3 +104,54 @@ def test_gll_tables_reject_bad_order(lib):
     for p in (0, 65):
         with pytest.raises(P.SemError):
             P.sem_gll_tables(p)
+
+
+# ---- the integer binary64 -> binary32 rounding of the MGCG update -------------
+
+_CONV_SRC = r'''
+#include "f32_round.h"
+extern "C" void conv(const double* x, float* y, long n) {
+  for (long i = 0; i < n; ++i) y[i] = sem::f32_from_f64_rn(x[i]);
+}
+'''
+
+
+def test_f32_rounding_matches_ieee_round_to_nearest_even(tmp_path):
+    """The FP32 copy of r is rounded by integer operations on the bit fields;
+    it must equal IEEE round-to-nearest-even (numpy's float64 -> float32)
+    bit for bit: random values over every binary32 binade and beyond, exact
+    ties on both parities, the largest binade's carry to infinity, the
+    subnormal boundary, zeros, infinities and NaN."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    src = tmp_path / "conv.cpp"
+    src.write_text(_CONV_SRC)
+    so = tmp_path / "conv.so"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1512_02390_gb300", "csrc")
+    subprocess.run(["g++", "-O2", "-shared", "-fPIC", "-I", inc, str(src), "-o", str(so)], check=True)
+    f = ctypes.CDLL(str(so)).conv
+    rng = np.random.default_rng(5)
+    n = 400000
+    x = np.ldexp(rng.uniform(0.5, 1.0, n), rng.integers(-160, 140, n)) * rng.choice([-1.0, 1.0], n)
+    # exact ties: a binary32 value plus half its ulp (even and odd last bits)
+    base = np.ldexp(rng.uniform(1.0, 2.0, 2000).astype(np.float32).astype(np.float64), rng.integers(-120, 120, 2000))
+    ulp = np.spacing(base.astype(np.float32)).astype(np.float64)
+    ties = np.concatenate([base + 0.5 * ulp, base - 0.5 * ulp * (base.astype(np.float32) != base)])
+    fmax = float(np.finfo(np.float32).max)
+    edge = np.array([0.0, -0.0, np.inf, -np.inf, fmax, -fmax, fmax * (1 + 2.0**-25), fmax * (1 + 2.0**-24),
+                     fmax + 2.0**103, np.nextafter(fmax + 2.0**103, 0), 2.0**128, 2.0**-126,
+                     np.nextafter(2.0**-126, 0), 2.0**-127, 2.0**-149, 2.0**-150, 3 * 2.0**-151, 1e-300,
+                     1e300, 1.0, -1.0, 1 + 2.0**-24, 1 + 3 * 2.0**-24, 1 + 2.0**-24 + 2.0**-52])
+    x = np.ascontiguousarray(np.concatenate([x, ties, edge]), dtype=np.float64)
+    y = np.empty(x.size, dtype=np.float32)
+    f(x.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(x.size))
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32)
+    assert np.array_equal(y.view(np.uint32), want.view(np.uint32))
+    z = np.array([np.nan], dtype=np.float64)
+    f(z.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(1))
+    assert np.isnan(y[0])
