@@ -11,9 +11,9 @@ namespace sem {
 // Number of partial sums a reduction-producing launch writes (one per CTA).
 constexpr int kMaxPartials = 1 << 17;
 // Elements per direction of one operator / grid-transfer tile at order P:
-// 32 x 32 owned nodes for P >= 8, 16 x 16 below (the low levels are small and
-// latency-bound: more, smaller CTAs).
-__host__ __device__ constexpr int tile_elems(int P) { return P >= 32 ? 1 : (P <= 4 ? 16 / P : 32 / P); }
+// 32 x 32 owned nodes for P >= 16, 16 x 16 for P <= 8 (the lower levels are
+// small and latency-bound: more, smaller CTAs).
+__host__ __device__ constexpr int tile_elems(int P) { return P >= 32 ? 1 : (P <= 8 ? 16 / P : 32 / P); }
 
 // ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
 // The MGCG direction update of Alg. 4 fused into the FP64 operator: the
