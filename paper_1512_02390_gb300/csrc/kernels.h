@@ -176,13 +176,17 @@ __device__ __forceinline__ void pcg_beta_finish(const double* part, int G, const
 }
 
 // z.q and z.r of Alg. 4's direction update, fused into the kernel that writes
-// z = MG(r) for one problem: CTA c of G writes part[c] and part[G + c]; the
-// last CTA to finish runs pcg_beta_finish (2 G <= kMaxPartials).
+// z = MG(r).  The nb problems are stacked along y, gyp tile rows each (no tile
+// straddles two): the CTA in tile row by belongs to problem k = by / gyp and
+// is number c of its G = gridDim.x gyp; it writes part[k G + c] and
+// part[(nb + k) G + c]; the last CTA to finish runs pcg_beta_finish
+// (2 nb G <= kMaxPartials).
 struct PcgDot {
   const double* q;
   const double* r;
   double* part;
   PcgState st;
+  int gyp;
 };
 
 // out = in + I uc as launch_prolong (double z; in may alias out), plus the

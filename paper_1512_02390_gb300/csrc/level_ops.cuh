@@ -333,9 +333,9 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
 
 // out = in + I uc.  Coarse nodes staged: [E0 pc, E0 pc + TNC] per direction.
 // One fine tile (bx, by); smem: prolong_smem<T, PF>() bytes.
-// DOT (TOut double): also the z.q and z.r partials of the written values z
-// (this tile's CTA c = by gridDim.x + bx) and, in the last CTA, beta and delta
-// (PcgDot); every CTA of the launch runs it.
+// DOT (TOut double): also the z.q and z.r partials of the written values z,
+// per problem, and, in the last CTA, beta and delta (PcgDot); every CTA of
+// the launch runs it.
 template <typename T, typename TOut, int PF, bool DOT = false>
 __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
                                              const DirView<T>& cy, const T* __restrict__ J,
@@ -399,12 +399,13 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     __shared__ int am_last;
     const double sq = block_sum_w0(zq, sred);
     const double sr = block_sum_w0(zr, sred);
-    const int G = gridDim.x * gridDim.y, c = by * gridDim.x + bx;
+    const int kp = by / dot->gyp, G = gridDim.x * dot->gyp;
+    const int c = (by - kp * dot->gyp) * gridDim.x + bx;
     if (threadIdx.x == 0) {
-      dot->part[c] = sq;
-      dot->part[G + c] = sr;
+      dot->part[(long)kp * G + c] = sq;
+      dot->part[(long)(dot->st.nb + kp) * G + c] = sr;
       __threadfence();
-      am_last = atomicAdd(dot->st.ticket, 1u) == (unsigned)(G - 1);
+      am_last = atomicAdd(dot->st.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
     if (!am_last) return;

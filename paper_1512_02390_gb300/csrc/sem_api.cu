@@ -402,8 +402,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
   for (int l = low + 1; l <= L; ++l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
-    const long nct = dot ? prolong_ctas(DX<T>(lv[l]).p, DX<T>(lv[l]).n, DY<T>(lv[l]).n) : -1;
-    if (dot && l == L && h->ns2[l] == 0 && nct > 0 && 2 * nct <= kMaxPartials) {
+    if (dot && l == L && h->ns2[l] == 0 && dot->gyp > 0) {
       // z = (dbl: ul +) I uc, with the dot products
       KL(h, SEM_K_PROLONG, s,
          (launch_prolong_dot<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), uc,
@@ -456,6 +455,18 @@ int apply64(sem_handle* h, const double* u, const double* f, double* out, int do
                              nullptr, pf, h->mixed ? -2 : 0);
 }
 
+// Tile rows per problem of the finest prolongation when it can form the
+// z.q, z.r partials (PcgDot), else 0: one problem (any height), or stacked
+// problems whose tiles do not straddle two; 2 x tiles <= kMaxPartials.
+int dot_tile_rows(const sem_handle* h) {
+  const Level& t = top(h);
+  const int te = tile_elems(t.p), ny = t.y64.n, nyp = ny / h->nb;
+  const long nct = prolong_ctas(t.p, t.x64.n, ny);
+  if (nct <= 0 || 2 * nct > kMaxPartials) return 0;
+  if (h->nb == 1) return (ny + te - 1) / te;
+  return (nyp * h->nb == ny && nyp % te == 0) ? nyp / te : 0;
+}
+
 // The direction update p = z + beta p of Alg. 4 fused into the FP64 operator
 // and the u, r update (Poisson operator): beta from the z.q, z.r reduction.
 bool fused_direction(const sem_handle* h) { return !top(h).var; }
@@ -506,10 +517,10 @@ int pcg_body(sem_handle* h, cudaStream_t s, cudaGraphConditionalHandle cond, int
   int rc;
   // the previous body's (or the prologue's) update kernel wrote r's FP32 copy
   if (fused_direction(h)) {
-    // one problem: the V-cycle's last launch forms z.q, z.r and beta
-    const PcgDot dot = {h->q, h->r, h->part, h->st};
+    // the V-cycle's last launch forms z.q, z.r and beta (per stacked problem)
+    const PcgDot dot = {h->q, h->r, h->part, h->st, dot_tile_rows(h)};
     bool dotted = false;
-    if ((rc = precond(h, h->r, h->z, s, true, h->nb == 1 ? &dot : nullptr, &dotted))) return rc;
+    if ((rc = precond(h, h->r, h->z, s, true, dot.gyp > 0 ? &dot : nullptr, &dotted))) return rc;
     if (!dotted) KL(h, SEM_K_VECTOR, s, launch_dot2_beta(n, h->z, h->r, h->q, h->part, h->st, s));
     return pcg_tail(h, s, cond, use_cond, true);
   }
