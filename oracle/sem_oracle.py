@@ -47,6 +47,12 @@ design notes of the repository):
   R8 lower-level corrections u_l (l < L) start from zero in every cycle.
   R9 n_{o,l} = min(rule(p_l), p_l - 1); level 0 is never smoothed.
   R10 nu_bar_s is the GLL-quadrature mean of nu over the embedded element.
+  R15 Alg. 1 (multiplicative Schwarz): each local problem is solved on the
+     whole extended subdomain, and the update adds the solution on the
+     element's own closed node set only (no weights).  Adding it on the whole
+     window converges faster than the paper's "mult" columns (r_bar 1.44 /
+     1.90 / 1.49 against the printed 1.01 / 1.29 / 1.26 of Table 1);
+     this reading reproduces Tables 1 and 3.
   R16 learned weights (not in the paper): per interface line a transition
      half-width scale s in (0, 1] and a shape degree kt in [1, 7], phi the
      convex blend of the two neighbouring odd-degree shape functions.
@@ -289,6 +295,15 @@ def overlap_rule(rule, p_l: int) -> int:
     return max(0, min(n, p_l - 1))
 
 
+def mult_colour_count(mesh: Mesh1D) -> int:
+    """Colour classes per direction of the coloured multiplicative order:
+    3 on a Dirichlet mesh, the smallest divisor q >= 3 of n on a periodic one
+    (so that e and e + q * j share a class also across the wrap)."""
+    if not mesh.periodic:
+        return 3
+    return next(q for q in range(3, mesh.n + 1) if mesh.n % q == 0)
+
+
 # ---------------------------------------------------------------------------
 # Weight functions (Sec. 3.1, Eq. (weight function), Eq. (shape function),
 # Table (weighting))
@@ -529,18 +544,48 @@ class Level:
             u = u + self.schwarz_correction(r)
         return u
 
-    def mschwarz(self, u: np.ndarray, f: np.ndarray, n_it: int) -> np.ndarray:
-        """Alg. 1, multiplicative Schwarz (lexicographic order, reversed on even sweeps)."""
-        ne = self.mx.n * self.my.n
+    def mult_order(self, order: str = "lex") -> list:
+        """Subdomain sequence of one forward sweep of Alg. 1 as (ex, ey) pairs.
+
+        "lex": the paper's order, s = e = 1..n_el (element rows of x fastest).
+        "colour": the same subdomains grouped by colour class
+        c = cy * qx + cx, with cx = ex mod qx and cy = ey mod qy, classes in
+        increasing c and lexicographic inside a class (mult_colour_count gives
+        q).  Two subdomains of one class lie at least q >= 3 elements apart in
+        x or in y, also across a periodic wrap (q divides n), so the update of
+        one (its element's closed node set, and the residual on the element
+        and its neighbours) never reaches the other's window (n_o < p): within
+        a class the order does not change the result.
+        """
+        nx, ny = self.mx.n, self.my.n
+        lex = [(ex, ey) for ey in range(ny) for ex in range(nx)]
+        if order == "lex":
+            return lex
+        if order != "colour":
+            raise ValueError(order)
+        qx, qy = mult_colour_count(self.mx), mult_colour_count(self.my)
+        return sorted(lex, key=lambda s: ((s[1] % qy) * qx + s[0] % qx, s[1], s[0]))
+
+    def mschwarz(self, u: np.ndarray, f: np.ndarray, n_it: int, order: str = "lex") -> np.ndarray:
+        """Alg. 1, multiplicative Schwarz: the subdomains in sequence, reversed on
+        even sweeps, the residual recomputed before each local solve.
+
+        Reading R15: the local problem is solved on the whole extended
+        subdomain (Sec. 3.1), and R_s^T of the update line adds the solution
+        on the nodes of the element itself, its boundary nodes included
+        (element-local indices 0..p), without weights.
+        """
+        seq = self.mult_order(order)
         for i in range(1, n_it + 1):
-            for e in range(ne):
-                s = e if i % 2 == 1 else ne - 1 - e
-                ey, ex = divmod(s, self.mx.n)
+            for ex, ey in (seq if i % 2 == 1 else seq[::-1]):
                 sx, sy = self.sub_x[ex], self.sub_y[ey]
                 r = f - self.apply(u)
                 rs = r[np.ix_(sy.g, sx.g)]
+                du = self.local_solve(ex, ey, rs)
+                own_x = (sx.k >= 0) & (sx.k <= self.p)
+                own_y = (sy.k >= 0) & (sy.k <= self.p)
                 u = u.copy()
-                u[np.ix_(sy.g, sx.g)] += self.local_solve(ex, ey, rs)
+                u[np.ix_(sy.g[own_y], sx.g[own_x])] += du[np.ix_(own_y, own_x)]
         return u
 
     def dense_operator(self) -> np.ndarray:
@@ -589,6 +634,7 @@ class Hierarchy:
     weight: object = 5
     nu: object = None
     smoother: str = "add"
+    mult_order: str = "lex"  # subdomain order of Alg. 1: "lex" or "colour"
     learned: object = None  # (params_x, params_y): arrays [level][interface][2]
     levels: list = field(default_factory=list)
 
@@ -628,7 +674,7 @@ class Hierarchy:
         if n <= 0:
             return u
         if self.smoother == "mult":
-            return lev.mschwarz(u, f, n)
+            return lev.mschwarz(u, f, n, self.mult_order)
         return lev.wschwarz(u, f, n)
 
     def vcycle(self, u: np.ndarray, f: np.ndarray, ns1, ns2) -> np.ndarray:

@@ -20,9 +20,9 @@ def _n10_close(got, want):
     return abs(got - want) <= max(1, 0.05 * want)
 
 
-def _periodic_case(p, weight, overlap, n=8, AR=1, seed=1):
+def _periodic_case(p, weight, overlap, n=8, AR=1, seed=1, **kw):
     H = O.Hierarchy(O.Mesh1D.uniform(n, 2.0 * AR, True), O.Mesh1D.uniform(n, 2.0, True), p,
-                    overlap=overlap, weight=weight)
+                    overlap=overlap, weight=weight, **kw)
     lev = H.top
     X, Y = lev.mx.coords(p), lev.my.coords(p)
     f = lev.mass(2 * np.pi**2 * np.sin(np.pi * X[None, :]) * np.sin(np.pi * Y[:, None]))
@@ -99,3 +99,117 @@ def test_dirichlet_unit_square_p4_converges_like_the_periodic_case():
     assert hist[-1] <= 1e-10 * hist[0] and 5 <= it <= 12
     # discretisation error of p = 4 on 4x4 elements
     assert np.abs(u - ue).max() < 1e-4
+
+
+# ---- the multiplicative smoother (Alg. 1, reading R15) ----------------------
+
+_T1_MULT = [(int(r[0]), float(r[7])) for r in _T1]
+
+
+@pytest.mark.parametrize("p,want", [c for c in _T1_MULT if c[0] <= 16])
+def test_table1_mult_rates(p, want):
+    """Table 1, column mult: MG(1,0) with Alg. 1, n_o = 1, 8 x 8 periodic."""
+    H, u0, f = _periodic_case(p, 5, 1, smoother="mult")
+    _, hist = H.mg_solve(u0, f)
+    rb = O.rate(hist)
+    assert _close(rb, want), (p, rb, want)
+    assert _n10_close(O.n10(rb), math.ceil(10 / want))
+
+
+@pytest.mark.slow
+def test_table1_mult_rate_p32():
+    p, want = _T1_MULT[-1]
+    H, u0, f = _periodic_case(p, 5, 1, smoother="mult")
+    _, hist = H.mg_solve(u0, f)
+    assert _close(O.rate(hist), want)
+
+
+_T3_MULT = rows("table3_mult.txt")
+
+
+def _table3_mult(row):
+    p, n, want, n10 = int(row[0]), int(row[1]), float(row[2]), int(row[3])
+    H, u0, f = _periodic_case(p, 5, "ceil8", n=n, smoother="mult")
+    _, hist = H.mg_solve(u0, f)
+    rb = O.rate(hist)
+    assert _close(rb, want), (rb, want)
+    assert _n10_close(O.n10(rb), n10)
+
+
+@pytest.mark.parametrize("row", [r for r in _T3_MULT if int(r[0]) * int(r[1]) <= 128],
+                         ids=lambda r: "p%s_n%s" % (r[0], r[1]))
+def test_table3_mult_rates(row):
+    """Table 3, columns MG(1,0) mult: Alg. 1 with n_o,l = ceil(p_l/8)."""
+    _table3_mult(row)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row", [r for r in _T3_MULT if int(r[0]) * int(r[1]) > 128],
+                         ids=lambda r: "p%s_n%s" % (r[0], r[1]))
+def test_table3_mult_rates_large(row):
+    _table3_mult(row)
+
+
+def test_mult_whole_window_update_misses_table1():
+    """The other reading of Alg. 1's update (R_s^T over the whole window) is
+    clearly faster than the printed mult column at p = 4 (Table 1: 1.01):
+    the pin above separates the two readings."""
+    H, u0, f = _periodic_case(4, 5, 1, smoother="mult")
+
+    def whole_window(lv):
+        def sweep(u, f_, n_it, order="lex"):
+            for i in range(1, n_it + 1):
+                seq = lv.mult_order(order)
+                for ex, ey in (seq if i % 2 == 1 else seq[::-1]):
+                    sx, sy = lv.sub_x[ex], lv.sub_y[ey]
+                    r = f_ - lv.apply(u)
+                    u = u.copy()
+                    u[np.ix_(sy.g, sx.g)] += lv.local_solve(ex, ey, r[np.ix_(sy.g, sx.g)])
+            return u
+        return sweep
+
+    for lv in H.levels[1:]:
+        lv.mschwarz = whole_window(lv)
+    _, hist = H.mg_solve(u0, f)
+    assert O.rate(hist) > 1.3
+
+
+@pytest.mark.parametrize("periodic,n", [(True, 8), (False, 7)])
+def test_mult_colour_classes_are_independent(periodic, n):
+    """Within one colour class of the coloured order the subdomains do not
+    interact: a sweep in any order inside the classes gives bitwise the same
+    result (the property a parallel implementation relies on)."""
+    if periodic:
+        H = O.Hierarchy(O.Mesh1D.uniform(n, 2.0, True), O.Mesh1D.uniform(n, 2.0, True), 4, overlap=2,
+                        smoother="mult", mult_order="colour")
+    else:
+        H = O.uniform_hierarchy(n, n - 1, 4, overlap=2, smoother="mult", mult_order="colour")
+    lev = H.top
+    rng = np.random.default_rng(3)
+    u0 = np.where(lev.unknown, rng.uniform(-1, 1, lev.unknown.shape), 0.0)
+    f = np.where(lev.unknown, rng.uniform(-1, 1, lev.unknown.shape), 0.0)
+    ref = lev.mschwarz(u0, f, 2, "colour")
+    qx, qy = O.mult_colour_count(lev.mx), O.mult_colour_count(lev.my)
+    seq = lev.mult_order("colour")
+    cls = [(ey % qy) * qx + ex % qx for ex, ey in seq]
+    assert cls == sorted(cls) and len(set(seq)) == len(seq) == lev.mx.n * lev.my.n
+    shuffled = []
+    for c in sorted(set(cls)):
+        members = [s for s, k in zip(seq, cls) if k == c]
+        shuffled += [members[i] for i in rng.permutation(len(members))]
+    lev.mult_order = lambda order="lex": shuffled
+    got = lev.mschwarz(u0, f, 2, "colour")
+    assert np.array_equal(got, ref)
+    # while the lexicographic order of Alg. 1 gives a different (valid) result
+    del lev.mult_order
+    assert not np.array_equal(lev.mschwarz(u0, f, 2, "lex"), ref)
+
+
+@pytest.mark.parametrize("p,want", [c for c in _T1_MULT if c[0] <= 16])
+def test_mult_colour_order_converges_at_least_as_fast(p, want):
+    """The coloured order (the departure from Alg. 1's lexicographic order that
+    a parallel smoother needs) converges at least as fast as the paper's
+    order: Table 1's mult column is a lower bound within the band."""
+    H, u0, f = _periodic_case(p, 5, 1, smoother="mult", mult_order="colour")
+    _, hist = H.mg_solve(u0, f)
+    assert O.rate(hist) >= want - (0.05 * want + 0.02), (p, O.rate(hist), want)
