@@ -6,7 +6,10 @@
 // never allocates: E lives in a file-scope static device array of fixed size,
 // which every GPU that loads the library holds until the process exits.  Its
 // device address is looked up once per device with cudaGetSymbolAddress, on
-// the first call made while that device is current.
+// the first call made while that device is current, and kept for the life of
+// the process.  cudaDeviceReset destroys the array with the context, so the
+// kept address is stale afterwards: a process that resets a device must not
+// call this entry point on that device again.
 #include <mutex>
 #include <string>
 
@@ -62,6 +65,19 @@ extern "C" int sem_schwarz_correction_noalloc(const sem_sweep_tables* tx, const 
     cudaGetLastError();
     return noalloc_fail(SEM_CUDA_ERROR, "sem_schwarz_correction_noalloc: no usable current CUDA device");
   }
+  // The FP64 local solve keeps four m x m and four m-long arrays of one
+  // subdomain in shared memory; a window too large for the device's per-block
+  // limit is a bad argument, rejected before anything is launched.
+  int smem_optin = 0;
+  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_fail(SEM_CUDA_ERROR, "sem_schwarz_correction_noalloc: cannot query the shared-memory limit");
+  }
+  const size_t smem_need = sizeof(double) * (4 * (size_t)m * m + 4 * (size_t)m);
+  if (smem_need > (size_t)smem_optin)
+    return noalloc_fail(SEM_BAD_ARG, "sem_schwarz_correction_noalloc: window m = " + std::to_string(m) + " needs " +
+                                         std::to_string(smem_need) + " bytes of shared memory per block; the device allows " +
+                                         std::to_string(smem_optin));
   double* E = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -98,6 +114,9 @@ extern "C" int sem_schwarz_correction_noalloc(const sem_sweep_tables* tx, const 
   // its whole m x m block), so the scratch needs no clearing between calls.
   cudaError_t e = sem::launch_sweep<double, double>(dx, dy, r, E, 0, nullptr, s);
   if (e == cudaSuccess) e = sem::launch_scatter<double, double>(dx, dy, E, u, true, s);
-  if (e != cudaSuccess) return noalloc_fail(SEM_CUDA_ERROR, std::string("launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear it, so that no later launch reports this failure as its own
+    return noalloc_fail(SEM_CUDA_ERROR, std::string("launch: ") + cudaGetErrorString(e));
+  }
   return SEM_OK;
 }

@@ -21,7 +21,7 @@ P = pytest.importorskip("paper_1512_02390_gb300")
 
 
 def _tables(cfg, level):
-    """Upload the x-direction tables that sem_inspect_level reports (square mesh: y = x)."""
+    """Upload the x-direction tables that sem_inspect_level reports."""
     t = P.sem_inspect_level(cfg, level)
     keep = [torch.from_numpy(np.ascontiguousarray(t["tab"])).cuda(),
             torch.from_numpy(np.ascontiguousarray(t["S"])).cuda(),
@@ -32,12 +32,22 @@ def _tables(cfg, level):
     return d, keep, t
 
 
+def _tables_xy(nx, ny, periodic, level=4):
+    """x tables of an nx x ny mesh, and its y tables as the x tables of the
+    ny x nx mesh on the same unit square (same element widths and walls)."""
+    kw = dict(p=16, periodic=periodic, overlap=2, weight=5)
+    dx, kx, t = _tables(P.make_config(nx=nx, ny=ny, **kw), level)
+    dy, ky, _ = _tables(P.make_config(nx=ny, ny=nx, **kw), level)
+    return dx, dy, kx + ky, t
+
+
 @pytest.mark.parametrize("periodic", [False, True])
-def test_noalloc_correction_matches_regular_entry_point(periodic):
+@pytest.mark.parametrize("nx,ny", [(8, 8), (8, 4)])
+def test_noalloc_correction_matches_regular_entry_point(periodic, nx, ny):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    S = P.Solver(nx=8, ny=8, p=16, periodic=periodic, overlap=2, weight=5)
-    d, keep, t = _tables(S.cfg, 4)
+    S = P.Solver(nx=nx, ny=ny, p=16, periodic=periodic, overlap=2, weight=5)
+    dx, dy, keep, t = _tables_xy(nx, ny, periodic)
     m = t["p"] + 1 + 2 * t["n_o"]
     # FP64 bar of the sweep tests: eps * m^3 (four length-m contractions)
     tol = max(1e-12, np.finfo(np.float64).eps * m**3)
@@ -46,7 +56,7 @@ def test_noalloc_correction_matches_regular_entry_point(periodic):
         u_ref = torch.zeros_like(r)
         S.smooth(u_ref, r, 1)  # from u = 0 the residual is r itself
         u = torch.zeros_like(r)
-        P.sem_schwarz_correction_noalloc(d, d, r, u)
+        P.sem_schwarz_correction_noalloc(dx, dy, r, u)
         torch.cuda.synchronize()
         a, b = u.cpu().numpy(), u_ref.cpu().numpy()
         assert np.abs(a - b).max() <= tol * np.abs(b).max()
@@ -59,9 +69,36 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch():
     cfg = P.make_config(nx=8, ny=8, p=16, overlap=2)
     d, keep, _ = _tables(cfg, 4)
     big = P.sem_sweep_tables(n=128, p=16, n_o=2, periodic=0, tab=d.tab, S=d.S, lam=d.lam, w=d.w)
-    r = torch.zeros(8, dtype=torch.float64, device="cuda")  # never touched: the call is rejected first
+    # never touched: the call is rejected before any device work
+    r = torch.zeros((128 * 16 + 1) ** 2, dtype=torch.float64, device="cuda")
     with pytest.raises(P.SemError) as ei:
         P.sem_schwarz_correction_noalloc(big, big, r, r)
     assert ei.value.status == P.SEM_BAD_ARG
     assert "static limit" in str(ei.value)
+    del keep
+
+
+def test_noalloc_rejects_windows_beyond_shared_memory_then_runs():
+    """p = 32, n_o = 26 (m = 85) fits the static scratch on 2 x 2 elements but
+    its FP64 local solve does not fit one block's shared memory: a bad
+    argument, and a valid call right after it still succeeds."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cfg = P.make_config(nx=8, ny=8, p=16, overlap=2)
+    d, keep, _ = _tables(cfg, 4)
+    wide = P.sem_sweep_tables(n=2, p=32, n_o=26, periodic=0, tab=d.tab, S=d.S, lam=d.lam, w=d.w)
+    r = torch.zeros((2 * 32 + 1) ** 2, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.SemError) as ei:
+        P.sem_schwarz_correction_noalloc(wide, wide, r, r)
+    assert ei.value.status == P.SEM_BAD_ARG
+    assert "shared memory" in str(ei.value)
+    S = P.Solver(nx=8, ny=8, p=16, overlap=2, weight=5)
+    rr = torch.from_numpy(SI.uniform_nodal(23, S.shape).ravel()).cuda()
+    u_ref = torch.zeros_like(rr)
+    S.smooth(u_ref, rr, 1)
+    u = torch.zeros_like(rr)
+    P.sem_schwarz_correction_noalloc(d, d, rr, u)
+    torch.cuda.synchronize()
+    a, b = u.cpu().numpy(), u_ref.cpu().numpy()
+    assert np.abs(a - b).max() <= max(1e-12, np.finfo(np.float64).eps * 21**3) * np.abs(b).max()
     del keep
