@@ -70,6 +70,28 @@ typedef enum sem_overlap_rule {
   SEM_OVERLAP_CEIL2 = 3
 } sem_overlap_rule;
 
+/* Smoother of the V-cycle (Sec. 3.1, Alg. 3).
+ *   SEM_SMOOTH_ADDITIVE  weighted additive Schwarz, Alg. 2 (the default).
+ *   SEM_SMOOTH_MULT      multiplicative Schwarz, Alg. 1: the subdomains one
+ *                        after another, the residual recomputed before each
+ *                        local solve, the local solution added on the
+ *                        element's own closed node set without weights; the
+ *                        order of every second sweep reversed.  The
+ *                        subdomains are visited by colour classes (element
+ *                        indices modulo q per direction: q = 3 with Dirichlet
+ *                        walls, the smallest divisor q >= 3 of n when
+ *                        periodic), a class at a time, instead of the paper's
+ *                        lexicographic order: members of a class do not
+ *                        interact, so each class is one parallel launch.
+ *                        Poisson operator (nu_kind 0), FP64 or FP32
+ *                        precision, one problem (not batched), n >= 3 per
+ *                        direction when periodic; the weight setting is
+ *                        unused. */
+typedef enum sem_smoother {
+  SEM_SMOOTH_ADDITIVE = 0,
+  SEM_SMOOTH_MULT = 1
+} sem_smoother;
+
 /* Arithmetic of the multigrid preconditioner.  The outer MGCG iteration, the
  * operator application q = A p, the coarse solve and all dot products are
  * FP64 in every mode.
@@ -119,6 +141,13 @@ typedef struct sem_config {
    * interface use the same pair, so the weights keep the partition of unity. */
   const double* learned_x;
   const double* learned_y;
+  int32_t smoother;        /* sem_smoother (default SEM_SMOOTH_ADDITIVE)          */
+  /* SEM_W_LEARNED with learned_x and learned_y both NULL: optional HOST array
+   * of SEM_MLP_PARAMS floats, the parameters of the weight network (layout
+   * below).  sem_create then computes the interface features
+   * (sem_learned_features), runs the network's forward kernel on the device
+   * and uses its (s, kt) outputs as learned_x / learned_y. */
+  const float* mlp_params;
 } sem_config;
 
 typedef struct sem_result {
@@ -132,7 +161,7 @@ typedef struct sem_result {
 typedef struct sem_handle sem_handle;
 
 /* Fill *cfg with defaults: 4x4 Dirichlet unit square, p = 4, n_o = 1, w_5,
- * MG(1,0) steps, FP64, tol 1e-10, i_max 200. */
+ * additive smoother, MG(1,0) steps, FP64, tol 1e-10, i_max 200. */
 void sem_default_config(sem_config* cfg);
 
 /* Set up a solver (sync).  Host FP64 set-up of Sec. 2 and Sec. 3: GLL nodes,
@@ -293,8 +322,8 @@ int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t);
 int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t);
 
 /* Allocation-free Schwarz correction.  The paper has no counterpart: this is a
- * deployment variant of the correction step of Alg. 2,
- *     u += sum_s R_s^T W A_ss^{-1} R_s r      (Eq. (correction:global)),
+ * deployment variant of the weighted additive correction
+ *     u += sum_s R_s^T W A_ss^{-1} R_s r
  * for callers that cannot call cudaMalloc: code that runs inside a host
  * framework which owns the device memory through its own pool and forbids
  * other allocators, code with a fixed memory budget, and latency-critical
@@ -312,9 +341,13 @@ int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t);
  * Scratch: the element-blocked corrections (n_x n_y m^2 doubles) live in one
  * static device array of 2^21 doubles (16 MiB) that every GPU loading this
  * library holds until the process exits.  Larger problems are rejected with
- * SEM_BAD_ARG and a message giving the size needed.  The first call on a
- * device (with that device current) looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.  All
+ * SEM_BAD_ARG and a message giving the size needed, and so are windows whose
+ * FP64 local solve (8 (4 m^2 + 4 m) bytes) exceeds the device's shared memory
+ * per block.  The first call on a device (with that device current) looks up
+ * the array's device address with cudaGetSymbolAddress and keeps it; make
+ * that first call before any stream capture.  cudaDeviceReset frees the array
+ * with the context: after a reset of a device, do not call this function on it
+ * again in the same process.  All
  * calls share the array and it keeps the last call's contents (every entry a
  * call reads is first written by the same call, so nothing needs clearing);
  * calls that overlap on the GPU, e.g. on two streams at once, race on it.
@@ -351,6 +384,16 @@ int sem_learned_features(const sem_config* cfg, float* feat_x, float* feat_y);
 /* Y[n][2] = network outputs for X[n][4]; transform = 1 maps them to
  * (s, kt) = (0.25 + 0.75 sigmoid(o0), 1 + 6 sigmoid(o1)). */
 int sem_mlp_forward(const float* params, const float* X, int32_t n, float* Y, int32_t transform, void* stream);
+/* Learned weights from the network, on an existing handle (sync): the
+ * handle is rebuilt as if sem_create had been called with its configuration,
+ * weight SEM_W_LEARNED and mlp_params = params (HOST array of SEM_MLP_PARAMS
+ * floats): interface features, one forward pass of the network on the device,
+ * (s, kt) per interface line and level, new weight tables.  The handle keeps
+ * its address; its captured solve graph and launch tuning are discarded.
+ * Errors: SEM_BAD_ARG (a handle of a batch, variable-cycle options that the
+ * learned weights do not support), SEM_CUDA_ERROR, SEM_OOM; on an error the
+ * handle is unchanged. */
+int sem_mlp_load(sem_handle* h, const float* params);
 /* Bytes of the caller-provided workspace for n samples. */
 int64_t sem_mlp_workspace_bytes(int32_t n);
 /* grad[SEM_MLP_PARAMS] and *loss (DEVICE) of the mean-squared loss against

@@ -25,12 +25,14 @@ SEM_W_TOPHAT, SEM_W_ARITH, SEM_W_IDENTITY, SEM_W_LEARNED = 100, 101, 102, 103
 SEM_OVERLAP_FIXED, SEM_OVERLAP_FLOOR8, SEM_OVERLAP_CEIL8, SEM_OVERLAP_CEIL2 = range(4)
 # sem_precision
 SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_TF32, SEM_PREC_BF16 = range(4)
+# sem_smoother
+SEM_SMOOTH_ADDITIVE, SEM_SMOOTH_MULT = range(2)
 
 EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
     "sem_inspect_level", "sem_gll_tables", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
-    "sem_learned_features", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
+    "sem_learned_features", "sem_mlp_load", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
     "sem_status_string", "sem_last_error",
@@ -51,6 +53,7 @@ class sem_config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("i_max", ctypes.c_int32),
         ("nu_kind", ctypes.c_int32), ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double),
         ("learned_x", ctypes.POINTER(ctypes.c_double)), ("learned_y", ctypes.POINTER(ctypes.c_double)),
+        ("smoother", ctypes.c_int32), ("mlp_params", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -114,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_schwarz_correction_noalloc": (i32, [ctypes.POINTER(sem_sweep_tables), ctypes.POINTER(sem_sweep_tables),
                                                  vp, vp, vp]),
         "sem_learned_features": (i32, [ctypes.POINTER(sem_config), vp, vp]),
+        "sem_mlp_load": (i32, [vp, ctypes.POINTER(ctypes.c_float)]),
         "sem_mlp_forward": (i32, [vp, vp, i32, vp, i32, vp]),
         "sem_mlp_workspace_bytes": (ctypes.c_int64, [i32]),
         "sem_mlp_loss_grad": (i32, [vp, vp, vp, i32, vp, vp, vp, vp]),
@@ -294,6 +298,13 @@ def sem_profile_read(h):
 
 def sem_schwarz_correction_noalloc(tx: sem_sweep_tables, ty: sem_sweep_tables, r, u, stream=None) -> None:
     """u += sum_s R_s^T W A_ss^{-1} R_s r without any allocation (see the C header for who needs this)."""
+    def nodes(t):
+        return t.n * t.p + (0 if t.periodic else 1)
+    want = nodes(tx) * nodes(ty)
+    for name, v in (("r", r), ("u", u)):
+        if v.numel() != want:
+            raise ValueError("%s has %d entries; the tables describe a %d x %d node grid"
+                             % (name, v.numel(), nodes(ty), nodes(tx)))
     _check(load_library().sem_schwarz_correction_noalloc(ctypes.byref(tx), ctypes.byref(ty), _ptr(r), _ptr(u),
                                                          _stream(stream)))
 
@@ -315,6 +326,14 @@ def sem_learned_features(cfg: sem_config):
     fy = np.zeros((L + 1, cfg.ny + 1, 4), dtype=np.float32)
     _check(load_library().sem_learned_features(ctypes.byref(cfg), fx.ctypes.data, fy.ctypes.data))
     return fx, fy
+
+
+def sem_mlp_load(h, params) -> None:
+    """Rebuild the handle's weights from the network parameters (HOST array)."""
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    if arr.size != SEM_MLP_PARAMS:
+        raise ValueError("expected %d network parameters, got %d" % (SEM_MLP_PARAMS, arr.size))
+    _check(load_library().sem_mlp_load(h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
 
 
 def sem_mlp_forward(params, X, Y, transform=True, stream=None):

@@ -84,6 +84,19 @@ template <typename T, typename TOut>
 cudaError_t launch_scatter(const DirView<T>& dx, const DirView<T>& dy, const T* E, TOut* u,
                            bool accum, cudaStream_t s);
 
+// ---- multiplicative Schwarz sweep (Alg. 1), k_mult.cu ---------------------
+// Colour classes per direction of the parallel order (0: no valid colouring,
+// a periodic mesh with n < 3).
+int mult_colours(int n, bool periodic);
+// Dynamic shared memory of one k_mult CTA at order p, window m, element size tsize.
+size_t mult_smem_bytes(int p, int m, size_t tsize);
+// One sweep of Alg. 1 over the level (u in place, right side f): the colour
+// classes in increasing order, or decreasing when reverse; one launch per
+// non-empty class (*launches receives the count).  Local solves in T.
+template <typename T, typename TU, typename TF>
+cudaError_t launch_mult_sweep(const DirView<T>& dx, const DirView<T>& dy, TU* u, const TF* f, bool reverse,
+                              cudaStream_t s, int* launches);
+
 // ---- grid transfer (Sec. 3.2), k_transfer.cu ------------------------------
 // fc = I^T rf from order pf to pf/2 on the same mesh (coarse walls 0).
 template <typename T>

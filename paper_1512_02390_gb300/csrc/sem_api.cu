@@ -7,12 +7,14 @@
 // launches and, once per MGCG iteration, reads the convergence flag.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <map>
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "kernels.h"
@@ -70,6 +72,7 @@ struct sem_handle {
   int device = 0;
   int L = 0;
   bool mixed = false;
+  bool mult = false;  // multiplicative Schwarz smoother (Alg. 1) instead of Alg. 2
   int sweep_mode = 0;
   Mesh1D mx, my;
   std::vector<Level> lev;
@@ -291,11 +294,25 @@ int sweep(sem_handle* h, const Level& l, const TIn* r, TU* u, bool accum, cudaSt
   return SEM_OK;
 }
 
+// n sweeps of the multiplicative Schwarz method (Alg. 1) on level l, u in
+// place, local solves in T; the class order is reversed on even sweeps
+template <typename T, typename TU, typename TF>
+int mult_sweeps(sem_handle* h, const Level& l, const TF* f, TU* u, int n, cudaStream_t s) {
+  const DirView<T>& dx = DX<T>(l);
+  const DirView<T>& dy = DY<T>(l);
+  const int nk = std::min(mult_colours(dx.n, dx.periodic != 0), dx.n) *
+                 std::min(mult_colours(dy.n, dy.periodic != 0), dy.n);
+  for (int i = 1; i <= n; ++i)
+    KLN(h, SEM_K_SWEEP, nk, s, (launch_mult_sweep<T, TU, TF>(dx, dy, u, f, i % 2 == 0, s, nullptr)));
+  return SEM_OK;
+}
+
 // n Schwarz steps from u = 0: the first residual is f itself
 template <typename T>
 int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cudaStream_t s) {
-  if (n <= 0) {
+  if (n <= 0 || h->mult) {
     CK(cudaMemsetAsync(u, 0, l.nodes * sizeof(T), s));
+    if (h->mult) return mult_sweeps<T, T, T>(h, l, f, u, n, s);
     return SEM_OK;
   }
   int rc = sweep<T, T, T>(h, l, f, u, false, s);
@@ -310,6 +327,7 @@ int smooth_from_zero(sem_handle* h, const Level& l, const T* f, T* u, int n, cud
 
 template <typename T, typename TF = T>
 int smooth(sem_handle* h, const Level& l, const TF* f, T* u, int n, cudaStream_t s) {
+  if (h->mult) return mult_sweeps<T, T, TF>(h, l, f, u, n, s);
   T* r = static_cast<T*>(l.r);
   for (int k = 0; k < n; ++k) {
     int rc = level_apply<T, TF>(h, l, SEM_K_APPLY_MG, u, f, r, 0, nullptr, nullptr, s);
@@ -357,7 +375,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
   for (int l = L; l >= 1 && l > low; --l) {
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     T* rl = static_cast<T*>(lv[l].r);
-    const bool fuse = lv[l].tune.fuse && h->ns1[l] == 1 && !lv[l].var;
+    const bool fuse = lv[l].tune.fuse && h->ns1[l] == 1 && !lv[l].var && !h->mult;
     if (l == L && !convert_top) {  // right side rtop (FP64)
       if (fuse) {
         if ((rc = level_down_fused<T, double>(h, lv[l], rtop, ul, s))) return rc;
@@ -732,7 +750,7 @@ int autotune(sem_handle* h, const std::string& path, cudaStream_t s) {
       lv.tune = v;
       continue;
     }
-    const bool allow_fuse = h->ns1[l] == 1 && !lv.var;
+    const bool allow_fuse = h->ns1[l] == 1 && !lv.var && !h->mult;
     if (!allow_fuse && !(h->mixed && h->sweep_mode != 0)) {
       lv.tune = TuneVal{};  // a single candidate: nothing to time
     } else if (!h->mixed) {
@@ -874,6 +892,14 @@ static int validate(const sem_config& c, int& L) {
       }
   }
   if (c.nu_kind && c.periodic) return fail(SEM_BAD_ARG, "variable diffusivity needs Dirichlet walls");
+  if (c.smoother != SEM_SMOOTH_ADDITIVE && c.smoother != SEM_SMOOTH_MULT) return fail(SEM_BAD_ARG, "unknown smoother");
+  if (c.smoother == SEM_SMOOTH_MULT) {
+    if (c.precision != SEM_PREC_FP64 && c.precision != SEM_PREC_FP32)
+      return fail(SEM_BAD_ARG, "the multiplicative smoother runs in FP64 or FP32 precision");
+    if (c.nu_kind) return fail(SEM_BAD_ARG, "the multiplicative smoother needs the Poisson operator (nu_kind 0)");
+    if (c.periodic && (c.nx < 3 || c.ny < 3))
+      return fail(SEM_BAD_ARG, "the multiplicative smoother needs n >= 3 per direction on a periodic mesh");
+  }
   if (c.nu_kind == 1 && !(c.nu_a >= 1.0)) return fail(SEM_BAD_ARG, "contrast must be >= 1");
   if (c.nu_kind == 2 && !(std::fabs(c.nu_a) < 1.0)) return fail(SEM_BAD_ARG, "amplitude must be in (-1, 1)");
   if (!c.x_edges && !(c.lx > 0)) return fail(SEM_BAD_ARG, "lx must be positive");
@@ -1035,7 +1061,7 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     if (rc0) return rc0;
   }
   if (nb < 1) return fail(SEM_BAD_ARG, "nb must be positive");
-  if (nb > 1 && (c.periodic || c.y_edges || c.nu_kind || c.weight == SEM_W_LEARNED))
+  if (nb > 1 && (c.periodic || c.y_edges || c.nu_kind || c.weight == SEM_W_LEARNED || c.smoother != SEM_SMOOTH_ADDITIVE))
     return fail(SEM_BAD_ARG, "stacked problems must be uniform Dirichlet Poisson problems");
   if (nb > 1 && c.ny % tile_elems(c.p) != 0)
     return fail(SEM_BAD_ARG, "stacked problems need ny divisible by the operator tile height");
@@ -1045,6 +1071,7 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   h->cfg = c;
   h->cfg.x_edges = h->cfg.y_edges = nullptr;
   h->cfg.learned_x = h->cfg.learned_y = nullptr;
+  h->cfg.mlp_params = nullptr;
   h->nb = nb;
   Mesh1D my1;  // one problem's y mesh (coarse factors)
   if (!mesh(c.nx, c.lx, c.x_edges, c.periodic != 0, h->mx) || !mesh(c.ny, c.ly, c.y_edges, c.periodic != 0, my1) ||
@@ -1060,6 +1087,25 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   }
   h->L = L;
   h->mixed = c.precision != SEM_PREC_FP64;
+  h->mult = c.smoother == SEM_SMOOTH_MULT;
+  if (h->mult) {  // the largest window must fit one CTA's shared memory
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(SEM_CUDA_ERROR, "cannot query the shared-memory limit");
+    }
+    for (int l = 1; l <= L; ++l) {
+      const int pl = 1 << l, no = overlap_for(c, pl);
+      const size_t need = mult_smem_bytes(pl, pl + 1 + 2 * no, h->mixed ? sizeof(float) : sizeof(double));
+      if (need > (size_t)optin) {
+        delete h;
+        return fail(SEM_BAD_ARG, "multiplicative smoother: level p=" + std::to_string(pl) + " needs " +
+                                     std::to_string(need) + " bytes of shared memory per block; the device allows " +
+                                     std::to_string(optin));
+      }
+    }
+  }
   h->sweep_mode = c.precision == SEM_PREC_TF32 ? 1 : (c.precision == SEM_PREC_BF16 ? 2 : 0);
   h->ns1.assign(L + 1, 0);
   h->ns2.assign(L + 1, 0);
@@ -1267,10 +1313,101 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
   return SEM_OK;
 }
 
+// (s, kt) of every interface line and level from the weight network: the
+// features of sem_learned_features, one forward pass (with the output
+// transform) on the current device, widened to double.  lx / ly receive the
+// layout of sem_config.learned_x / learned_y.
+static int learned_from_network(const sem_config& c, const float* params, std::vector<double>& lx,
+                                std::vector<double>& ly) {
+  sem_config cw = c;
+  cw.weight = SEM_W_QUINTIC;
+  cw.learned_x = cw.learned_y = nullptr;
+  int L, rc;
+  if ((rc = validate(cw, L))) return rc;
+  const size_t nfx = (size_t)(L + 1) * (c.nx + 1), nfy = (size_t)(L + 1) * (c.ny + 1);
+  std::vector<float> fx(4 * nfx), fy(4 * nfy);
+  if ((rc = sem_learned_features(&cw, fx.data(), fy.data()))) return rc;
+  const size_t nmax = std::max(nfx, nfy);
+  float *dp = nullptr, *dX = nullptr, *dY = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dp);
+    cudaFree(dX);
+    cudaFree(dY);
+  };
+  if (cudaMalloc(&dp, SEM_MLP_PARAMS * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&dX, 4 * nmax * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&dY, 2 * nmax * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(SEM_OOM, "weight network: cudaMalloc failed");
+  }
+  std::vector<float> y;
+  for (int dir = 0; dir < 2 && rc == SEM_OK; ++dir) {
+    const std::vector<float>& f = dir ? fy : fx;
+    const size_t n = dir ? nfy : nfx;
+    y.assign(2 * n, 0.f);
+    if (cudaMemcpy(dp, params, SEM_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dX, f.data(), 4 * n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(SEM_CUDA_ERROR, "weight network: upload failed");
+      break;
+    }
+    if ((rc = sem_mlp_forward(dp, dX, (int32_t)n, dY, 1, nullptr))) break;
+    if (cudaMemcpy(y.data(), dY, 2 * n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(SEM_CUDA_ERROR, "weight network: forward pass failed");
+      break;
+    }
+    std::vector<double>& out = dir ? ly : lx;
+    out.assign(y.begin(), y.end());
+  }
+  cleanup();
+  return rc;
+}
+
 int sem_create(const sem_config* cfg, sem_handle** out) {
   g_err.clear();
   if (!cfg || !out) return fail(SEM_BAD_ARG, "null argument");
+  if (cfg->weight == SEM_W_LEARNED && !cfg->learned_x && !cfg->learned_y && cfg->mlp_params) {
+    std::vector<double> lx, ly;
+    int rc = learned_from_network(*cfg, cfg->mlp_params, lx, ly);
+    if (rc) return rc;
+    sem_config c = *cfg;
+    c.learned_x = lx.data();
+    c.learned_y = ly.data();
+    return create_handle(c, 1, out);
+  }
   return create_handle(*cfg, 1, out);
+}
+
+int sem_mlp_load(sem_handle* h, const float* params) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!params) return fail(SEM_BAD_ARG, "null parameters");
+  if (h->nb != 1) return fail(SEM_BAD_ARG, "sem_mlp_load: not for a handle of stacked problems");
+  if (cudaSetDevice(h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SEM_CUDA_ERROR, "cannot make the handle's device current");
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SEM_CUDA_ERROR, "device error before sem_mlp_load");
+  }
+  sem_config c = h->cfg;
+  const std::vector<double> xe = h->mx.edges, ye = h->my.edges;  // the handle's own mesh
+  c.x_edges = xe.data();
+  c.y_edges = ye.data();
+  c.weight = SEM_W_LEARNED;
+  c.learned_x = c.learned_y = nullptr;
+  std::vector<double> lx, ly;
+  if ((rc = learned_from_network(c, params, lx, ly))) return rc;
+  c.learned_x = lx.data();
+  c.learned_y = ly.data();
+  sem_handle* fresh = nullptr;
+  if ((rc = create_handle(c, 1, &fresh))) return rc;
+  std::swap(*h, *fresh);  // h takes the new state; fresh now owns the old one
+  sem_destroy(fresh);
+  return SEM_OK;
 }
 
 int sem_sizes(const sem_handle* h, int64_t* n_unknowns, int64_t* nx_nodes, int64_t* ny_nodes) {
@@ -1312,6 +1449,9 @@ int sem_smooth(sem_handle* h, double* u, const double* f, int32_t n_it, void* st
   if (!u || !f || n_it < 0) return fail(SEM_BAD_ARG, "invalid argument");
   cudaStream_t s = as_stream(stream);
   const Level& lv = top(h);
+  if (h->mult)  // Alg. 1: every local solve forms its own residual
+    return h->mixed ? mult_sweeps<float, double, double>(h, lv, f, u, n_it, s)
+                    : mult_sweeps<double, double, double>(h, lv, f, u, n_it, s);
   for (int k = 0; k < n_it; ++k) {
     if ((rc = apply64(h, u, f, h->r, 0, nullptr, s))) return rc;
     rc = h->mixed ? sweep<float, double, double>(h, lv, h->r, u, true, s)

@@ -15,8 +15,11 @@ _PREC = {"fp64": B.SEM_PREC_FP64, "fp32": B.SEM_PREC_FP32, "tf32": B.SEM_PREC_TF
 
 def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weight=5, ns1=1, ns2=0,
                 variable_cycle=False, precision="fp64", tol=1e-10, i_max=200, x_edges=None, y_edges=None,
-                nu=None, learned_x=None, learned_y=None):
-    """nu: None (Poisson), ("contrast", c) or ("paper", amplitude, shift)."""
+                nu=None, learned_x=None, learned_y=None, smoother="add", mlp_params=None):
+    """nu: None (Poisson), ("contrast", c) or ("paper", amplitude, shift).
+    smoother: "add" (Alg. 2) or "mult" (Alg. 1).  mlp_params: the weight
+    network's parameters, used by sem_create when weight="learned" and no
+    learned_x / learned_y are given."""
     cfg = B.sem_default_config()
     cfg.nx, cfg.ny, cfg.p, cfg.periodic = nx, ny, p, int(bool(periodic))
     cfg.lx, cfg.ly = lx, ly
@@ -28,6 +31,7 @@ def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weig
     cfg.ns1, cfg.ns2, cfg.variable_cycle = ns1, ns2, int(bool(variable_cycle))
     cfg.precision = _PREC[precision]
     cfg.tol, cfg.i_max = tol, i_max
+    cfg.smoother = {"add": B.SEM_SMOOTH_ADDITIVE, "mult": B.SEM_SMOOTH_MULT}[smoother]
     if nu is not None:
         if nu[0] == "contrast":
             cfg.nu_kind, cfg.nu_a, cfg.nu_b = 1, float(nu[1]), 0.0
@@ -41,6 +45,12 @@ def make_config(nx=4, ny=4, p=4, periodic=False, lx=1.0, ly=1.0, overlap=1, weig
             arr = np.ascontiguousarray(e, dtype=np.float64)
             keep.append(arr)
             setattr(cfg, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if mlp_params is not None:
+        arr = np.ascontiguousarray(mlp_params, dtype=np.float32)
+        if arr.size != B.SEM_MLP_PARAMS:
+            raise ValueError("expected %d network parameters" % B.SEM_MLP_PARAMS)
+        keep.append(arr)
+        cfg.mlp_params = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     cfg._keep = keep  # keep edge arrays alive while the config is in use
     return cfg
 
@@ -103,6 +113,10 @@ class Solver:
 
     def get_tune(self, level):
         return B.sem_get_tune(self.h, level)
+
+    def mlp_load(self, params):
+        """Learned weights from the network parameters (sem_mlp_load)."""
+        B.sem_mlp_load(self.h, params)
 
     def set_low_cycle(self, enable):
         B.sem_set_low_cycle(self.h, enable)

@@ -151,3 +151,55 @@ def test_learned_solve_full_size():
         got = ud.cpu().numpy().reshape(b.shape)
         assert np.linalg.norm(b - lev.apply(got)) <= 1.1e-10 * np.linalg.norm(b)
         assert _rel(got, ref) <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def c4_fp64_oracle():
+    """The oracle's FP64 MGCG solve of the learned-weight workload with w_5."""
+    H = O.Hierarchy(O.Mesh1D(np.asarray(SI.geometric_edges(N4, 1.0 / N4 / 32)), False),
+                    O.Mesh1D.uniform(N4, 1.0, False), P4, overlap=NO4, weight=5, nu=SI.nu_contrast(CONTRAST))
+    lev = H.top
+    b = lev.mass(SI.uniform_nodal(1, (lev.NY, lev.NX), -1.0, 1.0))
+    u, it, _ = H.mgcg(np.zeros_like(b), b, tol=1e-10, i_max=400)
+    return lev, b, u, it
+
+
+def test_fp64_variable_mgcg_full_size_matches_oracle(c4_fp64_oracle):
+    """The plain FP64 method on the learned-weight workload (B(nu) operator,
+    1/nu_bar local solves, dense coarse inverse): identical iterations and the
+    solution within 1e-12 of the oracle's."""
+    lev, b, want, it_o = c4_fp64_oracle
+    S = P.Solver(precision="fp64", weight=5, **_c4_kw())
+    S.autotune()
+    bd = _dev(b)
+    for _ in range(2):  # launch by launch, then the captured graph
+        ud = torch.zeros_like(bd)
+        res, _ = S.pcg_solve(ud, bd)
+        assert res.status == P.SEM_OK and res.iterations == it_o
+        got = ud.cpu().numpy().reshape(b.shape)
+        assert _rel(got, want) <= 1e-12
+
+
+def test_learned_handle_from_network_through_the_c_abi():
+    """The weight network evaluated inside the library: sem_create with the
+    network's parameters (features, forward kernel and (s, kt) tables in C),
+    and sem_mlp_load on a w_5 handle, solve bitwise like weights predicted in
+    Python and passed as learned_x / learned_y."""
+    from paper_1512_02390_gb300 import learned as LW
+    params, _ = LW.load_model()
+    px, py = LW.predict(params, **_c4_kw())
+    lev = _c4_level(weight=5)
+    bd = _dev(lev.mass(SI.uniform_nodal(1, (lev.NY, lev.NX), -1.0, 1.0)))
+    handles = [P.Solver(precision="tf32", weight="learned", learned_x=px.ravel(), learned_y=py.ravel(), **_c4_kw()),
+               P.Solver(precision="tf32", weight="learned", mlp_params=params, **_c4_kw()),
+               P.Solver(precision="tf32", weight=5, **_c4_kw())]
+    handles[2].mlp_load(params)
+    out = []
+    for S in handles:
+        ud = torch.zeros_like(bd)
+        res, hist = S.pcg_solve(ud, bd, history_len=400)
+        assert res.status == P.SEM_OK
+        out.append((res.iterations, hist, ud.cpu().numpy()))
+    for it, hist, u in out[1:]:
+        assert it == out[0][0]
+        assert np.array_equal(hist, out[0][1]) and np.array_equal(u, out[0][2])
