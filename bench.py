@@ -221,6 +221,37 @@ def _level_work(p, n_o_fixed, ne):
     return {"sweep_flops_per_cycle": sweep_flops, "sweep_launches_per_cycle": L, "sweep_bytes_per_cycle": sweep_bytes}
 
 
+def smoother_roofline(S, level_prof, tune, hbm_gbs, peak_src, steps):
+    """Roofline of the finest level's Schwarz smoothing step inside the
+    reduced-precision V-cycle, with the algorithmic bytes of the method:
+    one sweep from u = 0 reads the level residual and writes the correction,
+    4 + 4 B per node in FP32; when the scatter is fused into the level
+    residual, that kernel also reads f and u, + 8 B per node.  The element
+    windows E the sweep writes and the scatter reads are not counted.  Time:
+    the CUDA-event time of the level's sweep and scatter (or fused residual)
+    launches, per V-cycle."""
+    nodes = S.nx_nodes * S.ny_nodes
+    fused = bool(tune.get("fuse"))
+    sw_ms, sw_n = level_prof["sweep"]
+    if fused:
+        part_ms, part_n = level_prof["apply_mg"]
+        bytes_per_node = 16.0
+        kernels = "tcgen05 sweep + residual with the scatter fused"
+    else:
+        part_ms, part_n = level_prof["scatter"]
+        bytes_per_node = 8.0
+        kernels = "tcgen05 sweep + scatter"
+    cycles = max(1, sw_n)
+    t_ms = (sw_ms + part_ms) / cycles
+    alg = bytes_per_node * nodes
+    ach = alg / (t_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+            "traffic": None, "kernels": kernels, "level_p": S.cfg.p, "nodes": nodes,
+            "algorithmic_bytes_per_node": bytes_per_node, "algorithmic_bytes_per_step": alg,
+            "us_per_step": t_ms * 1e3, "sweep_us": sw_ms / cycles * 1e3, "second_kernel_us": part_ms / cycles * 1e3,
+            "v_cycles_timed": cycles, "peak_source": peak_src}
+
+
 def c5_configs(seed=7, count=512, prec="tf32"):
     """512 problems: n x n elements, n in {8,16,32,64}; p in {4,8,16,32};
     n_o in {1,2}, drawn uniformly and independently with SplitMix64."""
@@ -230,13 +261,13 @@ def c5_configs(seed=7, count=512, prec="tf32"):
                  tol=TOL, i_max=200) for a, b, c in d]
 
 
-def run_batched(args, flush, stream):
+def run_batched(args, flush, stream, prec="tf32"):
     """C5: one batch solve (all 512 problems, one graph launch) per step."""
     import torch
     import paper_1512_02390_gb300 as P
     import sem_inputs as SI
 
-    cfgs = c5_configs()
+    cfgs = c5_configs(prec=prec)
     t0 = time.perf_counter()
     batch = P.Batch(cfgs)
     setup_s = time.perf_counter() - t0
@@ -283,11 +314,12 @@ def run_batched(args, flush, stream):
     ms = float(np.mean(times))
     its = [r.iterations for r in res]
     ok = sum(1 for r in res if r.status == P.SEM_OK)
+    batch.close()
     return {"problems": len(cfgs), "groups": batch.groups, "unknowns": batch.unknowns, "ms_per_batch_solve": ms,
             "dof_per_s": batch.unknowns / (ms * 1e-3), "converged": ok, "iterations_min_max": [min(its), max(its)],
             "kernel_launches_per_solve": launches, "graph_launches_per_solve": 1, "setup_s": round(setup_s, 2),
             "autotune_s": round(tune_s, 2),
-            "precision": "tf32", "workload": "512 problems, seed 7: n^2 elements n in {8,16,32,64}, p in "
+            "precision": prec, "workload": "512 problems, seed 7: n^2 elements n in {8,16,32,64}, p in "
                                            "{4,8,16,32}, n_o in {1,2}, U[-1,1] nodal RHS, MGCG(1,0) w_5 to 1e-10"}
 
 
@@ -338,6 +370,189 @@ def run_learned(args, stream):
                        "h_y/32), nu = 1 + (c-1)(1/2 + 1/2 sin 2 pi x cos 2 pi y), MGCG to 1e-10, i_max 400; "
                        "fp64_w5: plain FP64 method; w5 / learned: TF32 V-cycle")
     return out
+
+
+def run_mult(args, stream):
+    """The multiplicative Schwarz smoother (Alg. 1, coloured order) against
+    the additive one on the headline workload, FP64 and FP32 V-cycles."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    out = {}
+    b = None
+    for smoother, prec in (("add", "fp64"), ("mult", "fp64"), ("mult", "fp32")):
+        S = P.Solver(nx=NX, ny=NY, p=P_ORDER, overlap=N_O, weight=5, precision=prec, smoother=smoother, tol=TOL,
+                     i_max=100)
+        if b is None:
+            fn = torch.from_numpy(SI.uniform_nodal(SEED, S.shape).ravel()).cuda()
+            b = torch.empty_like(fn)
+            S.mass(fn, b)
+        u = torch.zeros_like(b)
+        for _ in range(2):
+            u.zero_()
+            res, _ = S.pcg_solve(u, b)
+        times = []
+        for _ in range(3):
+            u.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, _ = S.pcg_solve(u, b)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        out["%s_%s" % (smoother, prec)] = {"iterations": res.iterations, "status": res.status, "rbar": res.rbar,
+                                           "ms_per_solve": ms, "dof_per_s": S.n_unknowns / (ms * 1e-3)}
+        S.close()
+    out["workload"] = WORKLOAD + "; mult: Alg. 1 in colour classes (9 launches per sweep)"
+    return out
+
+
+def run_aspect_study(args):
+    """Sec. 4.2, Fig. 3: MGCG variants at p = 16 on 16 x 16 periodic elements
+    of aspect ratio AR, r_bar and operator applications per decade omega_1
+    (the cost model of Sec. 4)."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    variants = {
+        "add_w5_10": ("add", 5, "ceil8", (1, 0), False), "add_w5_11": ("add", 5, "ceil8", (1, 1), False),
+        "mult_11": ("mult", 5, "ceil8", (1, 1), False), "add_w5_11_var": ("add", 5, "ceil8", (1, 1), True),
+        "mult_no0_22": ("mult", 5, 0, (2, 2), False), "add_wa_no1_11": ("add", "a", 1, (1, 1), False)}
+    out = {}
+    for AR in (1, 2, 4, 8, 16):
+        row = {}
+        for name, (sm, w, ov, ns, var) in variants.items():
+            S = P.Solver(nx=16, ny=16, p=16, periodic=True, lx=2.0 * AR, ly=2.0, overlap=ov, weight=w, smoother=sm,
+                         ns1=ns[0], ns2=ns[1], variable_cycle=var, tol=TOL, i_max=400)
+            x, y = S.coords()
+            f = 2 * np.pi**2 * np.sin(np.pi * x[None, :]) * np.sin(np.pi * y[:, None])
+            b = torch.empty(f.size, dtype=torch.float64, device="cuda")
+            S.mass(torch.from_numpy(f.ravel()).cuda(), b)
+            u = torch.from_numpy(SI.uniform_nodal(1, S.shape, 0.0, 1.0).ravel()).cuda()
+            res, _ = S.pcg_solve(u, b)
+            no = 2 if ov == "ceil8" else ov
+            cs = 2.0 if var else 4.0 / 3.0
+            om = (4 * (1 + 2 * no / 17) ** 3 * cs * sum(ns) + 2 * cs + 2.0) / 2.0 / res.rbar
+            row[name] = {"rbar": round(res.rbar, 4), "iterations": res.iterations, "omega1": round(om, 2)}
+            S.close()
+        out["AR%d" % AR] = row
+    out["workload"] = ("16x16 periodic elements, p=16, [0,2AR]x[0,2], u = sin(pi x) sin(pi y), random u0, MGCG to "
+                       "1e-10; add = Alg. 2, mult = Alg. 1 (coloured order); _10/_11/_22 = (pre, post) steps; "
+                       "var = variable V-cycle")
+    return out
+
+
+def run_variable_periodic(args, stream):
+    """Sec. 4.3 on the GPU: periodic [0,1]^2 (and [0,AR] x [0,1]) with
+    nu = 1 + nu_hat sin 2 pi (x - 0.2) sin 2 pi (y - 0.2), u = sin 2 pi x
+    sin 2 pi y, w_5.  First series: 8 x 8, p = 16, n_o = ceil(p_l/8),
+    MG(1,1) and MGCG(1,1) against nu_hat.  Second series: MGCG with the
+    variable V-cycle at nu_hat = 0.9 against AR, n_o = ceil(p_l/2)."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    def problem(n, p, nu_hat, AR=1, **kw):
+        S = P.Solver(nx=n, ny=n, p=p, periodic=True, lx=float(AR), ly=1.0, weight=5, nu=("paper", nu_hat, 0.2),
+                     tol=TOL, i_max=400, **kw)
+        x, y = S.coords()
+        X, Y = x[None, :], y[:, None]
+        tp = 2 * np.pi
+        nu = 1 + nu_hat * np.sin(tp * (X - 0.2)) * np.sin(tp * (Y - 0.2))
+        src = -(nu * (-2 * tp**2 * np.sin(tp * X) * np.sin(tp * Y))
+                + nu_hat * tp * np.cos(tp * (X - 0.2)) * np.sin(tp * (Y - 0.2)) * tp * np.cos(tp * X) * np.sin(tp * Y)
+                + nu_hat * tp * np.sin(tp * (X - 0.2)) * np.cos(tp * (Y - 0.2)) * tp * np.sin(tp * X) * np.cos(tp * Y))
+        b = torch.empty(src.size, dtype=torch.float64, device="cuda")
+        S.mass(torch.from_numpy(np.ascontiguousarray(src).ravel()).cuda(), b)
+        u0 = torch.from_numpy(SI.uniform_nodal(1, S.shape, 0.0, 1.0).ravel()).cuda()
+        return S, b, u0
+
+    first = {}
+    for nu_hat in (0.0, 0.3, 0.6, 0.9):
+        S, b, u0 = problem(8, 16, nu_hat, overlap="ceil8", ns1=1, ns2=1)
+        rmg, _ = S.mg_solve(u0.clone(), b)
+        u = u0.clone()
+        rcg, _ = S.pcg_solve(u, b)
+        u = u0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rcg, _ = S.pcg_solve(u, b)
+        e1.record(stream)
+        e1.synchronize()
+        first["nu_hat=%.1f" % nu_hat] = {"mg_rbar": round(rmg.rbar, 4), "mg_cycles": rmg.iterations,
+                                         "mgcg_rbar": round(rcg.rbar, 4), "mgcg_iterations": rcg.iterations,
+                                         "mgcg_ms": e0.elapsed_time(e1)}
+        S.close()
+    r9, r0 = first["nu_hat=0.9"]["mgcg_rbar"], first["nu_hat=0.0"]["mgcg_rbar"]
+    first["paper"] = {"mgcg_rbar_at_0.9": 0.91, "cycle_ratio_0.9_over_0": 2.2}
+    first["measured"] = {"mgcg_rbar_at_0.9": r9, "cycle_ratio_0.9_over_0": float(np.ceil(10 / r9) / np.ceil(10 / r0)),
+                         "mgcg_over_mg_at_0.9": r9 / first["nu_hat=0.9"]["mg_rbar"]}
+    second = {}
+    for n in (8, 16, 32):
+        for p in (8, 16):
+            row = {}
+            for AR in (1, 2, 4, 8, 16):
+                S, b, u0 = problem(n, p, 0.9, AR=AR, overlap="ceil2", ns1=1, ns2=1, variable_cycle=True)
+                res, _ = S.pcg_solve(u0, b)
+                row["AR%d" % AR] = {"rbar": round(res.rbar, 4), "iterations": res.iterations,
+                                    "status": P.status_name(res.status)}
+                S.close()
+            second["%dx%d_p%d" % (n, n, p)] = row
+    return {"first_series": first, "second_series_mgcg_var": second,
+            "workload": "periodic, nu_hat sweep on 8x8 p=16 (MG(1,1), MGCG(1,1), n_o=ceil(p_l/8)); AR sweep at "
+                        "nu_hat=0.9, MGCG(1,1) variable V-cycle, n_o=ceil(p_l/2); random u0 in [0,1], tol 1e-10"}
+
+
+def host_cpu():
+    """Model name and logical core count of the host CPU."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or "unknown", "logical_cores": os.cpu_count()}
+
+
+def oracle_all_cores(nx, ny, p, n_o, seed, tol):
+    """One single-threaded oracle solve in each of nproc processes at once
+    (replicas with seeds seed, seed + 1, ...): aggregate DOF/s over the
+    wall time, the all-cores counterpart of the one-thread baseline."""
+    n = os.cpu_count() or 1
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "from oracle import sem_oracle as O\n"
+        "import sem_inputs as SI\n"
+        "H = O.uniform_hierarchy(%d, %d, %d, periodic=False, overlap=%d, weight=5)\n"
+        "lev = H.top\n"
+        "f = lev.mass(SI.uniform_nodal(int(sys.argv[1]), (lev.NY, lev.NX), -1.0, 1.0))\n"
+        "sys.stdout.write('ready\\n'); sys.stdout.flush(); sys.stdin.readline()\n"
+        "t = time.perf_counter(); u, it, hist = H.mgcg(np.zeros_like(f), f, tol=%r)\n"
+        "print(json.dumps({'t': time.perf_counter() - t, 'unknowns': int(lev.unknown.sum()), 'it': it}))\n"
+    ) % (ROOT, nx, ny, p, n_o, tol)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(seed + k)], stdin=subprocess.PIPE,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env) for k in range(n)]
+    for pr in procs:  # set-up done everywhere before the clock starts
+        pr.stdout.readline()
+    t0 = time.perf_counter()
+    for pr in procs:
+        pr.stdin.write("go\n")
+        pr.stdin.flush()
+    res = [json.loads(pr.communicate(timeout=3600)[0].strip().splitlines()[-1]) for pr in procs]
+    wall = time.perf_counter() - t0
+    return {"value": sum(r["unknowns"] for r in res) / wall, "unit": "DOF/s", "cores": n, "kind": "oracle",
+            "sample": "%d concurrent single-threaded oracle MGCG solves of the workload (seeds %d..%d), aggregate "
+                      "unknowns / wall time" % (n, seed, seed + n - 1), "wall_s": round(wall, 2)}
 
 
 def replica_seed(rank):
@@ -456,7 +671,12 @@ def run_large(args, stream):
         u.zero_()
         S.pcg_solve(u, b)
         prof = S.profile_read()
+        top_prof = S.profile_read_level(S.levels)
         S.profile(False)
+        if prec != "fp64":
+            pk, src = _peaks()
+            out["smoother_roofline"] = smoother_roofline(S, top_prof, S.get_tune(S.levels), pk.get("hbm_gbs", 6800.0),
+                                                         src, 1)
         out[prec] = {"ms_per_solve": ms, "step_ms": [round(t, 3) for t in times],
                      "dof_per_s": S.n_unknowns / (ms * 1e-3), "iterations": res.iterations,
                      "status": res.status, "class_ms_per_solve": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
@@ -592,6 +812,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, from a profiled pass (same steps)
     _, _, kprof = timed(S, b, args.steps, 1, profile=True)
+    top_prof = S.profile_read_level(S.levels)
     S.profile(False)
     dom = max(kprof, key=lambda k: kprof[k][0])
     peaks, src = _peaks()
@@ -630,6 +851,8 @@ def run_ours(args):
     roof["class_ms"] = {k: round(v[0] / args.steps, 4) for k, v in kprof.items()}
     roof["class_launches_per_step"] = {k: v[1] / args.steps for k, v in kprof.items()}
 
+    sroof = {"64x64_p16 (L2-resident)": smoother_roofline(S, top_prof, S.get_tune(S.levels),
+                                                          peaks.get("hbm_gbs") or 6800.0, src, args.steps)}
     line = {
         "metric": METRIC, "value": variants["%s_no%d" % (HEADLINE, N_O)]["dof_per_s"], "unit": "DOF/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -645,18 +868,30 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(b.numel() * 8), "d2h_bytes_per_step": int(b.numel() * 8)},
         "gpu_launches": gpu_launches,
         "roofline": roof,
+        "smoother_roofline": sroof,
         "clocks": clocks,
     }
     if args.variants == "all" and rank == 0:
         line["batched"] = run_batched(args, flush, stream)
+        b64 = run_batched(args, flush, stream, prec="fp64")
+        line["batched"]["fp64"] = {k: b64[k] for k in ("ms_per_batch_solve", "dof_per_s", "converged",
+                                                       "iterations_min_max", "kernel_launches_per_solve")}
+        line["batched"]["speedup_vs_fp64"] = line["batched"]["dof_per_s"] / b64["dof_per_s"]
         line["learned"] = run_learned(args, stream)
         line["high_order_bf16"] = run_high_order(args, stream)
         line["large"] = run_large(args, stream)
+        if "smoother_roofline" in line["large"]:
+            sroof["256x256_p16 (HBM)"] = line["large"].pop("smoother_roofline")
+        line["mult_smoother"] = run_mult(args, stream)
+        line["aspect_study"] = run_aspect_study(args)
+        line["variable_diffusion_periodic"] = run_variable_periodic(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
         line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",
                                 "sample": "one full oracle MGCG solve of the same workload (%d iterations), "
-                                          "numpy FP64, single thread" % o["iterations"]}
+                                          "numpy FP64, single thread" % o["iterations"], "host": host_cpu()}
+        if args.variants == "all":
+            line["cpu_baseline_all_cores"] = oracle_all_cores(NX, NY, P_ORDER, N_O, SEED, TOL)
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -129,7 +129,8 @@ typedef struct sem_config {
    * nu is evaluated at the GLL nodes of every level; the residual uses B(nu),
    * the local solves are divided by the element mean nu_bar_s
    * (Eq. (subproblem:solution)) and the coarse problem is solved with a dense
-   * FP64 inverse of B_0(nu).  Dirichlet walls only. */
+   * FP64 inverse of B_0(nu) (periodic meshes: its pseudo-inverse, at most
+   * 32 x 32 elements). */
   int32_t nu_kind;
   double nu_a, nu_b;
   /* SEM_W_LEARNED: optional HOST arrays [level 0..L][interface 0..n][2] of
@@ -265,6 +266,12 @@ typedef enum sem_kernel_class {
  * pointer may be NULL (HOST arrays). */
 int sem_profile(sem_handle* h, int32_t enable);
 int sem_profile_read(sem_handle* h, double* ms, int64_t* launches);
+/* The timed launches since sem_profile of one V-cycle level (1..L: the
+ * level's smoothing, residual, restriction to level - 1 and prolongation
+ * from level - 1; 0: the coarse solve; -1: everything outside the V-cycle,
+ * e.g. the outer FP64 operator and MGCG vector updates), per class as in
+ * sem_profile_read; only launches timed with profiling on are counted. */
+int sem_profile_read_level(sem_handle* h, int32_t level, double* ms, int64_t* launches);
 
 /* ---- launch-shape autotuning --------------------------------------------------
  * Not in the paper: launch choices per level l = 1..log2(p) that change the

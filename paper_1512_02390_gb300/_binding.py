@@ -31,7 +31,7 @@ SEM_SMOOTH_ADDITIVE, SEM_SMOOTH_MULT = range(2)
 EXPORTS = [
     "sem_default_config", "sem_create", "sem_destroy", "sem_sizes", "sem_coords", "sem_mass",
     "sem_apply", "sem_smooth", "sem_vcycle", "sem_mg_solve", "sem_pcg_solve",
-    "sem_inspect_level", "sem_gll_tables", "sem_profile", "sem_profile_read", "sem_schwarz_correction_noalloc",
+    "sem_inspect_level", "sem_gll_tables", "sem_profile", "sem_profile_read", "sem_profile_read_level", "sem_schwarz_correction_noalloc",
     "sem_learned_features", "sem_mlp_load", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
@@ -114,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_gll_tables": (i32, [i32, dp, dp, dp, dp]),
         "sem_profile": (i32, [vp, i32]),
         "sem_profile_read": (i32, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "sem_profile_read_level": (i32, [vp, i32, dp, ctypes.POINTER(ctypes.c_int64)]),
         "sem_schwarz_correction_noalloc": (i32, [ctypes.POINTER(sem_sweep_tables), ctypes.POINTER(sem_sweep_tables),
                                                  vp, vp, vp]),
         "sem_learned_features": (i32, [ctypes.POINTER(sem_config), vp, vp]),
@@ -293,6 +294,16 @@ def sem_profile_read(h):
     cnt = np.zeros(n, dtype=np.int64)
     _check(load_library().sem_profile_read(h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def sem_profile_read_level(h, level: int):
+    """{class: (ms, launches)} of one V-cycle level since the last sem_profile call."""
+    n = len(KERNEL_CLASSES)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(load_library().sem_profile_read_level(h, int(level), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 

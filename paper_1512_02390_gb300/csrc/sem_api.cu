@@ -104,6 +104,9 @@ struct sem_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, end)
   std::vector<int> ev_cls;
+  std::vector<int> ev_lvl;  // V-cycle level of each traced launch (-1: outside the V-cycle)
+  std::vector<int> ev_nk;   // kernels in each traced launch
+  int cur_level = -1;       // level the V-cycle is working on (tracing)
   int ev_used = 0;
 };
 
@@ -198,8 +201,12 @@ void prof_begin(sem_handle* h, int cls, cudaStream_t s, int kernels = 1) {
     h->ev.push_back(a);
     h->ev.push_back(b);
     h->ev_cls.push_back(cls);
+    h->ev_lvl.push_back(-1);
+    h->ev_nk.push_back(0);
   }
   h->ev_cls[h->ev_used] = cls;
+  h->ev_lvl[h->ev_used] = h->cur_level;
+  h->ev_nk[h->ev_used] = kernels;
   cudaEventRecord(h->ev[2 * h->ev_used], s);
 }
 
@@ -372,7 +379,12 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
   int rc;
   // levels 1 .. low run in the persistent kernel (0: none)
   const int low = (!dbl && h->low_ok && h->low_on) ? h->lowc.top : 0;
+  struct LevelTag {  // tracing: launches inside the cycle carry their level
+    sem_handle* h;
+    ~LevelTag() { h->cur_level = -1; }
+  } tag{h};
   for (int l = L; l >= 1 && l > low; --l) {
+    h->cur_level = l;
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     T* rl = static_cast<T*>(lv[l].r);
     const bool fuse = lv[l].tune.fuse && h->ns1[l] == 1 && !lv[l].var && !h->mult;
@@ -407,6 +419,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
        launch_restrict<T>(DX<T>(lv[l]), DY<T>(lv[l]), DX<T>(lv[l - 1]), DY<T>(lv[l - 1]), JL<T>(lv[l]), rl,
                           static_cast<T*>(lv[l - 1].f), s));
   }
+  h->cur_level = low ? low : 0;
   if (low) {
     KL(h, SEM_K_LOW_CYCLE, s, launch_low_cycle(h->lowc, h->sweep_mode, 1 << low, nullptr, s));
   } else if (h->Binv) {
@@ -418,6 +431,7 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
   }
   bool z_written = dbl;
   for (int l = low + 1; l <= L; ++l) {
+    h->cur_level = l;
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
     if (dot && l == L && h->ns2[l] == 0 && dot->gyp > 0) {
@@ -891,7 +905,8 @@ static int validate(const sem_config& c, int& L) {
             return fail(SEM_BAD_ARG, "learned (s, kt) must satisfy 0 < s <= 1, 1 <= kt <= 7");
       }
   }
-  if (c.nu_kind && c.periodic) return fail(SEM_BAD_ARG, "variable diffusivity needs Dirichlet walls");
+  if (c.nu_kind && c.periodic && (long)c.nx * c.ny > 1024)
+    return fail(SEM_BAD_ARG, "periodic variable diffusivity: at most 32 x 32 elements (dense coarse pseudo-inverse)");
   if (c.smoother != SEM_SMOOTH_ADDITIVE && c.smoother != SEM_SMOOTH_MULT) return fail(SEM_BAD_ARG, "unknown smoother");
   if (c.smoother == SEM_SMOOTH_MULT) {
     if (c.precision != SEM_PREC_FP64 && c.precision != SEM_PREC_FP32)
@@ -1677,6 +1692,25 @@ int sem_profile_read(sem_handle* h, double* ms, int64_t* launches) {
   }
   if (launches)
     for (int c = 0; c < SEM_K_NCLASS; ++c) launches[c] = h->launches[c];
+  return SEM_OK;
+}
+
+int sem_profile_read_level(sem_handle* h, int32_t level, double* ms, int64_t* launches) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (level < -1 || level > h->L) return fail(SEM_BAD_ARG, "level must be in [-1, L]");
+  for (int c = 0; c < SEM_K_NCLASS; ++c) {
+    if (ms) ms[c] = 0.0;
+    if (launches) launches[c] = 0;
+  }
+  for (int k = 0; k < h->ev_used; ++k) {
+    if (h->ev_lvl[k] != level) continue;
+    CK(cudaEventSynchronize(h->ev[2 * k + 1]));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->ev[2 * k], h->ev[2 * k + 1]));
+    if (ms) ms[h->ev_cls[k]] += t;
+    if (launches) launches[h->ev_cls[k]] += h->ev_nk[k];
+  }
   return SEM_OK;
 }
 

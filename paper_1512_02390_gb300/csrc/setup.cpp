@@ -490,9 +490,85 @@ void build_var(const Mesh1D& mx, const Mesh1D& my, int p, int kind, double a, do
     }
 }
 
+// Periodic mesh: B_0 is singular with the constants as null space, and the
+// coarse solution of Alg. 3 is the pseudo-inverse B_0^+ f_0.  Dense: with
+// M = B_0 + c 1 1^T (c = trace(B_0) / n^2, symmetric positive definite) and
+// the projector P = I - 1 1^T / n onto the range, B_0^+ = P M^{-1} P (for f in
+// the range, x = M^{-1} f solves B_0 x = f and is orthogonal to 1).
+static std::string coarse_var_pinv_periodic(const Mesh1D& mx, const Mesh1D& my, int kind, double a, double b,
+                                            std::vector<double>& inv) {
+  const int nx = mx.n, ny = my.n, n = nx * ny;
+  VarData v;
+  build_var(mx, my, 1, kind, a, b, v);
+  std::vector<double> M((size_t)n * n, 0.0);
+  const double* D = v.D.data();
+  for (int ey = 0; ey < ny; ++ey)
+    for (int ex = 0; ex < nx; ++ex) {
+      const size_t e = (size_t)ey * nx + ex;
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i)
+          for (int l = 0; l < 2; ++l)
+            for (int k = 0; k < 2; ++k) {
+              double kv = 0.0;
+              if (j == l)
+                for (int q = 0; q < 2; ++q) kv += v.Gx[e * 4 + j * 2 + q] * D[q * 2 + i] * D[q * 2 + k];
+              if (i == k)
+                for (int q = 0; q < 2; ++q) kv += v.Gy[e * 4 + q * 2 + i] * D[q * 2 + j] * D[q * 2 + l];
+              const int r = ((ey + j) % ny) * nx + (ex + i) % nx, c = ((ey + l) % ny) * nx + (ex + k) % nx;
+              M[(size_t)r * n + c] += kv;
+            }
+    }
+  double tr = 0.0;
+  for (int i = 0; i < n; ++i) tr += M[(size_t)i * n + i];
+  const double cst = tr / n / n;
+  for (auto& x : M) x += cst;
+  // dense Cholesky M = L L^T (lower triangle in place)
+  for (int j = 0; j < n; ++j) {
+    double d = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= M[(size_t)j * n + k] * M[(size_t)j * n + k];
+    if (!(d > 0.0)) return "coarse variable-diffusivity matrix is not positive definite on the range";
+    const double ljj = std::sqrt(d);
+    M[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double sum = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) sum -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+      M[(size_t)i * n + j] = sum / ljj;
+    }
+  }
+  // columns of M^{-1} P: solve M x = e_c - 1/n
+  std::vector<double> X((size_t)n * n), y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) y[i] = (i == c ? 1.0 : 0.0) - 1.0 / n;
+    for (int i = 0; i < n; ++i) {
+      double sum = y[i];
+      for (int k = 0; k < i; ++k) sum -= M[(size_t)i * n + k] * y[k];
+      y[i] = sum / M[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double sum = y[i];
+      for (int k = i + 1; k < n; ++k) sum -= M[(size_t)k * n + i] * y[k];
+      y[i] = sum / M[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + c] = y[i];
+  }
+  // P (M^{-1} P): subtract the column means
+  inv.assign((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    double mean = 0.0;
+    for (int i = 0; i < n; ++i) mean += X[(size_t)i * n + c];
+    mean /= n;
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = X[(size_t)i * n + c] - mean;
+  }
+  return "";
+}
+
 std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, double a, double b,
                                std::vector<double>& inv) {
-  if (mx.periodic || my.periodic) return "variable diffusivity needs Dirichlet walls";
+  if (mx.periodic != my.periodic) return "mixed periodic and Dirichlet directions are not supported";
+  if (mx.periodic) {
+    if ((long)mx.n * my.n > 1024) return "periodic variable diffusivity: at most 1024 coarse unknowns (32 x 32 elements)";
+    return coarse_var_pinv_periodic(mx, my, kind, a, b, inv);
+  }
   const int nux = mx.n - 1, nuy = my.n - 1, n = nux * nuy, bw = nux + 1;  // half bandwidth
   VarData v;
   build_var(mx, my, 1, kind, a, b, v);

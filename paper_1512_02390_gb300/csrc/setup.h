@@ -107,7 +107,8 @@ struct VarData {
 void build_var(const Mesh1D& mx, const Mesh1D& my, int p, int kind, double a, double b, VarData& out);
 
 // Dense inverse of B(nu) at p = 1 over the Dirichlet unknowns (row-major,
-// (nx-1)(ny-1) squared), by a banded Cholesky factorisation.
+// (nx-1)(ny-1) squared), by a banded Cholesky factorisation; on a periodic
+// mesh the dense pseudo-inverse over all nx ny coarse nodes (at most 1024).
 std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, double a, double b,
                                std::vector<double>& inv);
 

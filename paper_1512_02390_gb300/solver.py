@@ -103,6 +103,9 @@ class Solver:
     def profile_read(self):
         return B.sem_profile_read(self.h)
 
+    def profile_read_level(self, level):
+        return B.sem_profile_read_level(self.h, level)
+
     def autotune(self, cache_path=None, stream=None):
         """Pick the launch shapes of every level by timing (results unchanged)."""
         B.sem_autotune(self.h, cache_path, stream)

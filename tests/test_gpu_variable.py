@@ -99,3 +99,113 @@ def test_variable_pcg_matches_oracle(prec):
     else:
         assert np.linalg.norm(f - lev.apply(got)) <= 1.1e-10 * np.linalg.norm(f)
         assert _rel(got, want) < 1e-9
+
+
+# ---- the paper's variable-diffusion study (Sec. 4.3): periodic meshes ---------
+
+def _periodic_pair(nx, ny, p, nu_hat, shift=0.2, overlap="ceil8", **kw):
+    S = P.Solver(nx=nx, ny=ny, p=p, periodic=True, overlap=overlap, weight=5, nu=("paper", nu_hat, shift), **kw)
+    H = O.Hierarchy(O.Mesh1D.uniform(nx, 1.0, True), O.Mesh1D.uniform(ny, 1.0, True), p, overlap=overlap, weight=5,
+                    nu=SI.nu_paper(nu_hat, shift))
+    return S, H
+
+
+def _demean(a):
+    return a - a.mean()
+
+
+@pytest.mark.parametrize("case", [dict(nx=4, ny=4, p=8, nu_hat=0.9), dict(nx=5, ny=3, p=4, nu_hat=0.5, overlap=2),
+                                  dict(nx=3, ny=6, p=16, nu_hat=0.9)],
+                         ids=lambda c: "p%d_%dx%d" % (c["p"], c["nx"], c["ny"]))
+def test_periodic_variable_operator_sweep_vcycle_match_oracle(case):
+    """B(nu) with the periodic wrap, one Schwarz sweep, and the V-cycle with
+    the dense coarse pseudo-inverse of B_0(nu)."""
+    S, H = _periodic_pair(**case)
+    lev = H.top
+    u = SI.uniform_nodal(35, (lev.NY, lev.NX))
+    out = torch.empty(u.size, dtype=torch.float64, device="cuda")
+    S.apply(_dev(u), out)
+    assert _rel(_host(out, u.shape), lev.apply(u)) < 1e-13
+    f = lev.mass(SI.uniform_nodal(36, (lev.NY, lev.NX)))
+    m = lev.p + 1 + 2 * lev.n_o
+    tol = max(1e-12, np.finfo(np.float64).eps * m**3)
+    ud = _dev(u)
+    S.smooth(ud, _dev(f), 1)
+    assert _rel(_host(ud, u.shape), lev.wschwarz(u, f, 1)) < tol
+    ud = _dev(u)
+    S.vcycle(ud, _dev(f))
+    want = H.vcycle(u, f, *H.steps(1, 0))
+    assert _rel(_demean(_host(ud, u.shape)), _demean(want)) < tol
+
+
+def test_periodic_variable_mg11_variable_cycle_matches_oracle():
+    """The settings of the second variable-diffusion series: [0, 2] x [0, 1]
+    (AR = 2), n_o,l = ceil(p_l/2), one pre- and one post-smoothing, the
+    variable V-cycle."""
+    S = P.Solver(nx=4, ny=4, p=8, periodic=True, lx=2.0, ly=1.0, overlap="ceil2", weight=5, nu=("paper", 0.9, 0.2),
+                 ns1=1, ns2=1, variable_cycle=True)
+    H = O.Hierarchy(O.Mesh1D.uniform(4, 2.0, True), O.Mesh1D.uniform(4, 1.0, True), 8, overlap="ceil2", weight=5,
+                    nu=SI.nu_paper(0.9, 0.2))
+    lev = H.top
+    u = SI.uniform_nodal(37, (lev.NY, lev.NX))
+    f = lev.mass(SI.uniform_nodal(38, (lev.NY, lev.NX)))
+    ud = _dev(u)
+    S.vcycle(ud, _dev(f))
+    want = H.vcycle(u, f, *H.steps(1, 1, variable=True))
+    m = lev.p + 1 + 2 * lev.n_o
+    assert _rel(_demean(_host(ud, u.shape)), _demean(want)) < max(1e-12, np.finfo(np.float64).eps * m**3)
+
+
+def _study(nu_hat):
+    """Sec. 4.3, first series: periodic [0,1]^2, 8 x 8 elements, p = 16,
+    u = sin(2 pi x) sin(2 pi y), source -(nu lap u + grad nu . grad u),
+    n_o,l = ceil(p_l/8), w_5, one pre- and one post-smoothing, random u^0."""
+    s0 = 0.2
+    S, H = _periodic_pair(8, 8, 16, nu_hat, s0, ns1=1, ns2=1, tol=1e-10, i_max=100)
+    lev = H.top
+    X, Y = lev.mx.coords(16)[None, :], lev.my.coords(16)[:, None]
+    tp = 2 * np.pi
+    nu = SI.nu_paper(nu_hat, s0)(X, Y)
+    src = -(nu * (-2 * tp**2 * np.sin(tp * X) * np.sin(tp * Y))
+            + nu_hat * tp * np.cos(tp * (X - s0)) * np.sin(tp * (Y - s0)) * tp * np.cos(tp * X) * np.sin(tp * Y)
+            + nu_hat * tp * np.sin(tp * (X - s0)) * np.cos(tp * (Y - s0)) * tp * np.sin(tp * X) * np.cos(tp * Y))
+    b = lev.mass(src)
+    u0 = SI.uniform_nodal(1, b.shape, 0.0, 1.0)
+    return S, H, b, u0
+
+
+@pytest.mark.parametrize("nu_hat", [0.0, 0.9])
+def test_variable_diffusion_study_matches_oracle(nu_hat):
+    """MGCG(1,1) and MG(1,1) of the printed study on the GPU: the oracle's
+    iteration counts and residual histories, the MGCG solution within 1e-12
+    (up to the constant of the periodic null space)."""
+    S, H, b, u0 = _study(nu_hat)
+    want, it_o, hist_o = H.mgcg(u0.copy(), b, n1=1, n2=1, tol=1e-10, i_max=100)
+    ud = _dev(u0)
+    res, hist = S.pcg_solve(ud, _dev(b), history_len=101)
+    assert res.status == P.SEM_OK and res.iterations == it_o
+    np.testing.assert_allclose(hist, hist_o, rtol=1e-8, atol=1e-13 * hist_o[0])
+    assert _rel(_demean(_host(ud, b.shape)), _demean(want)) < 1e-12
+    _, hist_mg = H.mg_solve(u0.copy(), b, n1=1, n2=1, max_cycles=100)
+    ud = _dev(u0)
+    res_mg, hmg = S.mg_solve(ud, _dev(b), history_len=101)
+    assert res_mg.iterations == len(hist_mg) - 1
+    np.testing.assert_allclose(hmg, hist_mg, rtol=1e-8, atol=1e-13 * hist_mg[0])
+
+
+def test_variable_diffusion_study_reproduces_printed_values():
+    """Sec. 4.3 on the GPU: MGCG r_bar = 0.91 at nu_hat = 0.9 (within the
+    pins' band), nearly twice MG's rate, and 2.2 times the cycles of
+    nu_hat = 0."""
+    rates = {}
+    for nu_hat in (0.0, 0.9):
+        S, H, b, u0 = _study(nu_hat)
+        res, _ = S.pcg_solve(_dev(u0), _dev(b))
+        assert res.status == P.SEM_OK
+        rates[nu_hat] = res.rbar
+    S, H, b, u0 = _study(0.9)
+    res_mg, _ = S.mg_solve(_dev(u0), _dev(b))
+    assert abs(rates[0.9] - 0.91) <= 0.05 * 0.91 + 0.02, rates
+    assert 1.6 <= rates[0.9] / res_mg.rbar <= 2.0, (rates[0.9], res_mg.rbar)
+    ratio = np.ceil(10 / rates[0.9]) / np.ceil(10 / rates[0.0])
+    assert abs(ratio - 2.2) <= 0.25, ratio
