@@ -508,6 +508,46 @@ def run_variable_periodic(args, stream):
                         "nu_hat=0.9, MGCG(1,1) variable V-cycle, n_o=ceil(p_l/2); random u0 in [0,1], tol 1e-10"}
 
 
+def run_3d(args, stream):
+    """The three-dimensional extension: 16 x 16 x 16 Dirichlet elements,
+    p = 8 (2,048,383 unknowns), n_o = 1, w_5, MGCG(1,0) to 1e-10 from u = 0,
+    FP64 against the FP32 V-cycle inside the FP64 MGCG."""
+    import torch
+    import paper_1512_02390_gb300 as P
+    import sem_inputs as SI
+
+    out = {}
+    b = u64 = None
+    for prec in ("fp64", "fp32"):
+        S = P.Solver3(nx=16, ny=16, nz=16, p=8, overlap=1, weight=5, precision=prec, tol=TOL, i_max=100)
+        if b is None:
+            fn = torch.from_numpy(SI.uniform_nodal(SEED, S.shape).ravel()).cuda()
+            b = torch.empty_like(fn)
+            S.mass(fn, b)
+        u = torch.zeros_like(b)
+        res, _ = S.pcg_solve(u, b)
+        times = []
+        for _ in range(3):
+            u.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, _ = S.pcg_solve(u, b)
+            torch.cuda.synchronize()
+            times.append(1e3 * (time.perf_counter() - t0))
+        ms = float(np.median(times))
+        row = {"iterations": res.iterations, "status": res.status, "rbar": res.rbar, "ms_per_solve": ms,
+               "dof_per_s": S.n_unknowns / (ms * 1e-3), "unknowns": S.n_unknowns}
+        if prec == "fp64":
+            u64 = u.clone()
+        else:
+            row["rel_error_vs_fp64"] = float((u - u64).abs().max() / u64.abs().max())
+        out[prec] = row
+        S.close()
+    out["workload"] = ("3D: 16^3 Dirichlet elements on the unit cube, p=8, n_o=1, w_5, U[-1,1] nodal RHS (b = M f), "
+                       "MGCG(1,0) to 1e-10; host-driven iteration (wall time of the sync call)")
+    return out
+
+
 def host_cpu():
     """Model name and logical core count of the host CPU."""
     model = None
@@ -885,6 +925,7 @@ def run_ours(args):
         line["mult_smoother"] = run_mult(args, stream)
         line["aspect_study"] = run_aspect_study(args)
         line["variable_diffusion_periodic"] = run_variable_periodic(args, stream)
+        line["three_d"] = run_3d(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         o = _oracle_job(NX, NY, P_ORDER, N_O, SEED, TOL, 1)
         line["cpu_baseline"] = {"value": o["unknowns"] / o["times"][0], "unit": "DOF/s", "cores": 1, "kind": "oracle",

@@ -97,9 +97,13 @@ class Level3:
         """Delta u_s = A_ss^{-1} r_s by fast diagonalisation: three contractions
         with S^T, the division by lam_z + lam_y + lam_x, three with S."""
         sx, sy, sz = self.dx.subs[ex], self.dy.subs[ey], self.dz.subs[ez]
-        X = np.einsum("ka,jb,ic,kji->abc", sz.S, sy.S, sx.S, rs)
+        X = np.einsum("ka,kji->aji", sz.S, rs)     # S_z^T along z
+        X = np.einsum("jb,aji->abi", sy.S, X)      # S_y^T along y
+        X = np.einsum("ic,abi->abc", sx.S, X)      # S_x^T along x
         X = X / (sz.lam[:, None, None] + sy.lam[None, :, None] + sx.lam[None, None, :])
-        return np.einsum("ka,jb,ic,abc->kji", sz.S, sy.S, sx.S, X)
+        X = np.einsum("ka,abc->kbc", sz.S, X)      # S_z along z
+        X = np.einsum("jb,kbc->kjc", sy.S, X)      # S_y along y
+        return np.einsum("ic,kjc->kji", sx.S, X)   # S_x along x
 
     def schwarz_correction(self, r: np.ndarray) -> np.ndarray:
         """sum_s R_s^T W A_ss^{-1} R_s r with W = W_z (x) W_y (x) W_x."""
@@ -191,12 +195,16 @@ class Hierarchy3:
     def prolong(self, l: int, uc: np.ndarray) -> np.ndarray:
         """I_l u_{l-1} = (P_z (x) P_y (x) P_x) u_{l-1}."""
         Px, Py, Pz = self.P[l]
-        return np.einsum("ZK,YJ,XI,KJI->ZYX", Pz, Py, Px, uc)
+        u = np.einsum("XI,KJI->KJX", Px, uc)
+        u = np.einsum("YJ,KJX->KYX", Py, u)
+        return np.einsum("ZK,KYX->ZYX", Pz, u)
 
     def restrict(self, l: int, rf: np.ndarray) -> np.ndarray:
         """I_l^T r_l; coarse wall entries are not unknowns."""
         Px, Py, Pz = self.P[l]
-        rc = np.einsum("ZK,YJ,XI,ZYX->KJI", Pz, Py, Px, rf)
+        rc = np.einsum("XI,ZYX->ZYI", Px, rf)
+        rc = np.einsum("YJ,ZYI->ZJI", Py, rc)
+        rc = np.einsum("ZK,ZJI->KJI", Pz, rc)
         return np.where(self.levels[l - 1].unknown, rc, 0.0)
 
     def vcycle(self, u: np.ndarray, f: np.ndarray, ns1: int = 1, ns2: int = 0) -> np.ndarray:

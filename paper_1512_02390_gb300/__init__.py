@@ -7,4 +7,4 @@ include/sem_schwarz.h); this package only marshals arguments to it.
 """
 from ._binding import *  # noqa: F401,F403
 from ._binding import EXPORTS, LIB_PATH, SemError, load_library, sem_config, sem_result  # noqa: F401
-from .solver import Batch, Solver, make_config  # noqa: F401
+from .solver import Batch, Solver, Solver3, make_config  # noqa: F401

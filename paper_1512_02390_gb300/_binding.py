@@ -36,6 +36,8 @@ EXPORTS = [
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
     "sem_status_string", "sem_last_error",
+    "sem3_default_config", "sem3_create", "sem3_destroy", "sem3_sizes", "sem3_coords", "sem3_mass", "sem3_apply",
+    "sem3_smooth", "sem3_vcycle", "sem3_pcg_solve",
 ]
 SEM_MLP_PARAMS = 4610
 # sem_kernel_class
@@ -54,6 +56,16 @@ class sem_config(ctypes.Structure):
         ("nu_kind", ctypes.c_int32), ("nu_a", ctypes.c_double), ("nu_b", ctypes.c_double),
         ("learned_x", ctypes.POINTER(ctypes.c_double)), ("learned_y", ctypes.POINTER(ctypes.c_double)),
         ("smoother", ctypes.c_int32), ("mlp_params", ctypes.POINTER(ctypes.c_float)),
+    ]
+
+
+class sem3_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("p", ctypes.c_int32),
+        ("periodic", ctypes.c_int32), ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("overlap_rule", ctypes.c_int32), ("overlap", ctypes.c_int32), ("weight", ctypes.c_int32),
+        ("ns1", ctypes.c_int32), ("ns2", ctypes.c_int32), ("precision", ctypes.c_int32), ("tol", ctypes.c_double),
+        ("i_max", ctypes.c_int32),
     ]
 
 
@@ -134,6 +146,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_batch_autotune": (i32, [vp, ctypes.c_char_p, vp]),
         "sem_set_low_cycle": (i32, [vp, i32]),
         "sem_get_low_cycle": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "sem3_default_config": (None, [ctypes.POINTER(sem3_config)]),
+        "sem3_create": (i32, [ctypes.POINTER(sem3_config), ctypes.POINTER(vp)]),
+        "sem3_destroy": (None, [vp]),
+        "sem3_sizes": (i32, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "sem3_coords": (i32, [vp, dp, dp, dp]),
+        "sem3_mass": (i32, [vp, vp, vp, vp]),
+        "sem3_apply": (i32, [vp, vp, vp, vp]),
+        "sem3_smooth": (i32, [vp, vp, vp, i32, vp]),
+        "sem3_vcycle": (i32, [vp, vp, vp, vp]),
+        "sem3_pcg_solve": (i32, [vp, vp, vp, ctypes.POINTER(sem_result), dp, i32, vp]),
         "sem_status_string": (ctypes.c_char_p, [i32]),
         "sem_last_error": (ctypes.c_char_p, []),
     }
@@ -435,3 +458,62 @@ def sem_get_low_cycle(h):
     _check(load_library().sem_get_low_cycle(h, ctypes.byref(a), ctypes.byref(e)))
     return bool(a.value), bool(e.value)
 
+
+
+# ---- three-dimensional extension (include/sem_schwarz3d.h) ---------------------
+
+def sem3_default_config() -> sem3_config:
+    cfg = sem3_config()
+    load_library().sem3_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def sem3_create(cfg: sem3_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().sem3_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def sem3_destroy(h) -> None:
+    load_library().sem3_destroy(h)
+
+
+def sem3_sizes(h):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load_library().sem3_sizes(h, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def sem3_coords(h):
+    _, nx, ny, nz = sem3_sizes(h)
+    x, y, z = np.zeros(nx), np.zeros(ny), np.zeros(nz)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load_library().sem3_coords(h, x.ctypes.data_as(dp), y.ctypes.data_as(dp), z.ctypes.data_as(dp)))
+    return x, y, z
+
+
+def sem3_mass(h, f_nodal, b, stream=None) -> None:
+    _check(load_library().sem3_mass(h, _ptr(f_nodal), _ptr(b), _stream(stream)))
+
+
+def sem3_apply(h, u, Au, stream=None) -> None:
+    _check(load_library().sem3_apply(h, _ptr(u), _ptr(Au), _stream(stream)))
+
+
+def sem3_smooth(h, u, f, n_it=1, stream=None) -> None:
+    _check(load_library().sem3_smooth(h, _ptr(u), _ptr(f), int(n_it), _stream(stream)))
+
+
+def sem3_vcycle(h, u, f, stream=None) -> None:
+    _check(load_library().sem3_vcycle(h, _ptr(u), _ptr(f), _stream(stream)))
+
+
+def sem3_pcg_solve(h, u, f, history_len=0, stream=None):
+    """(sem_result, residual norms) of Alg. 4 in 3D; non-OK statuses are returned, not raised."""
+    res = sem_result()
+    hist = np.zeros(max(1, history_len))
+    rc = load_library().sem3_pcg_solve(h, _ptr(u), _ptr(f), ctypes.byref(res),
+                                       hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history_len else None,
+                                       int(history_len), _stream(stream))
+    _check(rc, allow=(SEM_OK, SEM_NOT_CONVERGED, SEM_BREAKDOWN))
+    return res, hist[:res.iterations + 1] if history_len else None

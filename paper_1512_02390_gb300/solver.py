@@ -165,6 +165,57 @@ class Batch:
         B.sem_batch_autotune(self.h, cache_path, stream)
 
 
+class Solver3:
+    """One handle of the three-dimensional extension on the current CUDA device."""
+
+    def __init__(self, nx=4, ny=4, nz=4, p=4, periodic=False, lx=1.0, ly=1.0, lz=1.0, overlap=1, weight=5, ns1=1,
+                 ns2=0, precision="fp64", tol=1e-10, i_max=200):
+        cfg = B.sem3_default_config()
+        cfg.nx, cfg.ny, cfg.nz, cfg.p, cfg.periodic = nx, ny, nz, p, int(bool(periodic))
+        cfg.lx, cfg.ly, cfg.lz = lx, ly, lz
+        if isinstance(overlap, str):
+            cfg.overlap_rule, cfg.overlap = _OVERLAP[overlap], 0
+        else:
+            cfg.overlap_rule, cfg.overlap = B.SEM_OVERLAP_FIXED, int(overlap)
+        cfg.weight = _WEIGHTS[weight]
+        cfg.ns1, cfg.ns2 = ns1, ns2
+        cfg.precision = _PREC[precision]
+        cfg.tol, cfg.i_max = tol, i_max
+        self.cfg = cfg
+        self.h = B.sem3_create(cfg)
+        self.n_unknowns, nxn, nyn, nzn = B.sem3_sizes(self.h)
+        self.shape = (nzn, nyn, nxn)
+
+    def close(self):
+        if self.h is not None:
+            B.sem3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coords(self):
+        return B.sem3_coords(self.h)
+
+    def mass(self, f_nodal, b, stream=None):
+        B.sem3_mass(self.h, f_nodal, b, stream)
+
+    def apply(self, u, Au, stream=None):
+        B.sem3_apply(self.h, u, Au, stream)
+
+    def smooth(self, u, f, n_it=1, stream=None):
+        B.sem3_smooth(self.h, u, f, n_it, stream)
+
+    def vcycle(self, u, f, stream=None):
+        B.sem3_vcycle(self.h, u, f, stream)
+
+    def pcg_solve(self, u, f, history_len=0, stream=None):
+        return B.sem3_pcg_solve(self.h, u, f, history_len, stream)
+
+
 def main(argv=None):
     """Solve one seeded random-RHS problem (b = M f, f ~ U[-1, 1] at the GLL
     nodes, u0 = 0) a few times and print one JSON line per solve:
