@@ -255,10 +255,8 @@ def smoother_roofline(S, level_prof, tune, hbm_gbs, peak_src, steps):
 def c5_configs(seed=7, count=512, prec="tf32"):
     """512 problems: n x n elements, n in {8,16,32,64}; p in {4,8,16,32};
     n_o in {1,2}, drawn uniformly and independently with SplitMix64."""
-    import sem_inputs as SI
-    d = (SI.uniform01(seed, 3 * count).reshape(count, 3) * np.array([4, 4, 2])).astype(int)
-    return [dict(nx=8 << int(a), ny=8 << int(a), p=4 << int(b), overlap=1 + int(c), weight=5, precision=prec,
-                 tol=TOL, i_max=200) for a, b, c in d]
+    from paper_1512_02390_gb300.solver import batch_workload
+    return batch_workload(count, seed, prec, TOL, 200)
 
 
 def run_batched(args, flush, stream, prec="tf32"):

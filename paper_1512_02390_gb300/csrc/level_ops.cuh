@@ -113,6 +113,44 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
     wcnt[i] = n;
   }
   __syncthreads();
+  if (E && 2 * dx.n_o < P) {
+    // at most two windows per direction hold a node: the loads of SB staged
+    // nodes (up to 4 windows each) are issued before any is summed, so one
+    // memory latency covers them; each node sums its windows in the order
+    // of the general loop below
+    constexpr int SB = 2;
+    for (int i0 = threadIdx.x; i0 < LN * LN; i0 += SB * blockDim.x) {
+      T w[SB][4];
+      int nyq[SB], nxq[SB];
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        const int idx = i0 + q * blockDim.x;
+        const int ly = idx / LN, lx = idx - ly * LN;
+        const bool in = idx < LN * LN && gnode[lx] >= 0 && gnode[LN + ly] >= 0;
+        nyq[q] = in ? wcnt[LN + ly] : 0;
+        nxq[q] = in ? wcnt[lx] : 0;
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < 2; ++ix)
+            w[q][iy * 2 + ix] =
+                (iy < nyq[q] && ix < nxq[q]) ? E[woff[(LN + ly) * 3 + iy] + woff[lx * 3 + ix]] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        const int idx = i0 + q * blockDim.x;
+        if (idx >= LN * LN) break;
+        const int ly = idx / LN, lx = idx - ly * LN;
+        T v = T(0);
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < 2; ++ix)
+            if (iy < nyq[q] && ix < nxq[q]) v += w[q][iy * 2 + ix];
+        su[ly * LP + lx] = v;
+      }
+    }
+  } else {
   for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
     const int ly = idx / LN, lx = idx - ly * LN;
     const int gx = gnode[lx], gy = gnode[LN + ly];
@@ -129,6 +167,7 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
       }
     }
     su[ly * LP + lx] = v;
+  }
   }
   // element stiffness of the tile and of its low-side neighbour (slot 0)
   for (int idx = threadIdx.x; idx < (TE + 1) * NP * NP; idx += blockDim.x) {

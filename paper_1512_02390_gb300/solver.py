@@ -136,6 +136,17 @@ class Solver:
             B.sem_set_tune(self.h, l, t["fuse"], t["spw"], tc, t["eo"])
 
 
+def batch_workload(count=512, seed=7, precision="tf32", tol=1e-10, i_max=200):
+    """The seeded batched workload: problem k has n x n elements (n in
+    {8, 16, 32, 64}), order p in {4, 8, 16, 32} and overlap n_o in {1, 2},
+    drawn uniformly and independently with SplitMix64 (seed 7), Dirichlet
+    walls, w_5."""
+    import sem_inputs as SI
+    d = (SI.uniform01(seed, 3 * count).reshape(count, 3) * np.array([4, 4, 2])).astype(int)
+    return [dict(nx=8 << int(a), ny=8 << int(a), p=4 << int(b), overlap=1 + int(c), weight=5, precision=precision,
+                 tol=tol, i_max=i_max) for a, b, c in d]
+
+
 class Batch:
     """Many independent problems solved together (sem_batch_*)."""
 
@@ -244,7 +255,40 @@ def main(argv=None):
     ap.add_argument("--trace", action="store_true")
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--set-tune", action="append", default=[])
+    ap.add_argument("--batch", type=int, default=0,
+                    help="solve the first N problems of the seeded batched workload instead (one batch "
+                         "solve per --solves; the first runs launch by launch, later ones replay the graph)")
     a = ap.parse_args(argv)
+    if a.batch:
+        cfgs = batch_workload(a.batch, precision=a.precision, tol=a.tol)
+        shapes = {}
+        for c in cfgs:
+            key = (c["nx"], c["p"], c["overlap"])
+            shapes[key] = shapes.get(key, 0) + 1
+        print(json.dumps({"groups": [{"n": k[0], "p": k[1], "n_o": k[2], "problems": v,
+                                      "nodes": v * (k[0] * k[1] + 1) ** 2} for k, v in sorted(shapes.items())]}))
+        Bt = Batch(cfgs)
+        if a.tune:
+            Bt.autotune()
+        us, fs = [], []
+        for k, c in enumerate(cfgs):
+            n = c["nx"] * c["p"] + 1
+            fs.append(torch.from_numpy(SI.uniform_nodal(1000 + k, (n, n)).ravel()).cuda())
+            us.append(torch.zeros_like(fs[-1]))
+        for k in range(a.solves):
+            for u in us:
+                u.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = Bt.solve(us, fs)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            print(json.dumps({"batch_solve": k, "problems": len(cfgs), "groups": Bt.groups, "unknowns": Bt.unknowns,
+                              "converged": sum(1 for r in res if r.status == 0), "ms": round(ms, 3),
+                              "dof_per_s": Bt.unknowns / (ms * 1e-3)}))
+        Bt.close()
+        return
     S = Solver(nx=a.nx, ny=a.ny, p=a.p, overlap=a.overlap, precision=a.precision, tol=a.tol, i_max=500)
     if a.tune:
         S.autotune()
