@@ -464,8 +464,12 @@ struct TcGeo {
   static constexpr uint32_t A_REGION = ((A_BYTES > STAGE_BYTES ? A_BYTES : STAGE_BYTES) + 15u) / 16u * 16u;
   static constexpr int PAD_CHUNK = M / EPC;  // first K chunk that holds padding columns
   static constexpr int COLS = NP <= 32 ? 32 : 64;
+  static constexpr int CW = (M + 31) / 32;  // gather passes over a window row (one column per lane)
+  // windows beyond 32 (p = 32) hold three subdomains per stack and about
+  // 60 KB of shared memory: three CTAs per SM, more registers per thread
+  static constexpr int MIN_CTAS = M <= 32 ? 8 : 3;
   static constexpr size_t SMEM = A_REGION + 4 * (size_t)B_BYTES + (size_t)(M * M + M) * sizeof(float);
-  static_assert(M <= 32 && ROWS <= kTcThreads && KP >= M, "window size outside the row-linear kernel");
+  static_assert(M <= 48 && ROWS <= kTcThreads && KP >= M, "window size outside the row-linear kernel");
   __host__ __device__ static constexpr uint32_t off_a(int r, int k) {
     return (uint32_t)(k / EPC) * LBO_A + (uint32_t)r * 16u + (uint32_t)(k % EPC) * ES;
   }
@@ -514,7 +518,7 @@ __device__ __forceinline__ void op_put16(unsigned char* p, const float* x) {
 }
 
 template <typename TIn, int MODE, int M>
-__global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, DirView<float> dy,
+__global__ void __launch_bounds__(kTcThreads, TcGeo<M, MODE>::MIN_CTAS) k_sweep_tcm(DirView<float> dx, DirView<float> dy,
                                                              const TIn* __restrict__ r, float* __restrict__ E,
                                                              const float* __restrict__ nu_inv, TcWork wk) {
   using Q = TcGeo<M, MODE>;
@@ -555,8 +559,10 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
   const bool row_ok = t < Q::ROWS;
   // transposed writes: element (row s_me M + c, column j_me) = tr + 16 c
   const uint32_t tr = Q::off_a(s_me * M, j_me);
-  // gather writes: element (row s M + warp + 4 i, column lane) = g_base + 16 (s M + 4 i)
-  const uint32_t g_base = Q::off_a(warp, min(lane, M - 1));
+  // gather writes: element (row s M + warp + 4 i, column lane + 32 c) = g_base[c] + 16 (s M + 4 i)
+  uint32_t g_base[Q::CW];
+#pragma unroll
+  for (int c = 0; c < Q::CW; ++c) g_base[c] = Q::off_a(warp, min(lane + 32 * c, M - 1));
   const int p = dx.p, no = dx.n_o, Nx = dx.N;
   const int per = (wk.ngroups + gridDim.x - 1) / gridDim.x;
   const int g0 = blockIdx.x * per, g1 = min(wk.ngroups, g0 + per);
@@ -645,13 +651,13 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
       }
     }
     // gather R_s r: warp w takes window rows w, w + 4, ... of every slot, lane
-    // b node b of the row; the loads of SB slots at a time are all issued
-    // before their stores, so one memory latency covers SB slots
+    // b nodes b, b + 32, ... of the row; the loads of SB slots at a time are
+    // all issued before their stores, so one memory latency covers SB slots
     constexpr int NA = (M + 3) / 4;
-    constexpr int SB = (Q::G + 1) / 2;
+    constexpr int SB = Q::CW > 1 ? 1 : (Q::G + 1) / 2;
 #pragma unroll
     for (int s0 = 0; s0 < Q::G; s0 += SB) {
-      TIn xv[SB][NA];
+      TIn xv[SB][Q::CW][NA];
 #pragma unroll
       for (int ds = 0; ds < SB; ++ds) {
         const int s = s0 + ds;
@@ -659,35 +665,42 @@ __global__ void __launch_bounds__(kTcThreads, 8) k_sweep_tcm(DirView<float> dx, 
         const int oy = __shfl_sync(0xffffffffu, oy_l, src);
         const int ox = __shfl_sync(0xffffffffu, ox_l, src);
         const int fl = s < Q::G ? __shfl_sync(0xffffffffu, fl_l, src) : 0;
-        if (fl == 1) {
-          // window inside the walls (warp-uniform): lanes past the window
-          // read its last column again and do not store
-          const TIn* rp = r + (long)(oy + warp) * Nx + ox + min(lane, M - 1);
-          const long step = 4L * Nx;
 #pragma unroll
-          for (int i = 0; i < NA; ++i)
-            xv[ds][i] = (i + 1 < NA || warp + 4 * i < M) ? rp[i * step] : TIn(0);
-        } else {
+        for (int c = 0; c < Q::CW; ++c) {
+          const int col = lane + 32 * c;
+          if (fl == 1) {
+            // window inside the walls (warp-uniform): lanes past the window
+            // read its last column again and do not store
+            const TIn* rp = r + (long)(oy + warp) * Nx + ox + min(col, M - 1);
+            const long step = 4L * Nx;
 #pragma unroll
-          for (int i = 0; i < NA; ++i) {
-            const int a = warp + 4 * i;
-            xv[ds][i] = TIn(0);
-            if (a < M && lane < M && fl != 0) {
-              const int gy = node_or_wall(oy + a, dy.N, dy.periodic, dy.segN);
-              const int gx = node_or_wall(ox + lane, Nx, dx.periodic, dx.segN);
-              if (gx >= 0 && gy >= 0) xv[ds][i] = r[(long)gy * Nx + gx];
+            for (int i = 0; i < NA; ++i)
+              xv[ds][c][i] = (i + 1 < NA || warp + 4 * i < M) ? rp[i * step] : TIn(0);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NA; ++i) {
+              const int a = warp + 4 * i;
+              xv[ds][c][i] = TIn(0);
+              if (a < M && col < M && fl != 0) {
+                const int gy = node_or_wall(oy + a, dy.N, dy.periodic, dy.segN);
+                const int gx = node_or_wall(ox + col, Nx, dx.periodic, dx.segN);
+                if (gx >= 0 && gy >= 0) xv[ds][c][i] = r[(long)gy * Nx + gx];
+              }
             }
           }
         }
       }
-      if (lane < M) {
 #pragma unroll
-        for (int ds = 0; ds < SB; ++ds) {
-          const int s = s0 + ds;
+      for (int c = 0; c < Q::CW; ++c) {
+        if (lane + 32 * c < M) {
 #pragma unroll
-          for (int i = 0; i < NA; ++i)
-            if (s < Q::G && (i + 1 < NA || warp + 4 * i < M))
-              op_put<MODE>(sA, g_base + (uint32_t)(s * M + 4 * i) * 16u, convert_to<float>(xv[ds][i]));
+          for (int ds = 0; ds < SB; ++ds) {
+            const int s = s0 + ds;
+#pragma unroll
+            for (int i = 0; i < NA; ++i)
+              if (s < Q::G && (i + 1 < NA || warp + 4 * i < M))
+                op_put<MODE>(sA, g_base[c] + (uint32_t)(s * M + 4 * i) * 16u, convert_to<float>(xv[ds][c][i]));
+          }
         }
       }
     }
@@ -880,10 +893,13 @@ cudaError_t sweep_tc_mode(const DirView<float>& dx, const DirView<float>& dy, co
                           const float* nu_inv, const TcWork& wk, cudaStream_t s) {
   if (dx.m != dy.m || dx.m > 64 || dx.m < 2 || wk.G != kTcThreads / dx.m || wk.ngroups <= 0 || !wk.sub || !wk.err)
     return cudaErrorInvalidValue;
-  switch (dx.m) {  // the finest levels at p = 16 (n_o = 1, 2, 3)
+  switch (dx.m) {  // the finest levels at p = 16 and p = 32 (n_o = 1, 2, 3)
     case 19: return sweep_tcm_launch<TIn, MODE, 19>(dx, dy, r, E, nu_inv, wk, s);
     case 21: return sweep_tcm_launch<TIn, MODE, 21>(dx, dy, r, E, nu_inv, wk, s);
     case 23: return sweep_tcm_launch<TIn, MODE, 23>(dx, dy, r, E, nu_inv, wk, s);
+    case 35: return sweep_tcm_launch<TIn, MODE, 35>(dx, dy, r, E, nu_inv, wk, s);
+    case 37: return sweep_tcm_launch<TIn, MODE, 37>(dx, dy, r, E, nu_inv, wk, s);
+    case 39: return sweep_tcm_launch<TIn, MODE, 39>(dx, dy, r, E, nu_inv, wk, s);
     default: break;
   }
   const TcLay L = tc_layout<MODE>(dx.m);

@@ -36,6 +36,8 @@ CASES = [
     dict(nx=12, ny=12, p=16, overlap=2, stretch=True),      # m = 21, a table per column (tables change mid-range)
     dict(nx=12, ny=10, p=16, overlap=1, nu=("contrast", 10.0)),  # m = 19, 1 / nu_bar per subdomain
     dict(nx=7, ny=6, p=32, overlap=2),                      # m = 37, three per stack, 48-column accumulator
+    dict(nx=6, ny=7, p=32, overlap=1, periodic=True),       # m = 35, periodic wrap
+    dict(nx=5, ny=6, p=32, overlap=3),                      # m = 39, two gather passes per window row
     dict(nx=24, ny=24, p=8, overlap=1, stretch=True),       # x geometric: a table per column
     dict(nx=16, ny=16, p=8, overlap=1, nu=("contrast", 10.0)),  # 1 / nu_bar per subdomain
 ]
