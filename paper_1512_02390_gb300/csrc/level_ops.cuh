@@ -74,8 +74,12 @@ __device__ __forceinline__ void apply_tile(const DirView<T>& dx, const DirView<T
   T* sMx = sLy + (TE + 1) * NP * NP;               // TN + 1
   T* sMy = sMx + (TN + 1);
   T* sbx = sMy + (TN + 1);                                    // [(TN + 1) x TE] left-edge x sums
-  double* sred = reinterpret_cast<double*>(
-      (reinterpret_cast<uintptr_t>(sbx + (TN + 1) * TE) + 15) & ~static_cast<uintptr_t>(15));
+  // the double / long tables start at the next 16-byte boundary; the offset
+  // is a constant, so the pointers stay derived from the shared array and
+  // their loads are shared-memory loads
+  constexpr size_t kTabOff =
+      (sizeof(T) * (LN * LP + 2 * (TE + 1) * NP * NP + 2 * (TN + 1) + (TN + 1) * TE) + 15) / 16 * 16;
+  double* sred = reinterpret_cast<double*>(smem_raw + kTabOff);
   long* woff = reinterpret_cast<long*>(sred + kRedThreads);  // [2 LN][3] E offsets (columns, then rows)
   int* gnode = reinterpret_cast<int*>(woff + 2 * 3 * LN);    // [2 LN] node or -1
   int* wcnt = gnode + 2 * LN;                                // [2 LN] windows holding it
