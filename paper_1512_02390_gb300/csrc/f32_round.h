@@ -1,5 +1,6 @@
-// IEEE 754 binary64 -> binary32 conversion, round to nearest, ties to even,
-// by integer operations on the bit fields.  On this GPU the conversion
+// Roundings by integer operations on the bit fields.
+//
+// IEEE 754 binary64 -> binary32 conversion, round to nearest, ties to even.  On this GPU the conversion
 // instruction issues on the narrow FP64 pipe; in the FP64-bound MGCG update
 // the integer form runs on the idle integer ALU instead.  Results whose
 // binary32 form is normal or overflows (|x| >= 2^-126) are formed here; zero
@@ -51,5 +52,13 @@ SEM_F32R_FN float f32_from_f64_rn(double x) {
 #endif
   return out;
 }
+
+// binary32 -> TF32 (the sign, the 8 exponent bits and the top 10 of the 23
+// fraction bits; the 13 dropped bits are zero in the result), round to
+// nearest, ties away from zero, on the bit pattern: add half a unit of the
+// last kept bit (bit 12) to the magnitude and clear the dropped bits.  A
+// carry out of the fraction moves the value to the next binade, which is the
+// correctly rounded result.  For finite values below the largest binade.
+SEM_F32R_FN uint32_t tf32_bits_rna(uint32_t f32_bits) { return (f32_bits + 0x1000u) & 0xFFFFE000u; }
 
 }  // namespace sem

@@ -32,6 +32,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "f32_round.h"
 #include "kernels.h"
 
 namespace sem {
@@ -136,11 +137,9 @@ __device__ __forceinline__ uint32_t op_off(int row, int k, const TcLay& L) {
   return row_off(row, L.sbo) + k_off<MODE>(k);
 }
 
-__device__ __forceinline__ uint32_t round_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// TF32 operand bits, round to nearest, ties away from zero (f32_round.h:
+// two integer operations)
+__device__ __forceinline__ uint32_t round_tf32(float x) { return tf32_bits_rna(__float_as_uint(x)); }
 
 template <int MODE>
 __device__ __forceinline__ void op_put(unsigned char* base, uint32_t off, float v) {

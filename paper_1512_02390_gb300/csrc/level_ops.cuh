@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "f32_round.h"
 #include "kernels.h"
 
 namespace sem {
@@ -484,11 +485,7 @@ constexpr size_t prolong_smem() {
 // Padding rows/columns of S are zero, so the padded products are exact
 // extensions of the m x m ones.
 
-__device__ __forceinline__ uint32_t f2tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+__device__ __forceinline__ uint32_t f2tf32(float x) { return tf32_bits_rna(__float_as_uint(x)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   uint32_t r;

@@ -155,3 +155,58 @@ def test_f32_rounding_matches_ieee_round_to_nearest_even(tmp_path):
     z = np.array([np.nan], dtype=np.float64)
     f(z.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(1))
     assert np.isnan(y[0])
+
+
+_TF32_SRC = r'''
+#include "f32_round.h"
+extern "C" void tf32(const unsigned* x, unsigned* y, long n) {
+  for (long i = 0; i < n; ++i) y[i] = sem::tf32_bits_rna(x[i]);
+}
+'''
+
+
+def test_tf32_rounding_is_round_to_nearest_ties_away(tmp_path):
+    """The tensor-core operands are rounded to TF32 by integer operations on
+    the binary32 bits; the result must be the nearer of the two neighbouring
+    TF32 values (10 fraction bits), ties away from zero, computed here by
+    exact float64 arithmetic: random values over the normal binades, exact
+    ties, values just below and above a tie, a carry into the next binade,
+    and zeros."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    src = tmp_path / "tf32.cpp"
+    src.write_text(_TF32_SRC)
+    so = tmp_path / "tf32.so"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1512_02390_gb300", "csrc")
+    subprocess.run(["g++", "-O2", "-shared", "-fPIC", "-I", inc, str(src), "-o", str(so)], check=True)
+    f = ctypes.CDLL(str(so)).tf32
+    rng = np.random.default_rng(7)
+    n = 200000
+    x = (np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-120, 120, n)) * rng.choice([-1.0, 1.0], n)).astype(np.float32)
+    # exact ties and their neighbours: a TF32 value plus half its unit, plus / minus one binary32 ulp
+    t = np.ldexp(rng.integers(1024, 2048, 3000).astype(np.float64) / 1024.0, rng.integers(-100, 100, 3000))
+    half = np.ldexp(1.0, np.frexp(t)[1] - 12)   # half a TF32 unit of t
+    ties = (t + half).astype(np.float32)
+    near = np.concatenate([ties, np.nextafter(ties, np.float32(0)), np.nextafter(ties, np.float32(np.inf)), -ties])
+    edge = np.array([0.0, -0.0, 1.0, -1.0, 2.0 - 2.0**-11, 2.0 - 2.0**-23, 1.0 + 2.0**-11, 1.0 + 2.0**-12],
+                    dtype=np.float32)
+    x = np.ascontiguousarray(np.concatenate([x, near, edge]).astype(np.float32))
+    y = np.empty(x.size, dtype=np.uint32)
+    f(x.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(x.size))
+    got = y.view(np.float32).astype(np.float64)
+    v = x.astype(np.float64)
+    mag = np.abs(v)
+    with np.errstate(divide="ignore"):
+        e = np.where(mag > 0, np.frexp(mag)[1] - 1, 0)   # v = m 2^e, 1 <= m < 2
+    unit = np.ldexp(1.0, e - 10)                          # TF32 unit in the binade of v
+    lo = np.floor(mag / unit) * unit
+    hi = lo + unit
+    want = np.where(mag - lo < hi - mag, lo, hi) * np.sign(v)
+    want = np.where(mag - lo == hi - mag, hi * np.sign(v), want)   # ties away from zero
+    want = np.where(mag == 0, v, want)
+    assert np.array_equal(got, want)
+    assert np.all((y & 0x1FFF) == 0)
