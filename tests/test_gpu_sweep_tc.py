@@ -28,7 +28,12 @@ def _need_gpu():
 U_IN = {"tf32": 2.0**-11, "bf16": 2.0**-8}
 
 CASES = [
+    dict(nx=32, ny=30, p=2, overlap=1),                     # m = 5, 25 per stack
     dict(nx=24, ny=20, p=4, overlap=1),                     # m = 7, 18 per stack, wall classes
+    dict(nx=20, ny=18, p=4, overlap=2, periodic=True),      # m = 9
+    dict(nx=16, ny=16, p=4, overlap=3),                     # m = 11
+    dict(nx=14, ny=12, p=8, overlap=3),                     # m = 15
+    dict(nx=12, ny=14, p=8, overlap=4),                     # m = 17, 7 per stack
     dict(nx=16, ny=12, p=8, overlap=2, periodic=True),      # m = 13, one table class
     dict(nx=12, ny=10, p=16, overlap=2),                    # m = 21, the bench's window
     dict(nx=12, ny=9, p=16, overlap=1),                     # m = 19
