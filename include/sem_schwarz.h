@@ -325,6 +325,21 @@ int sem_autotune(sem_handle* h, const char* cache_path, void* stream);
  * SEM_BAD_ARG where it is not available; both calls discard the captured graph. */
 int sem_set_low_cycle(sem_handle* h, int32_t enable);
 int sem_get_low_cycle(const sem_handle* h, int32_t* available, int32_t* enabled);
+/* The up-leg of the V-cycle (Alg. 3) in ONE launch.  With no post-smoothing
+ * on any level the up-leg is u_l <- u_l + I_l u_{l-1}, l = 1 .. L, and every
+ * level has the same element mesh, so one kernel takes each tile of elements
+ * from the coarse solution through all levels in shared memory and writes only
+ * the finest level's z (with the fused dot products of the MGCG update where
+ * the level-by-level path has them).  Results are identical, bit for bit, to
+ * the level-by-level prolongations (the end rows of the interpolation tables
+ * are exactly 0 and 1, so a node shared by two tiles gets the same value from
+ * either); u_1 .. u_{L-1} are left as the down-leg wrote them.  Available when
+ * p >= 4 and ns2 = 0 (also under variable_cycle); on by default; not used
+ * while the persistent low-level cycle is on.  sem_set_fused_prolongation(h,
+ * 1) fails with SEM_BAD_ARG where it is not available; both calls discard the
+ * captured graph. */
+int sem_set_fused_prolongation(sem_handle* h, int32_t enable);
+int sem_get_fused_prolongation(const sem_handle* h, int32_t* available, int32_t* enabled);
 int sem_get_tune(const sem_handle* h, int32_t level, sem_level_tune* t);
 int sem_set_tune(sem_handle* h, int32_t level, const sem_level_tune* t);
 

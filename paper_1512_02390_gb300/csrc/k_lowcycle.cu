@@ -49,13 +49,11 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
   __syncthreads();
 }
 
-__host__ __device__ constexpr int ilog2(int p) { return p <= 1 ? 0 : 1 + ilog2(p / 2); }
-
 // one Schwarz step from zero, the residual and the restriction on level
 // l = log2(P)
 template <int MODE, int P>
 __device__ __forceinline__ void level_down(const LowCycle& c, unsigned char* smem) {
-  constexpr int l = ilog2(P);
+  constexpr int l = ilog2_c(P);
   const LowLevel& L = c.lev[l];
   const int nsub = L.x.n * L.y.n;
   const int warp = threadIdx.x >> 5;
@@ -87,7 +85,7 @@ __device__ __forceinline__ void level_down(const LowCycle& c, unsigned char* sme
 // u_l += I_l u_{l-1} on level l = log2(P)
 template <int P>
 __device__ __forceinline__ void level_up(const LowCycle& c, unsigned char* smem) {
-  constexpr int l = ilog2(P);
+  constexpr int l = ilog2_c(P);
   const LowLevel& L = c.lev[l];
   const LowLevel& C = c.lev[l - 1];
   constexpr int TE = TT<P>::TE;

@@ -57,6 +57,17 @@ __global__ void __launch_bounds__(256, 8) k_prolong_dot(DirView<T> fx, DirView<T
   prolong_tile<T, double, PF, true>(fx, fy, cx, cy, J, uc, in, out, blockIdx.x, blockIdx.y, smem_raw, &dot);
 }
 
+// the up-leg of the V-cycle in one launch (prolong_chain_tile)
+template <typename T, int PF, bool DOT>
+__global__ void __launch_bounds__(kChainThreads, 8) k_prolong_chain(ProlongChain<T> c, DirView<T> fx, DirView<T> fy,
+                                                                 const T* __restrict__ J, const T* in, double* out,
+                                                                 PcgDot dot) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  prolong_chain_tile<T, double, PF, DOT>(c.x, c.y, c.u, c.J, fx, fy, J, in, out, blockIdx.x, blockIdx.y, smem_raw,
+                                         &dot);
+}
+
 // Coarse solve as four small FP64 products over the unknowns (F: nuy x nux):
 //   T1 = S_y^T (F - mu),  T2 = (T1 S_x) ./ (lam_y + lam_x^T),  T3 = S_y T2,
 //   U  = T3 S_x^T - mean(U)
@@ -223,6 +234,27 @@ cudaError_t prolong_dot_p(const DirView<T>& fx, const DirView<T>& fy, const DirV
   return cudaGetLastError();
 }
 
+template <typename T, int PF, bool DOT>
+cudaError_t prolong_chain_p(const ProlongChain<T>& c, const DirView<T>& fx, const DirView<T>& fy, const T* J,
+                            const T* in, double* out, const PcgDot& dot, cudaStream_t s) {
+  using G = ChainGeo<PF>;
+  const size_t sm = prolong_chain_smem<T, PF>();
+  cudaError_t e = allow_smem(k_prolong_chain<T, PF, DOT>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((fx.n + G::TE - 1) / G::TE, (fy.n + G::TE - 1) / G::TE);
+  if (DOT && 2L * grid.x * grid.y > kMaxPartials) return cudaErrorInvalidConfiguration;
+  e = launch_pdl(k_prolong_chain<T, PF, DOT>, grid, dim3(kChainThreads), sm, s, c, fx, fy, J, in, out, dot);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <typename T, int PF>
+cudaError_t prolong_chain_d(const ProlongChain<T>& c, const DirView<T>& fx, const DirView<T>& fy, const T* J,
+                            const T* in, double* out, const PcgDot* dot, cudaStream_t s) {
+  if (dot) return prolong_chain_p<T, PF, true>(c, fx, fy, J, in, out, *dot, s);
+  return prolong_chain_p<T, PF, false>(c, fx, fy, J, in, out, PcgDot{}, s);
+}
+
 template <int PF>
 long prolong_ctas_p(int nx, int ny) {
   constexpr int TE = TT<PF>::TE;
@@ -261,6 +293,24 @@ template cudaError_t launch_prolong_dot<float>(const DirView<float>&, const DirV
 template cudaError_t launch_prolong_dot<double>(const DirView<double>&, const DirView<double>&,
                                                 const DirView<double>&, const DirView<double>&, const double*,
                                                 const double*, const double*, double*, const PcgDot&, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_prolong_chain(const ProlongChain<T>& c, const DirView<T>& fx, const DirView<T>& fy, const T* J,
+                                 const T* in, double* out, const PcgDot* dot, cudaStream_t s) {
+  switch (fx.p) {
+    case 4: return prolong_chain_d<T, 4>(c, fx, fy, J, in, out, dot, s);
+    case 8: return prolong_chain_d<T, 8>(c, fx, fy, J, in, out, dot, s);
+    case 16: return prolong_chain_d<T, 16>(c, fx, fy, J, in, out, dot, s);
+    case 32: return prolong_chain_d<T, 32>(c, fx, fy, J, in, out, dot, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_prolong_chain<float>(const ProlongChain<float>&, const DirView<float>&,
+                                                 const DirView<float>&, const float*, const float*, double*,
+                                                 const PcgDot*, cudaStream_t);
+template cudaError_t launch_prolong_chain<double>(const ProlongChain<double>&, const DirView<double>&,
+                                                  const DirView<double>&, const double*, const double*, double*,
+                                                  const PcgDot*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_restrict(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx, const DirView<T>& cy,

@@ -14,6 +14,7 @@ constexpr int kMaxPartials = 1 << 17;
 // 32 x 32 owned nodes for P >= 16, 16 x 16 for P <= 8 (the lower levels are
 // small and latency-bound: more, smaller CTAs).
 __host__ __device__ constexpr int tile_elems(int P) { return P >= 32 ? 1 : (P <= 8 ? 16 / P : 32 / P); }
+__host__ __device__ constexpr int ilog2_c(int p) { return p <= 1 ? 0 : 1 + ilog2_c(p / 2); }
 
 // ---- sum-factorised operator (Eq. (system matrix)), k_operator.cu --------
 // The MGCG direction update of Alg. 4 fused into the FP64 operator: the
@@ -211,6 +212,25 @@ template <typename T>
 cudaError_t launch_prolong_dot(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
                                const DirView<T>& cy, const T* J, const T* uc, const T* in, double* out,
                                const PcgDot& dot, cudaStream_t s);
+
+// The up-leg of the V-cycle without post-smoothing (Alg. 3) in one launch:
+// u_l + I_l u_{l-1} for l = 1 .. L-1 (u_0 the coarse solution), then
+// out = in + I_L u_{L-1} on the finest level L (order fx.p = 2^L, table J),
+// with the z.q, z.r and beta of *dot when dot != nullptr.  Each CTA carries
+// its tile of elements through the levels in shared memory (the mesh is the
+// same on every level); u_1 .. u_{L-1} are read, not written.  Results are
+// those of the level-by-level launches, bit for bit.  fx.p in {4, 8, 16, 32}.
+constexpr int kChainLevels = 6;    // levels 0 .. 5 (orders 1 .. 32)
+constexpr int kChainThreads = 256;
+template <typename T>
+struct ProlongChain {
+  DirView<T> x[kChainLevels], y[kChainLevels];  // level l: order 2^l
+  const T* u[kChainLevels];                      // u_0 .. u_{L-1}
+  const T* J[kChainLevels];                      // J[l]: order 2^(l-1) -> 2^l (l >= 1)
+};
+template <typename T>
+cudaError_t launch_prolong_chain(const ProlongChain<T>& c, const DirView<T>& fx, const DirView<T>& fy, const T* J,
+                                 const T* in, double* out, const PcgDot* dot, cudaStream_t s);
 
 int elementwise_grid(long n);
 // CTAs per problem of the batched vector kernels (grid = (chunks, nb))

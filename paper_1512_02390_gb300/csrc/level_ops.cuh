@@ -380,29 +380,19 @@ __device__ __forceinline__ void restrict_tile(const DirView<T>& fx, const DirVie
 // DOT (TOut double): also the z.q and z.r partials of the written values z,
 // per problem, and, in the last CTA, beta and delta (PcgDot); every CTA of
 // the launch runs it.
-template <typename T, typename TOut, int PF, bool DOT = false>
-__device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
-                                             const DirView<T>& cy, const T* __restrict__ J,
-                                             const T* __restrict__ uc, const T* in, TOut* out, int bx, int by,
-                                             unsigned char* smem_raw, const PcgDot* dot = nullptr) {
+// The part of prolong_tile after the staging: sc holds the tile's coarse
+// values (LC x LCP), sJ the table, st is scratch (LC x TP).
+template <typename T, typename TOut, int PF, bool DOT>
+__device__ __forceinline__ void prolong_finish(const DirView<T>& fx, const DirView<T>& fy, const T* sc, T* st,
+                                               const T* sJ, const T* in, TOut* out, int bx, int by,
+                                               const PcgDot* dot) {
   using Q = TT<PF>;
   constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
   constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
-  T* sc = reinterpret_cast<T*>(smem_raw);  // LC x LCP coarse values
-  T* st = sc + LC * LCP;                    // LC x TP  x-interpolated
-  T* sJ = st + LC * TP;
   const int E0x = bx * TE, E0y = by * TE;
   const bool lastx = E0x + TE >= fx.n, lasty = E0y + TE >= fy.n;
   const int ownx = min(TE, fx.n - E0x) * PF + ((!fx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, fy.n - E0y) * PF + ((!fy.periodic && lasty) ? 1 : 0);
-  for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
-    const int ly = idx / LC, lx = idx - ly * LC;
-    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
-    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic, cy.segN);
-    sc[ly * LCP + lx] = (gx >= 0 && gy >= 0) ? uc[(long)gy * cx.N + gx] : T(0);
-  }
-  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
-  __syncthreads();
   for (int idx = threadIdx.x; idx < LC * ownx; idx += blockDim.x) {
     const int ly = idx / ownx, ix = idx - ly * ownx;
     const int le = ix / PF, i = ix - le * PF;
@@ -456,6 +446,196 @@ __device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView
     __threadfence();
     pcg_beta_finish(dot->part, G, dot->st, sred);
   }
+}
+
+template <typename T, typename TOut, int PF, bool DOT = false>
+__device__ __forceinline__ void prolong_tile(const DirView<T>& fx, const DirView<T>& fy, const DirView<T>& cx,
+                                             const DirView<T>& cy, const T* __restrict__ J,
+                                             const T* __restrict__ uc, const T* in, TOut* out, int bx, int by,
+                                             unsigned char* smem_raw, const PcgDot* dot = nullptr) {
+  using Q = TT<PF>;
+  constexpr int PC = Q::PC, TE = Q::TE, TNF = Q::TNF, TNC = Q::TNC, NPC = Q::NPC;
+  constexpr int LC = TNC + 1, LCP = LC + 1, TP = TNF + 2;
+  T* sc = reinterpret_cast<T*>(smem_raw);  // LC x LCP coarse values
+  T* st = sc + LC * LCP;                    // LC x TP  x-interpolated
+  T* sJ = st + LC * TP;
+  const int E0x = bx * TE, E0y = by * TE;
+  for (int idx = threadIdx.x; idx < LC * LC; idx += blockDim.x) {
+    const int ly = idx / LC, lx = idx - ly * LC;
+    const int gx = node_or_wall(E0x * PC + lx, cx.N, cx.periodic, cx.segN);
+    const int gy = node_or_wall(E0y * PC + ly, cy.N, cy.periodic, cy.segN);
+    sc[ly * LCP + lx] = (gx >= 0 && gy >= 0) ? uc[(long)gy * cx.N + gx] : T(0);
+  }
+  for (int idx = threadIdx.x; idx < (PF + 1) * NPC; idx += blockDim.x) sJ[idx] = J[idx];
+  __syncthreads();
+  prolong_finish<T, TOut, PF, DOT>(fx, fy, sc, st, sJ, in, out, bx, by, dot);
+}
+
+// ---- the up-leg of the V-cycle in one pass ------------------------------------
+// Without post-smoothing the up-leg of Alg. 3 is u_l <- u_l + I_l u_{l-1},
+// l = 1 .. L, with u_0 the coarse solution.  Every level has the same element
+// mesh (only the order p_l = 2^l changes) and I_l acts element by element, so
+// a CTA can carry its tile of TE x TE elements (TE of the finest level) from
+// level 0 up to level L in shared memory.  Level l < L needs all
+// (TE p_l + 1)^2 nodes of the tile, the ones it shares with the next tile
+// included: such a node is interpolated from this tile's element, through the
+// end rows of J, which are exactly 0 and 1 (the GLL end points of both orders
+// are -1 and 1), so it gets the value the owning tile computes.  Per node the
+// arithmetic is that of prolong_tile, in the same order; results are identical
+// to the level-by-level launches.
+
+// level of order P in the chain: (TE P + 1)^2 nodes, row pitch TE P + 2
+__host__ __device__ constexpr int chain_nodes(int te, int P) { return te * P + 1; }
+// offset of the level of order P among the node buffers of orders 1, 2, .. P / 2
+__host__ __device__ constexpr int chain_voff(int te, int P) {
+  return P <= 1 ? 0 : chain_voff(te, P / 2) + chain_nodes(te, P / 2) * (chain_nodes(te, P / 2) + 1);
+}
+// flat index of the first staged node of the level of order P
+__host__ __device__ constexpr int chain_soff(int te, int P) {
+  return P <= 1 ? 0 : chain_soff(te, P / 2) + chain_nodes(te, P / 2) * chain_nodes(te, P / 2);
+}
+// offset of the table of order P / 2 -> P among those of orders 2, 4, .. P / 2
+__host__ __device__ constexpr int chain_joff(int P) { return P <= 2 ? 0 : chain_joff(P / 2) + (P / 2 + 1) * (P / 4 + 1); }
+
+template <int PF>
+struct ChainGeo {
+  static constexpr int TE = tile_elems(PF);
+  static constexpr int V = chain_voff(TE, PF);                   // node buffers of orders 1 .. PF / 2
+  static constexpr int NS = chain_soff(TE, PF);                  // staged nodes
+  static constexpr int J = chain_joff(PF) + (PF + 1) * (PF / 2 + 1);  // tables of orders 2 .. PF
+  static constexpr int ST = chain_nodes(TE, PF / 2) * (TE * PF + 2);  // x-interpolated rows (largest step)
+};
+
+template <typename T, int PF>
+constexpr size_t prolong_chain_smem() {
+  using G = ChainGeo<PF>;
+  return sizeof(T) * (G::V + G::ST + G::J);
+}
+
+// shared-memory offset and global address of staged node q (flat over the
+// levels of orders P, 2 P, .. PF / 2); addr = nullptr: wall (value 0)
+template <typename T, int P, int PF>
+__device__ __forceinline__ void chain_locate(const DirView<T>* cx, const DirView<T>* cy, const T* const* cu, int q,
+                                             int E0x, int E0y, int& off, const T*& addr) {
+  constexpr int TE = ChainGeo<PF>::TE, n = chain_nodes(TE, P);
+  if constexpr (P < PF) {
+    if (q < n * n) {
+      constexpr int l = ilog2_c(P);
+      const int ly = q / n, lx = q - ly * n;
+      const DirView<T>& x = cx[l];
+      const DirView<T>& y = cy[l];
+      const int gx = node_or_wall(E0x * P + lx, x.N, x.periodic, x.segN);
+      const int gy = node_or_wall(E0y * P + ly, y.N, y.periodic, y.segN);
+      off = chain_voff(TE, P) + ly * (n + 1) + lx;
+      addr = (gx >= 0 && gy >= 0) ? cu[l] + (long)gy * x.N + gx : nullptr;
+      return;
+    }
+    chain_locate<T, 2 * P, PF>(cx, cy, cu, q - n * n, E0x, E0y, off, addr);
+  }
+}
+
+// shared-memory offset (from the first table) and global address of entry q
+// of the tables of orders P / 2 -> P, P -> 2 P, .. PF / 2 -> PF
+template <typename T, int P, int PF>
+__device__ __forceinline__ void chain_locate_J(const T* const* cJ, const T* J, int q, int& off, const T*& addr) {
+  constexpr int n = (P + 1) * (P / 2 + 1);
+  if constexpr (P == PF) {
+    off = chain_joff(P) + q;
+    addr = J + q;
+  } else {
+    if (q < n) {
+      off = chain_joff(P) + q;
+      addr = cJ[ilog2_c(P)] + q;
+      return;
+    }
+    chain_locate_J<T, 2 * P, PF>(cJ, J, q - n, off, addr);
+  }
+}
+
+// level of order P from the level below (vc) into vf, which holds u of the
+// level on entry: vf <- vf + I vc on all (TE P + 1)^2 nodes of the tile
+template <typename T, int P, int TE>
+__device__ __forceinline__ void chain_step(const T* vc, T* vf, T* st, const T* sJ, const DirView<T>& fx,
+                                           const DirView<T>& fy, int E0x, int E0y) {
+  constexpr int PC = P / 2, NPC = PC + 1, LC = TE * PC + 1, LCP = LC + 1, LF = TE * P + 1, LFP = LF + 1;
+  constexpr int TP = TE * P + 2;
+  for (int idx = threadIdx.x; idx < LC * LF; idx += blockDim.x) {
+    const int ly = idx / LF, ix = idx - ly * LF;
+    const int le = min(ix / P, TE - 1), i = ix - le * P;
+    const T* row = vc + ly * LCP + le * PC;
+    T t = T(0);
+#pragma unroll
+    for (int k = 0; k < NPC; ++k) t += sJ[i * NPC + k] * row[k];
+    st[ly * TP + ix] = t;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < LF * LF; idx += blockDim.x) {
+    const int jy = idx / LF, ix = idx - jy * LF;
+    const int le = min(jy / P, TE - 1), j = jy - le * P;
+    const bool wall = wall_node(E0x * P + ix, fx.N, fx.periodic, fx.segN) ||
+                      wall_node(E0y * P + jy, fy.N, fy.periodic, fy.segN);
+    const T* col = st + (le * PC) * TP + ix;
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < NPC; ++k) v += sJ[j * NPC + k] * col[k * TP];
+    T* o = vf + jy * LFP + ix;
+    *o = wall ? T(0) : T(*o + v);
+  }
+  __syncthreads();
+}
+
+template <typename T, int P, int PF>
+__device__ __forceinline__ void chain_up(const DirView<T>* cx, const DirView<T>* cy, T* sv, T* st, const T* sJ,
+                                         int E0x, int E0y) {
+  constexpr int TE = ChainGeo<PF>::TE;
+  if constexpr (P < PF) {
+    constexpr int l = ilog2_c(P);
+    chain_step<T, P, TE>(sv + chain_voff(TE, P / 2), sv + chain_voff(TE, P), st, sJ + chain_joff(P), cx[l], cy[l],
+                         E0x, E0y);
+    chain_up<T, 2 * P, PF>(cx, cy, sv, st, sJ, E0x, E0y);
+  }
+}
+
+// One tile (bx, by) of the finest level (order PF >= 4): levels 1 .. L-1 in
+// shared memory, then out = in + I_L u_{L-1} as prolong_tile (with the dot
+// products when DOT).  cx, cy, cu, cJ: views, vectors and tables of levels
+// 0 .. L-1 (cJ[0] unused); J the finest level's table.
+template <typename T, typename TOut, int PF, bool DOT>
+__device__ __forceinline__ void prolong_chain_tile(const DirView<T>* cx, const DirView<T>* cy, const T* const* cu,
+                                                   const T* const* cJ, const DirView<T>& fx, const DirView<T>& fy,
+                                                   const T* __restrict__ J, const T* in, TOut* out, int bx, int by,
+                                                   unsigned char* smem_raw, const PcgDot* dot) {
+  using G = ChainGeo<PF>;
+  constexpr int TE = G::TE, NS = G::NS;
+  constexpr int PER = (NS + G::J + kChainThreads - 1) / kChainThreads;
+  T* sv = reinterpret_cast<T*>(smem_raw);  // node buffers of orders 1 .. PF / 2
+  T* st = sv + G::V;
+  T* sJ = st + G::ST;                       // tables of orders 2 .. PF
+  const int E0x = bx * TE, E0y = by * TE;
+  // every level's nodes of the tile and every table: all loads first, then
+  // the stores (one memory latency)
+  T val[PER];
+  int off[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int q = threadIdx.x + k * kChainThreads;
+    const T* addr = nullptr;
+    off[k] = -1;
+    if (q < NS) {
+      chain_locate<T, 1, PF>(cx, cy, cu, q, E0x, E0y, off[k], addr);
+    } else if (q < NS + G::J) {
+      chain_locate_J<T, 2, PF>(cJ, J, q - NS, off[k], addr);
+      off[k] += G::V + G::ST;
+    }
+    val[k] = addr ? *addr : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k)
+    if (off[k] >= 0) sv[off[k]] = val[k];
+  __syncthreads();
+  chain_up<T, 2, PF>(cx, cy, sv, st, sJ, E0x, E0y);
+  prolong_finish<T, TOut, PF, DOT>(fx, fy, sv + chain_voff(TE, PF / 2), st, sJ + chain_joff(PF), in, out, bx, by,
+                                   dot);
 }
 
 template <typename T, int PF>

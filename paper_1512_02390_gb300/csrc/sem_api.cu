@@ -88,6 +88,8 @@ struct sem_handle {
   // levels p_l <= 8 and the coarse solve in one persistent kernel (mixed modes)
   bool low_ok = false, low_on = false;
   LowCycle lowc{};
+  // the up-leg of the V-cycle in one launch (no post-smoothing, p >= 4)
+  bool chain_ok = false, chain_on = true;
   // the whole MGCG solve as one CUDA graph: prologue + WHILE node over one iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -244,6 +246,18 @@ const DirView<T>& DY(const Level& l) {
 template <typename T>
 const T* JL(const Level& l) {
   if constexpr (std::is_same<T, double>::value) return l.J64; else return l.J32;
+}
+// views, vectors and tables of levels 0 .. L-1 for the fused up-leg
+template <typename T>
+ProlongChain<T> chain_view(const sem_handle* h) {
+  ProlongChain<T> c{};
+  for (int l = 0; l < h->L && l < kChainLevels; ++l) {
+    c.x[l] = DX<T>(h->lev[l]);
+    c.y[l] = DY<T>(h->lev[l]);
+    c.u[l] = static_cast<const T*>(h->lev[l].u);
+    c.J[l] = l > 0 ? JL<T>(h->lev[l]) : nullptr;
+  }
+  return c;
 }
 template <typename T>
 const VarView<T>& VV(const Level& l) {
@@ -430,10 +444,22 @@ int vcycle_z(sem_handle* h, const double* rtop, double* zout, cudaStream_t s, bo
         launch_coarse<T>(h->coarse, static_cast<const T*>(lv[0].f), static_cast<T*>(lv[0].u), s));
   }
   bool z_written = dbl;
+  // without post-smoothing the finest level's launch carries the whole up-leg
+  const bool chain = low == 0 && h->chain_ok && h->chain_on;
   for (int l = low + 1; l <= L; ++l) {
     h->cur_level = l;
+    if (chain && l < L) continue;
     T* ul = (l == L) ? uL : static_cast<T*>(lv[l].u);
     const T* uc = static_cast<const T*>(lv[l - 1].u);
+    if (chain) {
+      const bool with_dot = dot && dot->gyp > 0;
+      KL(h, SEM_K_PROLONG, s,
+         (launch_prolong_chain<T>(chain_view<T>(h), DX<T>(lv[L]), DY<T>(lv[L]), JL<T>(lv[L]), ul, zout,
+                                  with_dot ? dot : nullptr, s)));
+      z_written = true;
+      if (with_dot) *dotted = true;
+      continue;
+    }
     if (dot && l == L && h->ns2[l] == 0 && dot->gyp > 0) {
       // z = (dbl: ul +) I uc, with the dot products
       KL(h, SEM_K_PROLONG, s,
@@ -1129,6 +1155,8 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     h->ns1[l] = c.ns1 * f;
     h->ns2[l] = c.ns2 * f;
   }
+  h->chain_ok = L >= 2 && L < kChainLevels;
+  for (int l = 1; l <= L; ++l) h->chain_ok = h->chain_ok && h->ns2[l] == 0;
   int rc = SEM_OK;
   auto bail = [&](int code) {
     sem_destroy(h);
@@ -1634,6 +1662,25 @@ int sem_set_low_cycle(sem_handle* h, int32_t enable) {
   CK(cudaDeviceSynchronize());
   h->low_on = enable != 0;
   drop_graph(h);
+  return SEM_OK;
+}
+
+int sem_set_fused_prolongation(sem_handle* h, int32_t enable) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (enable != 0 && enable != 1) return fail(SEM_BAD_ARG, "enable must be 0 or 1");
+  if (enable && !h->chain_ok) return fail(SEM_BAD_ARG, "no fused prolongation for this configuration");
+  CK(cudaDeviceSynchronize());
+  h->chain_on = enable != 0;
+  drop_graph(h);
+  return SEM_OK;
+}
+
+int sem_get_fused_prolongation(const sem_handle* h, int32_t* available, int32_t* enabled) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (available) *available = h->chain_ok ? 1 : 0;
+  if (enabled) *enabled = (h->chain_ok && h->chain_on) ? 1 : 0;
   return SEM_OK;
 }
 

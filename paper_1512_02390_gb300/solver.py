@@ -128,6 +128,13 @@ class Solver:
         """(available, enabled) of the persistent low-level cycle."""
         return B.sem_get_low_cycle(self.h)
 
+    def set_fused_prolongation(self, enable):
+        B.sem_set_fused_prolongation(self.h, enable)
+
+    def fused_prolongation(self):
+        """(available, enabled) of the one-launch up-leg of the V-cycle."""
+        return B.sem_get_fused_prolongation(self.h)
+
     def set_tune_from(self, other):
         """Copy the launch shapes of a handle with the same levels."""
         for l in range(1, self.levels + 1):
@@ -254,6 +261,9 @@ def main(argv=None):
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--trace", action="store_true")
     ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="with --tune: read the launch shapes from this JSON-lines cache, timing and "
+                         "appending only the missing ones")
     ap.add_argument("--set-tune", action="append", default=[])
     ap.add_argument("--batch", type=int, default=0,
                     help="solve the first N problems of the seeded batched workload instead (one batch "
@@ -269,7 +279,7 @@ def main(argv=None):
                                       "nodes": v * (k[0] * k[1] + 1) ** 2} for k, v in sorted(shapes.items())]}))
         Bt = Batch(cfgs)
         if a.tune:
-            Bt.autotune()
+            Bt.autotune(a.tune_cache)
         us, fs = [], []
         for k, c in enumerate(cfgs):
             n = c["nx"] * c["p"] + 1
@@ -291,7 +301,7 @@ def main(argv=None):
         return
     S = Solver(nx=a.nx, ny=a.ny, p=a.p, overlap=a.overlap, precision=a.precision, tol=a.tol, i_max=500)
     if a.tune:
-        S.autotune()
+        S.autotune(a.tune_cache)
     for spec in a.set_tune:
         lvl, fuse, spw, tc = (int(x) for x in spec.split(":"))
         S.set_tune(lvl, fuse, spw, tc)
