@@ -35,7 +35,8 @@ EXPORTS = [
     "sem_learned_features", "sem_mlp_load", "sem_mlp_forward", "sem_mlp_workspace_bytes", "sem_mlp_loss_grad", "sem_mlp_train",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_info", "sem_batch_solve", "sem_batch_launches",
     "sem_autotune", "sem_get_tune", "sem_set_tune", "sem_batch_autotune", "sem_set_low_cycle", "sem_get_low_cycle",
-    "sem_set_fused_prolongation", "sem_get_fused_prolongation",
+    "sem_set_fused_prolongation", "sem_get_fused_prolongation", "sem_set_fixed_point_operator",
+    "sem_get_fixed_point_operator",
     "sem_status_string", "sem_last_error",
     "sem3_default_config", "sem3_create", "sem3_destroy", "sem3_sizes", "sem3_coords", "sem3_mass", "sem3_apply",
     "sem3_smooth", "sem3_vcycle", "sem3_pcg_solve",
@@ -149,6 +150,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sem_get_low_cycle": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sem_set_fused_prolongation": (i32, [vp, i32]),
         "sem_get_fused_prolongation": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "sem_set_fixed_point_operator": (i32, [vp, i32]),
+        "sem_get_fixed_point_operator": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "sem3_default_config": (None, [ctypes.POINTER(sem3_config)]),
         "sem3_create": (i32, [ctypes.POINTER(sem3_config), ctypes.POINTER(vp)]),
         "sem3_destroy": (None, [vp]),
@@ -470,6 +473,17 @@ def sem_get_fused_prolongation(h):
     """(available, enabled) of the one-launch up-leg of the V-cycle."""
     a, e = ctypes.c_int32(), ctypes.c_int32()
     _check(load_library().sem_get_fused_prolongation(h, ctypes.byref(a), ctypes.byref(e)))
+    return bool(a.value), bool(e.value)
+
+
+def sem_set_fixed_point_operator(h, enable: bool) -> None:
+    _check(load_library().sem_set_fixed_point_operator(h, int(bool(enable))))
+
+
+def sem_get_fixed_point_operator(h):
+    """(available, enabled) of the FP64 operator in exact integer arithmetic."""
+    a, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().sem_get_fixed_point_operator(h, ctypes.byref(a), ctypes.byref(e)))
     return bool(a.value), bool(e.value)
 
 

@@ -1,0 +1,288 @@
+// The FP64 operator of Eq. (system matrix), A = M_y (x) L_x + L_y (x) M_x,
+// with the element-row products evaluated exactly in integers.
+//
+// The FP64 pipe of this part issues about 2 FMA lanes per clock per SM; a
+// 32 x 32 -> 64-bit integer multiply-add (mad.wide.s32) issues about 56.  The
+// directional products y_a = sum_k L[a][k] x_k of the node-centric operator
+// (the even-odd form of k_operator.cu) therefore run here on the integer pipe,
+// as an error-free splitting of both operands (the idea of Ozaki, Ogita and
+// Oishi's exact matrix products, with 64-bit integer instead of floating-point
+// accumulation):
+//   - the staged tile of u, x = X 2^-s with X an integer, |X| < 2^53: the tile's
+//     largest exponent keeps all 53 mantissa bits, smaller values are rounded
+//     to the same absolute step (2^-53 of the tile's bound);
+//   - the element matrix, L = L_int 2^-t with |L_int| < 2^73 (per element and
+//     direction, built on the host: setup.cpp fx_tables), exact for the GLL
+//     stiffness matrices (their entries span at most 20 binary exponents);
+//   - e_k = X_k + X_{p-k}, o_k = X_k - X_{p-k}, E = L_int[a][k] + L_int[a][p-k],
+//     O = L_int[a][k] - L_int[a][p-k] are exact integers; with the limbs
+//     e = e1 2^25 + e0 (e0 in [0, 2^25), |e1| < 2^29) and E = E2 2^50 + E1 2^25
+//     + E0 (E0, E1 in [0, 2^25), |E2| < 2^24) every limb product is below 2^54
+//     and goes to the int64 accumulator of its weight (2^0, 2^25, 2^50, 2^75);
+//     the even and odd sums together have p + 1 <= 33 terms, two products per
+//     weight and term, so each accumulator stays below 2^60: no sum rounds or
+//     overflows;
+//   - 2 y_a = YE + YO and 2 y_{p-a} = YE - YO are carry-normalised to
+//     C3 2^75 + R (R in [0, 2^75)) and rounded to FP64 once (nearest, ties to
+//     even).
+// A node's value is then My[j] y_x + Mx[i] y_y in FP64, as in the other forms.
+// The only roundings are the fixed-point step of x (2^-53 of the tile's
+// largest |x|) and the final ones; the even-odd folding itself is exact,
+// unlike its FP64 form.  The element tables (16 bytes per entry) are read with
+// warp-uniform loads, which the L1 cache serves.
+#include <algorithm>
+
+#include "fx_exact.h"
+#include "kernels.h"
+#include "level_ops.cuh"
+
+namespace sem {
+
+namespace {
+
+template <int P>
+struct FxTile {
+  static constexpr int H = P / 2;
+  static constexpr int TE = Tile<P>::TE, TN = Tile<P>::TN, LN = Tile<P>::LN, NP = P + 1;
+  static constexpr int LP = LN | 1;
+  static constexpr int NE = (H + 1) * (H + 1), NO = H * H, EO = NE + NO;
+  static constexpr int NV = 2 * H + 1;  // e_0..e_H, o_0..o_{H-1}
+  static constexpr int NW = 256 / 32;
+};
+
+template <int P>
+size_t apply_fx_smem() {
+  using Q = FxTile<P>;
+  const size_t eight = (size_t)Q::LN * Q::LP                // staged tile (double, then int64)
+                       + (size_t)(Q::TE + 1) * Q::NV * Q::TN  // e/o limb pairs of one direction
+                       + (size_t)Q::TN * (Q::TE + 1) * Q::NP  // x products
+                       + 2 * (Q::TN + 1);                    // mass diagonals
+  return 8 * eight + sizeof(double) * kRedThreads + sizeof(int) * Q::NW;
+}
+
+__device__ __forceinline__ int2 fx_pair(long long v) {
+  int lo, hi;
+  fx_limbs(v, lo, hi);
+  return make_int2(lo, hi);
+}
+
+// e/o limb pairs of one direction from the fixed-point tile sx
+template <int P, bool XDIR>
+__device__ __forceinline__ void fx_form_eo(const long long* sx, int2* ev) {
+  using Q = FxTile<P>;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LP = Q::LP, NV = Q::NV;
+  for (int idx = threadIdx.x; idx < (TE + 1) * H * TN; idx += blockDim.x) {
+    const int w = idx % TN;
+    const int q = idx / TN;
+    const int sl = q / H, k = q - sl * H;
+    long long xk, xm;
+    if (XDIR) {
+      const long long* x = sx + (w + P) * LP + sl * P;
+      xk = x[k];
+      xm = x[P - k];
+    } else {
+      const long long* x = sx + (sl * P) * LP + w + P;
+      xk = x[k * LP];
+      xm = x[(P - k) * LP];
+    }
+    ev[(sl * NV + k) * TN + w] = fx_pair(xk + xm);
+    ev[(sl * NV + H + 1 + k) * TN + w] = fx_pair(xk - xm);
+  }
+  for (int idx = threadIdx.x; idx < (TE + 1) * TN; idx += blockDim.x) {
+    const int w = idx % TN, sl = idx / TN;
+    ev[(sl * NV + H) * TN + w] = fx_pair(XDIR ? sx[(w + P) * LP + sl * P + H] : sx[(sl * P + H) * LP + w + P]);
+  }
+}
+
+// element-row products of one direction; item (slot, a, w), slot 0 (the
+// low-side neighbour) only for its y_P.  Slot sl is element e_first + sl (n
+// when it does not exist: the zero table).
+template <int P, bool XDIR>
+__device__ __forceinline__ void fx_products(const FxDir& fd, const DirView<double>& d, int e_first, int emax,
+                                            const int2* ev, double* dst_base) {
+  using Q = FxTile<P>;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, NP = Q::NP, EO = Q::EO, NE = Q::NE, NV = Q::NV;
+  constexpr int XI = TN * (1 + TE * (H + 1));
+  const int4* tab = reinterpret_cast<const int4*>(fd.tab);
+  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
+    const int w = idx % TN;
+    const int q = idx / TN;
+    const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
+    const int a = q == 0 ? 0 : (q - 1) % (H + 1);
+    int el = e_first + sl;
+    if (d.periodic) el = (el + d.n) % d.n;
+    else if (el < 0 || el >= d.n) el = d.n;
+    const int4* E = tab + (long)el * EO + a * (H + 1);
+    const int4* O = tab + (long)el * EO + NE + min(a, H - 1) * H;
+    const int2* e = ev + (sl * NV) * TN + w;
+    const int2* o = ev + (sl * NV + H + 1) * TN + w;
+    long long e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+#pragma unroll
+    for (int k = 0; k <= H; ++k) {
+      const int4 l = __ldg(E + k);
+      const int2 x = e[k * TN];
+      e0 += (long long)x.x * l.x;
+      e1 += (long long)x.x * l.y + (long long)x.y * l.x;
+      e2 += (long long)x.x * l.z + (long long)x.y * l.y;
+      e3 += (long long)x.y * l.z;
+    }
+    long long o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+    if (a < H) {  // uniform across a warp (w = lane)
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int4 l = __ldg(O + k);
+        const int2 x = o[k * TN];
+        o0 += (long long)x.x * l.x;
+        o1 += (long long)x.x * l.y + (long long)x.y * l.x;
+        o2 += (long long)x.x * l.z + (long long)x.y * l.y;
+        o3 += (long long)x.y * l.z;
+      }
+    }
+    // y = (YE +- YO) 2^-(s + t + 1), s = 1075 - emax
+    const int K = 1076 - emax + __ldg(fd.t + el);
+    double* dst = XDIR ? dst_base + (w * (TE + 1) + sl) * NP : dst_base + (sl * NP) * TN + w;
+    constexpr int step = XDIR ? 1 : TN;
+    if (a < H) dst[(P - a) * step] = fx_to_f64(e0 - o0, e1 - o1, e2 - o2, e3 - o3, K);
+    if (sl > 0) dst[a * step] = fx_to_f64(e0 + o0, e1 + o1, e2 + o2, e3 + o3, K);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_apply_fx(DirView<double> dx, DirView<double> dy, FxDir fx, FxDir fy,
+                                                  const double* __restrict__ u, const double* __restrict__ f,
+                                                  double* __restrict__ out, int dot, double* __restrict__ part,
+                                                  PcgFuse pf) {
+  pdl_enter();
+  using Q = FxTile<P>;
+  constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, NV = Q::NV, NW = Q::NW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* su = reinterpret_cast<double*>(smem_raw);  // LN x LP, then the fixed-point tile in place
+  long long* sx = reinterpret_cast<long long*>(su);
+  int2* ev = reinterpret_cast<int2*>(su + LN * LP);   // (TE+1) x NV x TN
+  double* xb = reinterpret_cast<double*>(ev + (TE + 1) * NV * TN);  // [row][slot][a]
+  double* yb = su;                                    // [slot][b][col], over the tile once the y e/o are formed
+  static_assert(TN * (TE + 1) * NP <= LN * LP, "y products must fit in the staged tile");
+  double* sMx = xb + TN * (TE + 1) * NP;
+  double* sMy = sMx + (TN + 1);
+  double* sred = sMy + (TN + 1);
+  int* semax = reinterpret_cast<int*>(sred + kRedThreads);
+
+  const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
+  const int Nx = dx.N, Ny = dy.N;
+  const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
+  const double beta = fused_beta(pf, blockIdx.y, gridDim.y);
+  int emax = 0;  // largest exponent field of the staged values
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
+    const double v = stage_value<P, double>(u, nullptr, dx, dy, pf, beta, gy, gx);
+    su[ly * LP + lx] = v;
+    emax = max(emax, (__double2hiint(v) >> 20) & 0x7ff);
+  }
+  for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
+    const int gx = ex0 * P + idx, gy = ey0 * P + idx;
+    sMx[idx] = gx < Nx ? dx.Mg[gx] : 0.0;
+    sMy[idx] = gy < Ny ? dy.Mg[gy] : 0.0;
+  }
+  emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+  if ((threadIdx.x & 31) == 0) semax[threadIdx.x >> 5] = emax;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < NW; ++w) emax = max(emax, semax[w]);
+  const bool finite = emax < 0x7ff;
+  const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
+  const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
+  const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
+  // the owned staged values (for the dot product) before the tile turns into integers
+  constexpr int KOWN = ((TN + 1) * (TN + 1) + 255) / 256;
+  double own[KOWN];
+#pragma unroll
+  for (int q = 0; q < KOWN; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    own[q] = 0.0;
+    if (idx < ownx * owny) {
+      const int jy = idx / ownx, ix = idx - jy * ownx;
+      own[q] = su[(jy + P) * LP + ix + P];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
+    const int ly = idx / LN, lx = idx - ly * LN;
+    sx[ly * LP + lx] = finite ? fx_of(su[ly * LP + lx], emax) : 0LL;
+  }
+  __syncthreads();
+  fx_form_eo<P, true>(sx, ev);
+  __syncthreads();
+  fx_products<P, true>(fx, dx, ex0 - 1, emax, ev, xb);
+  __syncthreads();
+  fx_form_eo<P, false>(sx, ev);
+  __syncthreads();
+  fx_products<P, false>(fy, dy, ey0 - 1, emax, ev, yb);
+  __syncthreads();
+
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < KOWN; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    if (idx >= ownx * owny) break;
+    const int jy = idx / ownx, ix = idx - jy * ownx;
+    const int gi = ex0 * P + ix, gj = ey0 * P + jy;
+    const long o = (long)gj * Nx + gi;
+    const bool wall = wall_node(gi, Nx, dx.periodic, dx.segN) || wall_node(gj, Ny, dy.periodic, dy.segN);
+    double val = 0.0;
+    if (!wall) {
+      const int lex = ix / P, a = ix - lex * P;
+      const int ley = jy / P, b = jy - ley * P;
+      const double* xr = xb + (jy * (TE + 1) + lex + 1) * NP;
+      double xs = xr[a];
+      if (a == 0) xs += xr[P - NP];  // y_P of the left slot
+      const double* yc = yb + ((ley + 1) * NP) * TN + ix;
+      double ys = yc[b * TN];
+      if (b == 0) ys += yc[(P - NP) * TN];
+      val = sMy[jy] * xs + sMx[ix] * ys;
+      if (!finite) val = __longlong_as_double(0x7FF8000000000000LL);
+      if (f) val = f[o] - val;
+    }
+    out[o] = val;
+    if (dot == 1) acc += own[q] * val;
+    else if (dot == 2) acc += val * val;
+  }
+  if (dot) {
+    const double s = block_sum_w0(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <int P>
+cudaError_t apply_fx_p(const DirView<double>& dx, const DirView<double>& dy, const FxDir& fx, const FxDir& fy,
+                       const double* u, const double* f, double* out, int dot, double* part, int* nparts,
+                       cudaStream_t s, const PcgFuse& pf) {
+  using Q = FxTile<P>;
+  dim3 grid((dx.n + Q::TE - 1) / Q::TE, (dy.n + Q::TE - 1) / Q::TE);
+  if (dot && (int)(grid.x * grid.y) > kMaxPartials) return cudaErrorInvalidConfiguration;
+  if (nparts) *nparts = grid.x * grid.y;
+  const size_t sm = apply_fx_smem<P>();
+  cudaError_t e = allow_smem(k_apply_fx<P>, sm);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(k_apply_fx<P>, grid, dim3(256), sm, s, dx, dy, fx, fy, u, f, out, dot, part, pf);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_apply_fx(const DirView<double>& dx, const DirView<double>& dy, const FxDir& fx,
+                            const FxDir& fy, const double* u, const double* f, double* out, int dot, double* part,
+                            int* nparts, cudaStream_t s, PcgFuse pf) {
+  if (!fx.tab || !fx.t || !fy.tab || !fy.t || dx.p != dy.p) return cudaErrorInvalidValue;
+  switch (dx.p) {
+    case 4: return apply_fx_p<4>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);
+    case 8: return apply_fx_p<8>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);
+    case 16: return apply_fx_p<16>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);
+    case 32: return apply_fx_p<32>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sem

@@ -40,6 +40,29 @@ cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u,
                          T* out, int dot, double* part, int* nparts, cudaStream_t s, const T* E = nullptr,
                          T* uout = nullptr, PcgFuse pf = PcgFuse(), int eo = -1);
 
+// The FP64 operator of Eq. (system matrix) evaluated exactly in integer
+// arithmetic (an error-free splitting in the manner of Ozaki et al.): each CTA
+// writes its staged tile of u as 53-bit fixed point (one power-of-two scale per
+// tile); the element matrices come as exact fixed-point integers (one scale per
+// element and direction); the even-odd products (E = L[a][k] + L[a][p-k],
+// O = L[a][k] - L[a][p-k], exact in integers) are accumulated exactly in
+// 64-bit integers (6 mad.wide.s32 per term, on the integer pipe), and each
+// directional sum sum_k L[i][k] u_k is rounded to FP64 once.  FxDir holds, per
+// element and direction, the tables of setup.h fx_tables: E[a][k],
+// a, k = 0..p/2 (entry k = p/2: 2 L[a][p/2]), then O[a][k], a, k < p/2, each
+// entry four ints (l0, l1, l2, 0) = l2 2^50 + l1 2^25 + l0; element n is all
+// zero (missing neighbours).
+struct FxDir {
+  const int* tab;   // (n + 1) x ((p/2+1)^2 + (p/2)^2) x 4
+  const int* t;     // n + 1: L_int = L * 2^t[e]
+};
+// out = A u (f == nullptr) or f - A u, FP64 (p in {4, 8, 16, 32}); dot and pf
+// as for launch_apply (no fused scatter).  A tile holding a non-finite value
+// writes NaN on its nodes.
+cudaError_t launch_apply_fx(const DirView<double>& dx, const DirView<double>& dy, const FxDir& fx,
+                            const FxDir& fy, const double* u, const double* f, double* out, int dot, double* part,
+                            int* nparts, cudaStream_t s, PcgFuse pf = PcgFuse());
+
 // Variable-diffusivity operator B(nu) (Sec. 4.3): element data of one level.
 template <typename T>
 struct VarView {

@@ -58,6 +58,7 @@ struct Level {
   void* E = nullptr;      // element-blocked Schwarz corrections
   TuneVal tune{};         // launch shapes (autotuner): fused scatter, sweep kernel and grid
   TcWork tc{};            // stacks of the tcgen05 sweep (ngroups == 0: not available)
+  FxDir fxx{}, fxy{};     // fixed-point even-odd tables (finest level; FP64 operator in integers)
 };
 
 }  // namespace
@@ -90,6 +91,8 @@ struct sem_handle {
   LowCycle lowc{};
   // the up-leg of the V-cycle in one launch (no post-smoothing, p >= 4)
   bool chain_ok = false, chain_on = true;
+  // the FP64 operator evaluated exactly in integers (Poisson operator, p >= 4)
+  bool fx_ok = false, fx_on = true;
   // the whole MGCG solve as one CUDA graph: prologue + WHILE node over one iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -502,14 +505,24 @@ int precond(sem_handle* h, const double* r, double* z, cudaStream_t s, bool r32_
 const Level& top(const sem_handle* h) { return h->lev[h->L]; }
 
 // The FP64 operator of the outer iteration: it defines the discrete problem.
-// In FP64 mode it applies the element matrices as stored (eo = 0): the
-// even-odd form folds them into (L_ak +- L_a,p-k) / 2, whose roundings move
-// the coefficients by up to half an ulp, and the exact discrete solution with
-// them (by about 1e-11 relative at 64 x 64 elements, p = 16).  The mixed
-// modes, whose solution bar is 1e-9, keep the even-odd form.
+// Where the fixed-point tables exist (Poisson operator, p >= 4) it runs in
+// exact integer arithmetic (launch_apply_fx): the even-odd folding is exact
+// there and the products are rounded once.  Otherwise, in FP64 mode, it
+// applies the element matrices as stored (eo = 0): the FP64 even-odd form folds
+// them into (L_ak +- L_a,p-k) / 2, whose roundings move the coefficients by up
+// to half an ulp, and the exact discrete solution with them (by about 1e-11
+// relative at 64 x 64 elements, p = 16); the mixed modes, whose solution bar
+// is 1e-9, keep that form.
 int apply64(sem_handle* h, const double* u, const double* f, double* out, int dot, int* np, cudaStream_t s,
             double* part = nullptr, PcgFuse pf = PcgFuse()) {
-  return level_apply<double>(h, top(h), SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s, nullptr,
+  const Level& t = top(h);
+  if (h->fx_ok && h->fx_on) {
+    KL(h, SEM_K_APPLY_FP64, s,
+       launch_apply_fx(DX<double>(t), DY<double>(t), t.fxx, t.fxy, u, f, out, dot, part ? part : h->part, np, s,
+                       pf));
+    return SEM_OK;
+  }
+  return level_apply<double>(h, t, SEM_K_APPLY_FP64, u, f, out, dot, part ? part : h->part, np, s, nullptr,
                              nullptr, pf, h->mixed ? -2 : 0);
 }
 
@@ -1196,6 +1209,16 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     if (l == L) {
       h->xc = dx.coords;
       h->yc = dy.coords;
+      std::vector<int> tx, ex, ty, ey;
+      if (lv.p >= 4 && !c.nu_kind && fx_tables(dx, tx, ex) && fx_tables(dy, ty, ey)) {
+        int *dtx, *dex, *dty, *dey;
+        if ((rc = upload(h, &dtx, tx)) || (rc = upload(h, &dex, ex)) || (rc = upload(h, &dty, ty)) ||
+            (rc = upload(h, &dey, ey)))
+          return bail(rc);
+        lv.fxx = FxDir{dtx, dex};
+        lv.fxy = FxDir{dty, dey};
+        h->fx_ok = true;
+      }
     }
     char* b;
     if ((rc = dev_alloc(h, &b, lv.nodes * tsz))) return bail(rc);
@@ -1662,6 +1685,25 @@ int sem_set_low_cycle(sem_handle* h, int32_t enable) {
   CK(cudaDeviceSynchronize());
   h->low_on = enable != 0;
   drop_graph(h);
+  return SEM_OK;
+}
+
+int sem_set_fixed_point_operator(sem_handle* h, int32_t enable) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (enable != 0 && enable != 1) return fail(SEM_BAD_ARG, "enable must be 0 or 1");
+  if (enable && !h->fx_ok) return fail(SEM_BAD_ARG, "no fixed-point operator for this configuration");
+  CK(cudaDeviceSynchronize());
+  h->fx_on = enable != 0;
+  drop_graph(h);
+  return SEM_OK;
+}
+
+int sem_get_fixed_point_operator(const sem_handle* h, int32_t* available, int32_t* enabled) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (available) *available = h->fx_ok ? 1 : 0;
+  if (enabled) *enabled = (h->fx_ok && h->fx_on) ? 1 : 0;
   return SEM_OK;
 }
 

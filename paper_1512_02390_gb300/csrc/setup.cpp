@@ -2,6 +2,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -630,6 +631,53 @@ std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, dou
     for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
   }
   return "";
+}
+
+bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t) {
+  const int p = d.p, np1 = p + 1, H = p / 2;
+  const int NE = (H + 1) * (H + 1), NO = H * H;
+  tab.assign((size_t)(d.n + 1) * (NE + NO) * 4, 0);  // element n: zeros (missing neighbours)
+  t.assign(d.n + 1, 0);
+  std::vector<__int128> li(np1 * np1);
+  for (int e = 0; e < d.n; ++e) {
+    const double* L = d.Le.data() + (size_t)e * np1 * np1;
+    double amax = 0.0;
+    for (int i = 0; i < np1 * np1; ++i) amax = std::max(amax, std::fabs(L[i]));
+    if (!(amax > 0.0) || !std::isfinite(amax)) return false;
+    int ex_max = 0;
+    std::frexp(amax, &ex_max);  // amax in [2^(ex_max-1), 2^ex_max)
+    const int te = 73 - ex_max;  // |L| 2^te < 2^73
+    t[e] = te;
+    for (int i = 0; i < np1 * np1; ++i) {
+      int ex = 0;
+      const double fr = std::frexp(L[i], &ex);        // L = fr 2^ex, |fr| in [0.5, 1)
+      const int64_t m = (int64_t)std::ldexp(fr, 53);  // exact: |m| < 2^53
+      const int sh = ex - 53 + te;                    // L 2^te = m 2^sh, sh <= 20
+      const __int128 am = m < 0 ? -(__int128)m : (__int128)m;
+      __int128 v;
+      if (L[i] == 0.0) v = 0;
+      else if (sh >= 0) v = am << sh;  // exact
+      else if (sh >= -100) v = (am + ((__int128)1 << (-sh - 1))) >> (-sh);  // nearest, ties away from zero
+      else v = 0;
+      li[i] = m < 0 ? -v : v;
+    }
+    for (int a = 0; a <= p; ++a)
+      for (int k = 0; k <= p; ++k)
+        if (li[(p - a) * np1 + (p - k)] != li[a * np1 + k]) return false;
+    int* out = tab.data() + (size_t)e * (NE + NO) * 4;
+    auto put = [&](int idx, __int128 v) {  // v = l2 2^50 + l1 2^25 + l0, l0, l1 in [0, 2^25)
+      const __int128 q1 = v >> 25, q2 = v >> 50;  // arithmetic shifts (floor)
+      out[4 * idx] = (int)(v - (q1 << 25));
+      out[4 * idx + 1] = (int)(q1 - (q2 << 25));
+      out[4 * idx + 2] = (int)q2;
+    };
+    for (int a = 0; a <= H; ++a)
+      for (int k = 0; k <= H; ++k)
+        put(a * (H + 1) + k, k == H ? 2 * li[a * np1 + H] : li[a * np1 + k] + li[a * np1 + p - k]);
+    for (int a = 0; a < H; ++a)
+      for (int k = 0; k < H; ++k) put(NE + a * H + k, li[a * np1 + k] - li[a * np1 + p - k]);
+  }
+  return true;
 }
 
 void interp_matrix(int pf, int pc, std::vector<double>& J) {

@@ -115,4 +115,17 @@ std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, dou
 // Interpolation J[i*(pc+1) + k] = phi_k^{(pc)}(xi_i^{(pf)}).
 void interp_matrix(int pf, int pc, std::vector<double>& J);
 
+// Fixed-point even-odd tables of one direction for the integer evaluation of
+// the FP64 operator (launch_apply_fx): per element e, L_int = L * 2^t[e] with
+// |L_int| < 2^73 (exact unless an element's entries span more than 20 binary
+// exponents; then rounded to nearest), E[a][k] = L_int[a][k] + L_int[a][p-k]
+// (k < p/2), E[a][p/2] = 2 L_int[a][p/2], O[a][k] = L_int[a][k] -
+// L_int[a][p-k], each stored as four ints (l0, l1, l2, 0) with value
+// l2 2^50 + l1 2^25 + l0, l0 and l1 in [0, 2^25).  tab: (n + 1) x
+// ((p/2+1)^2 + (p/2)^2) entries, element n all zero (t[n] = 0) for missing
+// neighbours.  Returns false (tables unusable) when an element matrix is not
+// centro-symmetric in these integers, L_int[p-a][p-k] == L_int[a][k], which
+// the even-odd form needs.
+bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t);
+
 }  // namespace sem

@@ -135,6 +135,13 @@ class Solver:
         """(available, enabled) of the one-launch up-leg of the V-cycle."""
         return B.sem_get_fused_prolongation(self.h)
 
+    def set_fixed_point_operator(self, enable):
+        B.sem_set_fixed_point_operator(self.h, enable)
+
+    def fixed_point_operator(self):
+        """(available, enabled) of the FP64 operator in exact integer arithmetic."""
+        return B.sem_get_fixed_point_operator(self.h)
+
     def set_tune_from(self, other):
         """Copy the launch shapes of a handle with the same levels."""
         for l in range(1, self.levels + 1):

@@ -210,3 +210,125 @@ def test_tf32_rounding_is_round_to_nearest_ties_away(tmp_path):
     want = np.where(mag == 0, v, want)
     assert np.array_equal(got, want)
     assert np.all((y & 0x1FFF) == 0)
+
+
+# ---- the exact fixed-point conversions of the integer FP64 operator ----------
+
+_FX_SRC = r'''
+#include "fx_exact.h"
+extern "C" void to_f64(const long long* c, const int* K, double* y, long n) {
+  for (long i = 0; i < n; ++i) y[i] = sem::fx_to_f64(c[4 * i], c[4 * i + 1], c[4 * i + 2], c[4 * i + 3], K[i]);
+}
+extern "C" void of(const double* x, const int* emax, long long* X, long n) {
+  for (long i = 0; i < n; ++i) X[i] = sem::fx_of(x[i], emax[i]);
+}
+extern "C" void limbs(const long long* v, int* lo, int* hi, long n) {
+  for (long i = 0; i < n; ++i) sem::fx_limbs(v[i], lo[i], hi[i]);
+}
+'''
+
+
+def _fx_lib(tmp_path):
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    src = tmp_path / "fx.cpp"
+    src.write_text(_FX_SRC)
+    so = tmp_path / "fx.so"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1512_02390_gb300", "csrc")
+    subprocess.run(["g++", "-O2", "-shared", "-fPIC", "-I", inc, str(src), "-o", str(so)], check=True)
+    return ctypes.CDLL(str(so))
+
+
+def test_fixed_point_sum_rounds_like_exact_rational_arithmetic(tmp_path):
+    """The integer FP64 operator turns four int64 accumulators (weights 2^0,
+    2^25, 2^50, 2^75, not carry-normalised, |c| < 2^62) times 2^-K into a
+    double.  Python's exact integers and its correctly rounded int -> float
+    division give the reference: every normal result must match bit for bit.
+    Cases: magnitudes of 1 to 136 bits of both signs, exact ties at the
+    rounding bit on both parities with their neighbours, carries spread over
+    the limbs in random ways, zero."""
+    import ctypes
+    from fractions import Fraction
+    lib = _fx_lib(tmp_path)
+    rng = np.random.default_rng(11)
+    vals = []
+    for nb in range(1, 137):
+        for _ in range(12):
+            v = int(rng.integers(1, 2**62)) << max(0, nb - 62)
+            v = (v | 1) & ((1 << nb) - 1) | (1 << (nb - 1))
+            vals.append(v if rng.random() < 0.5 else -v)
+    for _ in range(600):  # ties at the 53-bit rounding position and their neighbours
+        g = int(rng.integers(0, 80))
+        m = int(rng.integers(2**52, 2**53))
+        t = (2 * m + 1) << g
+        for v in (t, t - 1, t + 1):
+            vals.append(v if rng.random() < 0.5 else -v)
+    vals.append(0)
+    cs, Ks, want = [], [], []
+    B = 1 << 25
+    for v in vals:
+        c = [0, 0, 0, 0]
+        r = v
+        for i in range(3):  # canonical limbs, then move random carries between them
+            c[i] = r % B
+            r //= B
+        c[3] = r
+        for i in range(3):
+            a = int(rng.integers(-2**30, 2**30))
+            c[i] += a * B
+            c[i + 1] -= a
+        assert all(abs(x) < 2**62 for x in c)
+        assert c[0] + c[1] * B + c[2] * B**2 + c[3] * B**3 == v
+        top = abs(v).bit_length()
+        K = int(top + rng.integers(-1000, 1000)) if v else 5
+        w = float(Fraction(v, 1 << K)) if K >= 0 else float(v * (1 << -K))
+        if v and not (2.0**-1022 <= abs(w) < 2.0**1023):
+            continue
+        cs.append(c)
+        Ks.append(K)
+        want.append(w)
+    c = np.ascontiguousarray(np.array(cs, dtype=np.int64))
+    K = np.ascontiguousarray(np.array(Ks, dtype=np.int32))
+    y = np.empty(len(Ks))
+    lib.to_f64(c.ctypes.data_as(ctypes.c_void_p), K.ctypes.data_as(ctypes.c_void_p),
+               y.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(len(Ks)))
+    assert np.array_equal(y.view(np.uint64), np.array(want).view(np.uint64))
+
+
+def test_fixed_point_operand_and_limbs_are_exact(tmp_path):
+    """A staged double becomes X = x 2^(1075 - emax) rounded to the nearest
+    integer (ties away from zero), |X| < 2^53, and X +- X' splits exactly into
+    lo + hi 2^25 with lo in [0, 2^25)."""
+    import ctypes
+    from fractions import Fraction
+    lib = _fx_lib(tmp_path)
+    rng = np.random.default_rng(12)
+    n = 20000
+    x = np.ldexp(rng.uniform(0.5, 1.0, n), rng.integers(-1000, 1000, n)) * rng.choice([-1.0, 1.0], n)
+    ex = (x.view(np.uint64) >> np.uint64(52)) & np.uint64(0x7ff)
+    emax = (ex.astype(np.int64) + rng.integers(0, 60, n)).astype(np.int32)
+    x = np.concatenate([x, [0.0, -0.0, 2.0**-1074, 1.5, -1.5]])
+    emax = np.concatenate([emax, np.array([1023, 1023, 1023, 1023 + 53, 1023 + 53], dtype=np.int32)])
+    X = np.empty(x.size, dtype=np.int64)
+    lib.of(np.ascontiguousarray(x).ctypes.data_as(ctypes.c_void_p), np.ascontiguousarray(emax).ctypes.data_as(ctypes.c_void_p),
+           X.ctypes.data_as(ctypes.c_void_p), ctypes.c_long(x.size))
+    for xi, ei, Xi in zip(x, emax, X):
+        b = int(np.float64(xi).view(np.uint64))
+        if (b >> 52) & 0x7ff == 0:
+            assert Xi == 0
+            continue
+        q = Fraction(float(xi)) * Fraction(2) ** (1075 - int(ei))
+        r = int(abs(q) + Fraction(1, 2))  # nearest, ties away from zero
+        assert Xi == (r if q >= 0 else -r) and abs(int(Xi)) < 2**53
+    v = np.concatenate([rng.integers(-2**54 + 1, 2**54, 5000), [0, -1, 1, 2**25, -2**25, 2**54 - 1, -2**54 + 1]])
+    v = np.ascontiguousarray(v.astype(np.int64))
+    lo = np.empty(v.size, dtype=np.int32)
+    hi = np.empty(v.size, dtype=np.int32)
+    lib.limbs(v.ctypes.data_as(ctypes.c_void_p), lo.ctypes.data_as(ctypes.c_void_p), hi.ctypes.data_as(ctypes.c_void_p),
+              ctypes.c_long(v.size))
+    assert np.all((lo >= 0) & (lo < 2**25))
+    assert np.array_equal(lo.astype(np.int64) + hi.astype(np.int64) * 2**25, v)
