@@ -47,7 +47,9 @@ struct FxTile {
   static constexpr int LP = LN | 1;
   static constexpr int NE = (H + 1) * (H + 1), NO = H * H, EO = NE + NO;
   static constexpr int NV = 2 * H + 1;  // e_0..e_H, o_0..o_{H-1}
-  static constexpr int NW = 256 / 32;
+  static constexpr int NT = 256;  // threads per CTA
+  static constexpr int NW = NT / 32;
+  static constexpr int SB = P >= 32 ? 1 : 5;  // staging loads issued together per thread
 };
 
 template <int P>
@@ -57,7 +59,7 @@ size_t apply_fx_smem() {
                        + (size_t)(Q::TE + 1) * Q::NV * Q::TN  // e/o limb pairs of one direction
                        + (size_t)Q::TN * (Q::TE + 1) * Q::NP  // x products
                        + 2 * (Q::TN + 1);                    // mass diagonals
-  return 8 * eight + sizeof(double) * kRedThreads + sizeof(int) * Q::NW;
+  return 8 * eight + sizeof(double) * Q::NT + sizeof(int) * Q::NW;
 }
 
 __device__ __forceinline__ int2 fx_pair(long long v) {
@@ -148,7 +150,7 @@ __device__ __forceinline__ void fx_products(const FxDir& fd, const DirView<doubl
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) k_apply_fx(DirView<double> dx, DirView<double> dy, FxDir fx, FxDir fy,
+__global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, DirView<double> dy, FxDir fx, FxDir fy,
                                                   const double* __restrict__ u, const double* __restrict__ f,
                                                   double* __restrict__ out, int dot, double* __restrict__ part,
                                                   PcgFuse pf) {
@@ -165,20 +167,49 @@ __global__ void __launch_bounds__(256) k_apply_fx(DirView<double> dx, DirView<do
   double* sMx = xb + TN * (TE + 1) * NP;
   double* sMy = sMx + (TN + 1);
   double* sred = sMy + (TN + 1);
-  int* semax = reinterpret_cast<int*>(sred + kRedThreads);
+  int* semax = reinterpret_cast<int*>(sred + Q::NT);  // sred: NT doubles (block_sum_w0)
 
   const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
   const int Nx = dx.N, Ny = dy.N;
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
   const double beta = fused_beta(pf, blockIdx.y, gridDim.y);
+  // staging: the operand (z + beta p with the fused direction update, else
+  // u) on the tile and its low-side halo; the P x P corner below and left of
+  // the tile is read by neither direction and is zeroed.  The loads of kSB
+  // nodes are issued before their stores (one memory latency per batch).
   int emax = 0;  // largest exponent field of the staged values
-  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
-    const int ly = idx / LN, lx = idx - ly * LN;
-    const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
-    const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-    const double v = stage_value<P, double>(u, nullptr, dx, dy, pf, beta, gy, gx);
-    su[ly * LP + lx] = v;
-    emax = max(emax, (__double2hiint(v) >> 20) & 0x7ff);
+  constexpr int NT = Q::NT, kNS = (LN * LN + NT - 1) / NT, kSB = Q::SB;
+#pragma unroll
+  for (int b0 = 0; b0 < kNS; b0 += kSB) {
+    double va[kSB], vb[kSB];
+    int off[kSB];
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) {
+      const int idx = threadIdx.x + (b0 + j) * NT;
+      off[j] = -1;
+      va[j] = 0.0;
+      vb[j] = 0.0;
+      if (b0 + j < kNS && idx < LN * LN) {
+        const int ly = idx / LN, lx = idx - ly * LN;
+        off[j] = ly * LP + lx;
+        if (ly >= P || lx >= P) {
+          const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+          const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
+          if (gx >= 0 && gy >= 0) {
+            const long o = (long)gy * Nx + gx;
+            va[j] = u[o];
+            if (pf.z) vb[j] = pf.z[o];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) {
+      if (off[j] < 0) continue;
+      const double v = pf.z ? fma(beta, va[j], vb[j]) : va[j];  // as stage_value
+      su[off[j]] = v;
+      emax = max(emax, (__double2hiint(v) >> 20) & 0x7ff);
+    }
   }
   for (int idx = threadIdx.x; idx <= TN; idx += blockDim.x) {
     const int gx = ex0 * P + idx, gy = ey0 * P + idx;
@@ -195,11 +226,11 @@ __global__ void __launch_bounds__(256) k_apply_fx(DirView<double> dx, DirView<do
   const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
   // the owned staged values (for the dot product) before the tile turns into integers
-  constexpr int KOWN = ((TN + 1) * (TN + 1) + 255) / 256;
+  constexpr int KOWN = ((TN + 1) * (TN + 1) + NT - 1) / NT;
   double own[KOWN];
 #pragma unroll
   for (int q = 0; q < KOWN; ++q) {
-    const int idx = threadIdx.x + 256 * q;
+    const int idx = threadIdx.x + NT * q;
     own[q] = 0.0;
     if (idx < ownx * owny) {
       const int jy = idx / ownx, ix = idx - jy * ownx;
@@ -224,7 +255,7 @@ __global__ void __launch_bounds__(256) k_apply_fx(DirView<double> dx, DirView<do
   double acc = 0.0;
 #pragma unroll
   for (int q = 0; q < KOWN; ++q) {
-    const int idx = threadIdx.x + 256 * q;
+    const int idx = threadIdx.x + NT * q;
     if (idx >= ownx * owny) break;
     const int jy = idx / ownx, ix = idx - jy * ownx;
     const int gi = ex0 * P + ix, gj = ey0 * P + jy;
@@ -265,7 +296,7 @@ cudaError_t apply_fx_p(const DirView<double>& dx, const DirView<double>& dy, con
   const size_t sm = apply_fx_smem<P>();
   cudaError_t e = allow_smem(k_apply_fx<P>, sm);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_apply_fx<P>, grid, dim3(256), sm, s, dx, dy, fx, fy, u, f, out, dot, part, pf);
+  e = launch_pdl(k_apply_fx<P>, grid, dim3(Q::NT), sm, s, dx, dy, fx, fy, u, f, out, dot, part, pf);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
