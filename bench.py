@@ -44,6 +44,14 @@ FP64_PEAK_TFLOPS = 1.25
 # profiles/k_apply_eo_fp64_p16_64x64.md (writes stay in L2 within the launch)
 APPLY_EO_DRAM_BYTES = 17.02e6
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# 32 x 32 -> 64-bit integer multiply-adds (mad.wide.s32) per second of one
+# GB300: 56.2 per clock per SM measured at 2070 MHz
+# (profiles/alu_peaks_fma_probe.txt); the denominator of the integer FP64
+# operator, whose exact limb products run on that instruction
+INT_MAD_PEAK_TOPS = 56.24 * 152 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_apply_fx<16> launch on the 64 x 64,
+# p = 16 workload (profiles/k_apply_fx_p16_64x64.md): p and z read, q stays in L2
+APPLY_FX_DRAM_BYTES = 17.21e6
 
 
 def _peaks():
@@ -850,9 +858,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, from a profiled pass (same steps)
     _, _, kprof = timed(S, b, args.steps, 1, profile=True)
-    top_prof = S.profile_read_level(S.levels)
+    lvl_prof = {l: S.profile_read_level(l) for l in range(1, S.levels + 1)}
+    top_prof = lvl_prof[S.levels]
     S.profile(False)
-    dom = max(kprof, key=lambda k: kprof[k][0])
+    # the dominant KERNEL: a class launched on every level (one instantiation
+    # per order) counts with its largest level
+    kern = {k: v[0] for k, v in kprof.items()}
+    for cls in ("apply_mg", "sweep", "scatter", "restrict", "prolong"):
+        if cls in kern:
+            kern[cls] = max(lvl_prof[l].get(cls, (0.0, 0))[0] for l in lvl_prof)
+    dom = max(kern, key=lambda k: kern[k])
     peaks, src = _peaks()
     total_ms = sum(v[0] for v in kprof.values())
     iters = res.iterations
@@ -861,19 +876,36 @@ def run_ours(args):
     per_launch_ms = kprof[dom][0] / max(1, kprof[dom][1])
     if dom == "apply_fp64":
         # algorithmic count of the operator: two contractions of n_p^3 FMA per
-        # element, 4 n_p^3 / p^2 flop per unknown; the even-odd kernel executes
-        # 2 (2 ((p/2+1)^2 + (p/2)^2) + 2p) / p + 3 per unknown
+        # element, 4 n_p^3 / p^2 flop per unknown
         np_ = P_ORDER + 1
         alg = 4.0 * np_**3 / P_ORDER**2
         hh = P_ORDER // 2
-        executed = 2 * (2 * ((hh + 1) ** 2 + hh * hh) + 2 * P_ORDER) / P_ORDER + 3
-        ach = alg * S.n_unknowns / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": APPLY_EO_DRAM_BYTES,
-                "kernel": "k_apply_eo<double,16>: q = A (z + beta p), Eq. (system matrix), even-odd",
-                "flop_per_dof_algorithmic": alg, "flop_per_dof_executed": executed,
-                "algorithmic_bytes_per_launch": 24 * S.n_unknowns,
-                "peak_source": "nominal GB300 FP64 rate (FMA probe: 1.196 TFLOP/s measured)"}
+        fp64_eq = alg * S.n_unknowns / (per_launch_ms * 1e-3) / 1e12
+        if S.fixed_point_operator()[1]:
+            # the integer form: per element row and direction (p/2+1)^2 + (p/2)^2
+            # even-odd terms of 6 exact limb products (mad.wide.s32) for p owned
+            # outputs, two directions: 12 ((p/2+1)^2 + (p/2)^2) / p per unknown
+            mad = 12.0 * ((hh + 1) ** 2 + hh * hh) / P_ORDER
+            ach = mad * S.n_unknowns / (per_launch_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": INT_MAD_PEAK_TOPS, "unit": "Tops/s (mad.wide.s32)",
+                    "frac": ach / INT_MAD_PEAK_TOPS, "traffic": APPLY_FX_DRAM_BYTES,
+                    "kernel": "k_apply_fx<16>: q = A (z + beta p), Eq. (system matrix), even-odd products exact "
+                              "in int64 (fixed-point operands), one FP64 rounding per directional sum",
+                    "mad_wide_per_dof_algorithmic": mad, "algorithmic_bytes_per_launch": 24 * S.n_unknowns,
+                    "fp64_equivalent": {"flop_per_dof": alg, "achieved_tflops": fp64_eq,
+                                        "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                                        "ratio_to_fp64_peak": fp64_eq / FP64_PEAK_TFLOPS},
+                    "peak_source": "measured: integer multiply-add probe, 56.2 mad.wide.s32 per clock per SM "
+                                   "at 2070 MHz x 152 SMs"}
+        else:
+            # the FP64 even-odd kernel executes 2 (2 ((p/2+1)^2 + (p/2)^2) + 2p) / p + 3 per unknown
+            executed = 2 * (2 * ((hh + 1) ** 2 + hh * hh) + 2 * P_ORDER) / P_ORDER + 3
+            roof = {"bound": "alu", "achieved": fp64_eq, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fp64_eq / FP64_PEAK_TFLOPS, "traffic": APPLY_EO_DRAM_BYTES,
+                    "kernel": "k_apply_eo<double,16>: q = A (z + beta p), Eq. (system matrix), even-odd",
+                    "flop_per_dof_algorithmic": alg, "flop_per_dof_executed": executed,
+                    "algorithmic_bytes_per_launch": 24 * S.n_unknowns,
+                    "peak_source": "nominal GB300 FP64 rate (FMA probe: 1.196 TFLOP/s measured)"}
     elif dom == "sweep":
         w = _level_work(P_ORDER, N_O, ne)
         cycles = kprof[dom][1] / w["sweep_launches_per_cycle"]
@@ -885,7 +917,7 @@ def run_ours(args):
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None}
-    roof["share_of_device_time"] = kprof[dom][0] / total_ms if total_ms else None
+    roof["share_of_device_time"] = kern[dom] / total_ms if total_ms else None
     roof["class_ms"] = {k: round(v[0] / args.steps, 4) for k, v in kprof.items()}
     roof["class_launches_per_step"] = {k: v[1] / args.steps for k, v in kprof.items()}
 
@@ -895,7 +927,7 @@ def run_ours(args):
         "metric": METRIC, "value": variants["%s_no%d" % (HEADLINE, N_O)]["dof_per_s"], "unit": "DOF/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 outer MGCG + %s V-cycle" % HEADLINE, "data": "synthetic",
+        "dtype": "f64 outer MGCG (operator products exact in int64) + %s V-cycle" % HEADLINE, "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": S.n_unknowns, "precision": HEADLINE, "n_o": N_O,
                    "iterations": iters, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "seed": SEED},
