@@ -55,7 +55,7 @@ struct FxTile {
 template <int P>
 size_t apply_fx_smem() {
   using Q = FxTile<P>;
-  const size_t eight = (size_t)Q::LN * Q::LP                // staged tile (double, then int64)
+  const size_t eight = (size_t)Q::LN * Q::LP                // staged tile (double)
                        + (size_t)(Q::TE + 1) * Q::NV * Q::TN  // e/o limb pairs of one direction
                        + (size_t)Q::TN * (Q::TE + 1) * Q::NP  // x products
                        + 2 * (Q::TN + 1);                    // mass diagonals
@@ -68,9 +68,11 @@ __device__ __forceinline__ int2 fx_pair(long long v) {
   return make_int2(lo, hi);
 }
 
-// e/o limb pairs of one direction from the fixed-point tile sx
+// e/o limb pairs of one direction from the staged tile su, each value taken
+// to fixed point on the way (fx_of: bounded for any input, so a tile with a
+// non-finite value, whose outputs are NaN, needs no special case here)
 template <int P, bool XDIR>
-__device__ __forceinline__ void fx_form_eo(const long long* sx, int2* ev) {
+__device__ __forceinline__ void fx_form_eo(const double* su, int emax, int2* ev) {
   using Q = FxTile<P>;
   constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LP = Q::LP, NV = Q::NV;
   for (int idx = threadIdx.x; idx < (TE + 1) * H * TN; idx += blockDim.x) {
@@ -79,20 +81,21 @@ __device__ __forceinline__ void fx_form_eo(const long long* sx, int2* ev) {
     const int sl = q / H, k = q - sl * H;
     long long xk, xm;
     if (XDIR) {
-      const long long* x = sx + (w + P) * LP + sl * P;
-      xk = x[k];
-      xm = x[P - k];
+      const double* x = su + (w + P) * LP + sl * P;
+      xk = fx_of(x[k], emax);
+      xm = fx_of(x[P - k], emax);
     } else {
-      const long long* x = sx + (sl * P) * LP + w + P;
-      xk = x[k * LP];
-      xm = x[(P - k) * LP];
+      const double* x = su + (sl * P) * LP + w + P;
+      xk = fx_of(x[k * LP], emax);
+      xm = fx_of(x[(P - k) * LP], emax);
     }
     ev[(sl * NV + k) * TN + w] = fx_pair(xk + xm);
     ev[(sl * NV + H + 1 + k) * TN + w] = fx_pair(xk - xm);
   }
   for (int idx = threadIdx.x; idx < (TE + 1) * TN; idx += blockDim.x) {
     const int w = idx % TN, sl = idx / TN;
-    ev[(sl * NV + H) * TN + w] = fx_pair(XDIR ? sx[(w + P) * LP + sl * P + H] : sx[(sl * P + H) * LP + w + P]);
+    ev[(sl * NV + H) * TN + w] =
+        fx_pair(fx_of(XDIR ? su[(w + P) * LP + sl * P + H] : su[(sl * P + H) * LP + w + P], emax));
   }
 }
 
@@ -159,7 +162,6 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
   constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, NV = Q::NV, NW = Q::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* su = reinterpret_cast<double*>(smem_raw);  // LN x LP, then the fixed-point tile in place
-  long long* sx = reinterpret_cast<long long*>(su);
   int2* ev = reinterpret_cast<int2*>(su + LN * LP);   // (TE+1) x NV x TN
   double* xb = reinterpret_cast<double*>(ev + (TE + 1) * NV * TN);  // [row][slot][a]
   double* yb = su;                                    // [slot][b][col], over the tile once the y e/o are formed
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
   const bool lastx = ex0 + TE >= dx.n, lasty = ey0 + TE >= dy.n;
   const int ownx = min(TE, dx.n - ex0) * P + ((!dx.periodic && lastx) ? 1 : 0);
   const int owny = min(TE, dy.n - ey0) * P + ((!dy.periodic && lasty) ? 1 : 0);
-  // the owned staged values (for the dot product) before the tile turns into integers
+  // the owned staged values (for the dot product): the y products overwrite the tile
   constexpr int KOWN = ((TN + 1) * (TN + 1) + NT - 1) / NT;
   double own[KOWN];
 #pragma unroll
@@ -237,17 +239,11 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
       own[q] = su[(jy + P) * LP + ix + P];
     }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < LN * LN; idx += blockDim.x) {
-    const int ly = idx / LN, lx = idx - ly * LN;
-    sx[ly * LP + lx] = finite ? fx_of(su[ly * LP + lx], emax) : 0LL;
-  }
-  __syncthreads();
-  fx_form_eo<P, true>(sx, ev);
+  fx_form_eo<P, true>(su, emax, ev);
   __syncthreads();
   fx_products<P, true>(fx, dx, ex0 - 1, emax, ev, xb);
   __syncthreads();
-  fx_form_eo<P, false>(sx, ev);
+  fx_form_eo<P, false>(su, emax, ev);
   __syncthreads();
   fx_products<P, false>(fy, dy, ey0 - 1, emax, ev, yb);
   __syncthreads();
