@@ -343,13 +343,14 @@ int sem_get_fused_prolongation(const sem_handle* h, int32_t* available, int32_t*
 /* The FP64 operator of Eq. (system matrix) (the outer MGCG operator of
  * Alg. 4, sem_apply, the residuals of sem_mg_solve) evaluated exactly in
  * integer arithmetic.  Each tile of u becomes 53-bit fixed point with one
- * power-of-two scale, each element matrix 59-bit fixed point (built once at
- * sem_create); the even-odd products are summed exactly in 64-bit integers on
- * the integer pipe (the GPU's FP64 pipe is ~30x slower than its 32-bit integer
- * multiply-add) and each directional sum is rounded to FP64 once.  The only
- * roundings besides that last one are the fixed-point steps (2^-53 of a
- * tile's largest |u|, 2^-59 of an element's largest stiffness entry), so the
- * result is at least as accurate as the FP64 evaluation.  Available for the
+ * power-of-two scale; each element matrix becomes exact 75-bit fixed point
+ * (built once at sem_create; exact while an element's entries span at most 20
+ * binary exponents, as the GLL stiffness matrices do); the even-odd products
+ * are summed exactly in 64-bit integers on the integer pipe (the GPU's FP64
+ * pipe is ~30x slower than its 32-bit integer multiply-add) and each
+ * directional sum is rounded to FP64 once, to nearest.  The only other
+ * rounding is the fixed-point step of u (2^-53 of a tile's largest |u|), so
+ * the result is at least as accurate as the FP64 evaluation.  Available for the
  * Poisson operator at p >= 4 when every element matrix is centro-symmetric
  * (uniform and stretched meshes); on by default.  A tile that holds a
  * non-finite value writes NaN on its nodes.  sem_set_fixed_point_operator(h,
