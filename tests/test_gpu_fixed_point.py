@@ -3,9 +3,10 @@ arithmetic (fixed-point operands, exact 64-bit sums, one final rounding)
 against the oracle's FP64 operator and the library's FP64-pipe evaluation.
 
 Error model.  The FP64 evaluation of (A u)_i errs by about eps (|A| |u|)_i.
-The fixed-point one rounds each staged value to 2^-53 of its tile's largest
-|u| and each element matrix to 2^-59 of its largest entry, then sums exactly,
-so it errs by at most about eps (|A| 1)_i max|u| plus its one final rounding.
+The fixed-point one rounds each staged value to about eps of its tile's
+largest |u|, holds each element matrix exactly (75-bit fixed point), then sums
+exactly, so it errs by at most about eps (|A| 1)_i max|u| plus its one final
+rounding.
 The bar below, 16 eps ((|A| |u|)_i + (|A| 1)_i max|u|), holds both with room;
 |A| is bounded by M_y (x) |L_x| + |L_y| (x) M_x from the oracle's assembled 1D
 matrices.  Inputs: uniform random, and random with magnitudes spread over 30
