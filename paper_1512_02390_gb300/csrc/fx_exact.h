@@ -50,23 +50,22 @@ SEM_FX_FN int fx_clz64(uint64_t v) {  // v != 0
 // x = X 2^(emax - 1075) with emax >= the exponent field of x: X is the
 // mantissa (hidden bit included) divided by 2^(emax - exponent), rounded to
 // nearest, ties away from zero; 0 for zeros and subnormals.  |X| < 2^53.
+// Without branches: a shift of 54 or more leaves 0 (the mantissa is below
+// 2^53, the rounding half below 2^(shift - 1)), so the shift is capped at 63.
 SEM_FX_FN int64_t fx_of(double v, int emax) {
   const uint64_t b = fx_bits(v);
   const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex == 0) return 0;
-  const int64_t m = (int64_t)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
-  const int sh = emax - ex;  // >= 0
-  int64_t X;
-  if (sh == 0) X = m;
-  else if (sh <= 53) X = (m + ((int64_t)1 << (sh - 1))) >> sh;
-  else X = 0;
-  return (b >> 63) ? -X : X;
+  const uint64_t m = ex != 0 ? ((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52)) : 0ULL;
+  const int d = emax - ex;  // >= 0
+  const int sh = d < 63 ? d : 63;
+  const uint64_t X = (m + ((1ULL << sh) >> 1)) >> sh;
+  const int64_t sg = -(int64_t)(b >> 63);  // 0 or -1
+  return ((int64_t)X ^ sg) - sg;
 }
 
 SEM_FX_FN void fx_limbs(int64_t v, int& lo, int& hi) {
-  const int64_t h = v >> 25;  // floor
-  lo = (int)(v - h * ((int64_t)1 << 25));
-  hi = (int)h;
+  lo = (int)(v & (((int64_t)1 << 25) - 1));  // v mod 2^25 (two's complement)
+  hi = (int)(v >> 25);                        // floor(v / 2^25), |v| < 2^54
 }
 
 // top: the 64 bits of a magnitude from its leading one down (bit 63 set);
@@ -90,53 +89,51 @@ SEM_FX_FN double fx_round(uint64_t top, bool sticky, int e, bool neg) {
 }
 
 // (c0 + c1 2^25 + c2 2^50 + c3 2^75) 2^-K for |c| < 2^62, rounded to the
-// nearest double (ties to even; normal results exactly so)
+// nearest double (ties to even; normal results exactly so).  The value V can
+// need 138 bits, so it is held as V = W 2^11 + s with W = floor(V / 2^11)
+// a 128-bit two's complement (|W| < 2^127) and s in [0, 2^11); the branches
+// left are the rare zero and out-of-range results.
 SEM_FX_FN double fx_to_f64(int64_t c0, int64_t c1, int64_t c2, int64_t c3, int K) {
-  const int64_t B = (int64_t)1 << 25;
-  int64_t q = c0 >> 25;  // carries: c0, c1, c2 into [0, 2^25)
-  c0 -= q * B;
-  c1 += q;
-  q = c1 >> 25;
-  c1 -= q * B;
-  c2 += q;
-  q = c2 >> 25;
-  c2 -= q * B;
-  c3 += q;
-  // value = c3 2^75 + R, R = rh 2^64 + rl in [0, 2^75)
-  uint64_t rl = ((uint64_t)c2 << 50) | ((uint64_t)c1 << 25) | (uint64_t)c0;
-  uint64_t rh = (uint64_t)c2 >> 14;
-  const bool neg = c3 < 0;
-  uint64_t A = (uint64_t)c3;
-  if (neg) {  // magnitude (-c3) 2^75 - R = (-c3 - 1) 2^75 + (2^75 - R)
-    A = 0ULL - (uint64_t)c3;
-    if (rl | rh) {
-      A -= 1;
-      rh = (1ULL << 11) - rh - (rl != 0 ? 1ULL : 0ULL);
-      rl = 0ULL - rl;
-    }
-  }
-  // magnitude = A 2^75 + rh 2^64 + rl, A < 2^63, rh < 2^11
-  if (A != 0) {
-    const int lz = fx_clz64(A);
-    const int s2 = 75 - lz;  // bits of R below the top 64: 12 .. 75
-    uint64_t low;            // R >> s2
-    bool sticky;
-    if (s2 >= 64) {
-      low = s2 >= 75 ? 0ULL : (rh >> (s2 - 64));
-      sticky = rl != 0 || (s2 >= 75 ? rh != 0 : (rh & ((1ULL << (s2 - 64)) - 1)) != 0);
-    } else {
-      low = (rh << (64 - s2)) | (rl >> s2);
-      sticky = (rl << (64 - s2)) != 0;
-    }
-    return fx_round((lz == 0 ? A : (A << lz)) | low, sticky, 138 - lz - K, neg);
-  }
-  if (rh != 0) {
-    const int lz = fx_clz64(rh);  // >= 53
-    return fx_round((rh << lz) | (rl >> (64 - lz)), (rl << lz) != 0, 127 - lz - K, neg);
-  }
-  if (rl == 0) return 0.0;
-  const int lz = fx_clz64(rl);
-  return fx_round(rl << lz, false, 63 - lz - K, neg);
+  // S = c0 + c1 2^25 + c2 2^50, |S| < 2^113, as the words (sh, sl)
+  uint64_t sl = (uint64_t)c0, sh = (uint64_t)(c0 >> 63);
+  uint64_t t = (uint64_t)c1 << 25;
+  sl += t;
+  sh += (uint64_t)(c1 >> 39) + (sl < t ? 1ULL : 0ULL);
+  t = (uint64_t)c2 << 50;
+  sl += t;
+  sh += (uint64_t)(c2 >> 14) + (sl < t ? 1ULL : 0ULL);
+  // W = floor(S / 2^11) + c3 2^64 (c3 2^75 is a multiple of 2^11), s = S mod 2^11
+  const uint64_t s = sl & 0x7FFULL;
+  uint64_t wl = (sl >> 11) | (sh << 53);
+  uint64_t wh = (uint64_t)((int64_t)sh >> 11) + (uint64_t)c3;
+  // |V| = M 2^11 + z: V >= 0: M = W, z = s; V < 0: M = -W - (s != 0) = ~W + (s == 0),
+  // z = (2^11 - s) mod 2^11
+  const uint64_t ng = (uint64_t)((int64_t)wh >> 63);  // all ones when V < 0
+  const uint64_t inc = ng & (s == 0 ? 1ULL : 0ULL);
+  wl ^= ng;
+  wh ^= ng;
+  wl += inc;
+  wh += wl < inc ? 1ULL : 0ULL;
+  const uint64_t z = ((ng != 0 ? 0x800ULL - s : s) & 0x7FFULL) << 53;
+  // |V| 2^53 = wh 2^128 + wl 2^64 + z: its leading nonzero word a, the next b, the rest c
+  const bool h0 = wh == 0, h1 = h0 && wl == 0;
+  const uint64_t a = h0 ? (h1 ? z : wl) : wh;
+  const uint64_t b = h0 ? (h1 ? 0ULL : z) : wl;
+  const uint64_t c = h0 ? 0ULL : z;
+  if (a == 0) return 0.0;
+  const int l = fx_clz64(a);
+  const uint64_t top = (a << l) | ((b >> 1) >> (63 - l));
+  const bool sticky = (b << l) != 0 || c != 0;
+  const int e = (h0 ? (h1 ? 63 : 127) : 191) - l - 53 - K;  // the leading one has weight 2^e
+  uint64_t m = top >> 11;                                     // 53 bits
+  const uint64_t rb = (top >> 10) & 1ULL;
+  const uint64_t st = ((top & 0x3FFULL) != 0 || sticky) ? 1ULL : 0ULL;
+  m += rb & (st | (m & 1ULL));
+  const int be = e + 1023;  // biased exponent before a carry out of the rounding
+  const int bc = be + (int)(m >> 53);
+  if (bc <= 0 || bc >= 2047) return fx_round(top, sticky, e, ng != 0);
+  // m in [2^52, 2^53]: a carry to 2^53 moves into the exponent field
+  return fx_double((ng & (1ULL << 63)) | (((uint64_t)(be - 1) << 52) + m));
 }
 
 }  // namespace sem

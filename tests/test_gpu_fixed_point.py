@@ -36,6 +36,8 @@ EPS = np.finfo(np.float64).eps
 CASES = [
     dict(nx=4, ny=4, p=4),
     dict(nx=5, ny=3, p=4, overlap=2),                         # ragged tiles (4 elements per tile)
+    dict(nx=3, ny=5, p=4, periodic=True),                     # periodic tiles wider than the mesh
+    dict(nx=6, ny=3, p=4, periodic=True, overlap=2),
     dict(nx=4, ny=6, p=8, periodic=True, overlap=3),
     dict(nx=7, ny=5, p=16, overlap=2),                        # ragged tiles (2 elements per tile)
     dict(nx=3, ny=3, p=32),
