@@ -12,8 +12,9 @@
 //     largest exponent keeps all 53 mantissa bits, smaller values are rounded
 //     to the same absolute step (2^-53 of the tile's bound);
 //   - the element matrix, L = L_int 2^-t with |L_int| < 2^73 (per element and
-//     direction, built on the host: setup.cpp fx_tables), exact for the GLL
-//     stiffness matrices (their entries span at most 20 binary exponents);
+//     direction, built on the host: setup.cpp fx_tables; elements with equal
+//     matrices share one table), exact for the GLL stiffness matrices (their
+//     entries span at most 20 binary exponents);
 //   - e_k = X_k + X_{p-k}, o_k = X_k - X_{p-k}, E = L_int[a][k] + L_int[a][p-k],
 //     O = L_int[a][k] - L_int[a][p-k] are exact integers; with the limbs
 //     e = e1 2^25 + e0 (e0 in [0, 2^25), |e1| < 2^29) and E = E2 2^50 + E1 2^25
@@ -52,14 +53,35 @@ struct FxTile {
   static constexpr int SB = P >= 32 ? 1 : 5;  // staging loads issued together per thread
 };
 
+// Shared memory.  Two phase schedules, chosen per order by measurement:
+//  - merged (p != 16): the e/o pairs of both directions are formed from the
+//    staged tile, then all products run in one pass (one barrier less, and
+//    the items of both directions balance over the warps).  Region A holds
+//    the staged tile, later the x and y products; region B the e/o pairs of
+//    both directions, later the block-sum scratch.
+//  - separate (p = 16, where the larger footprint of the merged form lost at
+//    256 x 256 elements): e/o and products of x, then of y.  Region A holds
+//    the staged tile, later the y products; region B the e/o pairs of one
+//    direction, the x products and the block-sum scratch.
+// Then the mass diagonals, the per-warp exponent maxima and the per-slot
+// table indices and scales.
+template <int P>
+struct FxSmem {
+  using Q = FxTile<P>;
+  static constexpr bool kMerged = P != 16;
+  static constexpr int kTile = Q::LN * Q::LP;                // staged tile (double)
+  static constexpr int kProd = Q::TN * (Q::TE + 1) * Q::NP;  // products of one direction (double)
+  static constexpr int kEv = (Q::TE + 1) * Q::NV * Q::TN;    // e/o pairs of one direction (int2)
+  static constexpr int kA = kMerged ? (kTile > 2 * kProd ? kTile : 2 * kProd) : kTile;
+  static constexpr int kB = kMerged ? 2 * kEv : kEv + kProd + Q::NT;  // 8-byte words
+  static_assert(kMerged ? 2 * kEv >= Q::NT : kProd <= kTile, "shared-memory regions overlap");
+  static constexpr size_t kBytes =
+      8 * ((size_t)kA + kB + 2 * (Q::TN + 1)) + sizeof(int) * (Q::NW + 4 * (Q::TE + 1));
+};
+
 template <int P>
 size_t apply_fx_smem() {
-  using Q = FxTile<P>;
-  const size_t eight = (size_t)Q::LN * Q::LP                // staged tile (double)
-                       + (size_t)(Q::TE + 1) * Q::NV * Q::TN  // e/o limb pairs of one direction
-                       + (size_t)Q::TN * (Q::TE + 1) * Q::NP  // x products
-                       + 2 * (Q::TN + 1);                    // mass diagonals
-  return 8 * eight + sizeof(double) * Q::NT + sizeof(int) * Q::NW;
+  return FxSmem<P>::kBytes;
 }
 
 __device__ __forceinline__ int2 fx_pair(long long v) {
@@ -99,28 +121,23 @@ __device__ __forceinline__ void fx_form_eo(const double* su, int emax, int2* ev)
   }
 }
 
-// element-row products of one direction; item (slot, a, w), slot 0 (the
-// low-side neighbour) only for its y_P.  Slot sl is element e_first + sl (n
-// when it does not exist: the zero table).
+// element-row products of one direction, item idx = (slot, a, w) of
+// TN (1 + TE (H + 1)); slot 0 (the low-side neighbour) only for its y_P.
+// sts: the table of each slot's element, then its scale t (the zero table
+// where the element does not exist).
 template <int P, bool XDIR>
-__device__ __forceinline__ void fx_products(const FxDir& fd, const DirView<double>& d, int e_first, int emax,
-                                            const int2* ev, double* dst_base) {
+__device__ __forceinline__ void fx_item(const int4* __restrict__ tab, const int* sts, int emax, const int2* ev,
+                                        double* dst_base, int idx) {
   using Q = FxTile<P>;
   constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, NP = Q::NP, EO = Q::EO, NE = Q::NE, NV = Q::NV;
-  constexpr int XI = TN * (1 + TE * (H + 1));
-  const int4* tab = reinterpret_cast<const int4*>(fd.tab);
-  for (int idx = threadIdx.x; idx < XI; idx += blockDim.x) {
+  {
     const int w = idx % TN;
     const int q = idx / TN;
     const int sl = q == 0 ? 0 : 1 + (q - 1) / (H + 1);
     const int a = q == 0 ? 0 : (q - 1) % (H + 1);
-    // element e_first + sl, in [-1, n + TE - 2]; a periodic mesh has n >= 3
-    // and TE <= 4, so one wrap maps it into [0, n)
-    int el = e_first + sl;
-    if (d.periodic) el = el < 0 ? el + d.n : (el >= d.n ? el - d.n : el);
-    if (el < 0 || el >= d.n) el = d.n;
-    const int4* E = tab + (long)el * EO + a * (H + 1);
-    const int4* O = tab + (long)el * EO + NE + min(a, H - 1) * H;
+    const int ts = sts[sl];
+    const int4* E = tab + (long)ts * EO + a * (H + 1);
+    const int4* O = tab + (long)ts * EO + NE + min(a, H - 1) * H;
     const int2* e = ev + (sl * NV) * TN + w;
     const int2* o = ev + (sl * NV + H + 1) * TN + w;
     long long e0 = 0, e1 = 0, e2 = 0, e3 = 0, o0 = 0, o1 = 0, o2 = 0, o3 = 0;
@@ -177,7 +194,7 @@ __device__ __forceinline__ void fx_products(const FxDir& fd, const DirView<doubl
       }
     }
     // y = (YE +- YO) 2^-(s + t + 1), s = 1075 - emax
-    const int K = 1076 - emax + __ldg(fd.t + el);
+    const int K = 1076 - emax + sts[TE + 1 + sl];
     double* dst = XDIR ? dst_base + (w * (TE + 1) + sl) * NP : dst_base + (sl * NP) * TN + w;
     constexpr int step = XDIR ? 1 : TN;
     if (a < H) dst[(P - a) * step] = fx_to_f64(e0 - o0, e1 - o1, e2 - o2, e3 - o3, K);
@@ -192,17 +209,19 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
                                                   PcgFuse pf) {
   pdl_enter();
   using Q = FxTile<P>;
-  constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, NV = Q::NV, NW = Q::NW;
+  constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, NW = Q::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* su = reinterpret_cast<double*>(smem_raw);  // LN x LP, then the fixed-point tile in place
-  int2* ev = reinterpret_cast<int2*>(su + LN * LP);   // (TE+1) x NV x TN
-  double* xb = reinterpret_cast<double*>(ev + (TE + 1) * NV * TN);  // [row][slot][a]
-  double* yb = su;                                    // [slot][b][col], over the tile once the y e/o are formed
-  static_assert(TN * (TE + 1) * NP <= LN * LP, "y products must fit in the staged tile");
-  double* sMx = xb + TN * (TE + 1) * NP;
+  using S = FxSmem<P>;
+  double* su = reinterpret_cast<double*>(smem_raw);  // region A: the staged tile (LN x LP)
+  int2* evx = reinterpret_cast<int2*>(su + S::kA);    // region B: e/o pairs, (TE+1) x NV x TN
+  int2* evy = S::kMerged ? evx + S::kEv : evx;
+  double* xb = S::kMerged ? su : reinterpret_cast<double*>(evx + S::kEv);  // [row][slot][a]
+  double* yb = S::kMerged ? su + S::kProd : su;                            // [slot][b][col]
+  double* sred = S::kMerged ? reinterpret_cast<double*>(evx) : xb + S::kProd;  // NT doubles
+  double* sMx = su + S::kA + S::kB;
   double* sMy = sMx + (TN + 1);
-  double* sred = sMy + (TN + 1);
-  int* semax = reinterpret_cast<int*>(sred + Q::NT);  // sred: NT doubles (block_sum_w0)
+  int* semax = reinterpret_cast<int*>(sMy + (TN + 1));
+  int* stab = semax + NW;  // per direction: TE + 1 tables, TE + 1 scales
 
   const int ex0 = blockIdx.x * TE, ey0 = blockIdx.y * TE;
   const int Nx = dx.N, Ny = dy.N;
@@ -251,6 +270,21 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
     sMx[idx] = gx < Nx ? dx.Mg[gx] : 0.0;
     sMy[idx] = gy < Ny ? dy.Mg[gy] : 0.0;
   }
+  if (threadIdx.x < 2 * (TE + 1)) {
+    // the table and scale of each slot's element (slot sl: element e0 - 1 + sl,
+    // in [-1, n + TE - 2]; a periodic mesh has n >= 3 and TE <= 4, so one wrap
+    // maps it into [0, n); "element" n is the zero table)
+    const bool ydir = threadIdx.x > TE;
+    const int sl = ydir ? threadIdx.x - (TE + 1) : threadIdx.x;
+    const DirView<double>& d = ydir ? dy : dx;
+    const FxDir& fd = ydir ? fy : fx;
+    int el = (ydir ? ey0 : ex0) - 1 + sl;
+    if (d.periodic) el = el < 0 ? el + d.n : (el >= d.n ? el - d.n : el);
+    if (el < 0 || el >= d.n) el = d.n;
+    const int ts = __ldg(fd.slot + el);
+    stab[(ydir ? 2 * (TE + 1) : 0) + sl] = ts;
+    stab[(ydir ? 3 : 1) * (TE + 1) + sl] = __ldg(fd.t + ts);
+  }
   emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
   if ((threadIdx.x & 31) == 0) semax[threadIdx.x >> 5] = emax;
   __syncthreads();
@@ -272,14 +306,28 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
       own[q] = su[(jy + P) * LP + ix + P];
     }
   }
-  fx_form_eo<P, true>(su, emax, ev);
-  __syncthreads();
-  fx_products<P, true>(fx, dx, ex0 - 1, emax, ev, xb);
-  __syncthreads();
-  fx_form_eo<P, false>(su, emax, ev);
-  __syncthreads();
-  fx_products<P, false>(fy, dy, ey0 - 1, emax, ev, yb);
-  __syncthreads();
+  const int4* tabx = reinterpret_cast<const int4*>(fx.tab);
+  const int4* taby = reinterpret_cast<const int4*>(fy.tab);
+  constexpr int XI = TN * (1 + TE * (Q::H + 1));  // product items per direction
+  if constexpr (S::kMerged) {
+    fx_form_eo<P, true>(su, emax, evx);
+    fx_form_eo<P, false>(su, emax, evy);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 2 * XI; idx += NT) {
+      if (idx < XI) fx_item<P, true>(tabx, stab, emax, evx, xb, idx);
+      else fx_item<P, false>(taby, stab + 2 * (TE + 1), emax, evy, yb, idx - XI);
+    }
+    __syncthreads();
+  } else {
+    fx_form_eo<P, true>(su, emax, evx);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < XI; idx += NT) fx_item<P, true>(tabx, stab, emax, evx, xb, idx);
+    __syncthreads();
+    fx_form_eo<P, false>(su, emax, evy);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < XI; idx += NT) fx_item<P, false>(taby, stab + 2 * (TE + 1), emax, evy, yb, idx);
+    __syncthreads();
+  }
 
   double acc = 0.0;
 #pragma unroll
@@ -335,7 +383,7 @@ cudaError_t apply_fx_p(const DirView<double>& dx, const DirView<double>& dy, con
 cudaError_t launch_apply_fx(const DirView<double>& dx, const DirView<double>& dy, const FxDir& fx,
                             const FxDir& fy, const double* u, const double* f, double* out, int dot, double* part,
                             int* nparts, cudaStream_t s, PcgFuse pf) {
-  if (!fx.tab || !fx.t || !fy.tab || !fy.t || dx.p != dy.p) return cudaErrorInvalidValue;
+  if (!fx.tab || !fx.t || !fx.slot || !fy.tab || !fy.t || !fy.slot || dx.p != dy.p) return cudaErrorInvalidValue;
   switch (dx.p) {
     case 4: return apply_fx_p<4>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);
     case 8: return apply_fx_p<8>(dx, dy, fx, fy, u, f, out, dot, part, nparts, s, pf);

@@ -48,13 +48,15 @@ cudaError_t launch_apply(const DirView<T>& dx, const DirView<T>& dy, const T* u,
 // O = L[a][k] - L[a][p-k], exact in integers) are accumulated exactly in
 // 64-bit integers (6 mad.wide.s32 per term, on the integer pipe), and each
 // directional sum sum_k L[i][k] u_k is rounded to FP64 once.  FxDir holds, per
-// element and direction, the tables of setup.h fx_tables: E[a][k],
-// a, k = 0..p/2 (entry k = p/2: 2 L[a][p/2]), then O[a][k], a, k < p/2, each
-// entry four ints (l0, l1, l2, 0) = l2 2^50 + l1 2^25 + l0; element n is all
-// zero (missing neighbours).
+// direction, the tables of setup.h fx_tables: per distinct element matrix
+// E[a][k], a, k = 0..p/2 (entry k = p/2: 2 L[a][p/2]), then O[a][k], a, k <
+// p/2, each entry four ints (l0, l1, l2, 0) = l2 2^50 + l1 2^25 + l0, and per
+// element the index of its table; "element" n maps to an all-zero table
+// (missing neighbours).
 struct FxDir {
-  const int* tab;   // (n + 1) x ((p/2+1)^2 + (p/2)^2) x 4
-  const int* t;     // n + 1: L_int = L * 2^t[e]
+  const int* tab;   // k + 1 distinct tables of ((p/2+1)^2 + (p/2)^2) x 4 ints, the last all zero
+  const int* t;     // k + 1: L_int = L * 2^t[table]
+  const int* slot;  // n + 1: element e's table (slot[n]: the zero table)
 };
 // out = A u (f == nullptr) or f - A u, FP64 (p in {4, 8, 16, 32}); dot and pf
 // as for launch_apply (no fused scatter).  A tile holding a non-finite value

@@ -1209,14 +1209,14 @@ static int create_handle(const sem_config& c, int nb, sem_handle** out) {
     if (l == L) {
       h->xc = dx.coords;
       h->yc = dy.coords;
-      std::vector<int> tx, ex, ty, ey;
-      if (lv.p >= 4 && !c.nu_kind && fx_tables(dx, tx, ex) && fx_tables(dy, ty, ey)) {
-        int *dtx, *dex, *dty, *dey;
-        if ((rc = upload(h, &dtx, tx)) || (rc = upload(h, &dex, ex)) || (rc = upload(h, &dty, ty)) ||
-            (rc = upload(h, &dey, ey)))
+      std::vector<int> tx, ex, sx, ty, ey, sy;
+      if (lv.p >= 4 && !c.nu_kind && fx_tables(dx, tx, ex, sx) && fx_tables(dy, ty, ey, sy)) {
+        int *dtx, *dex, *dsx, *dty, *dey, *dsy;
+        if ((rc = upload(h, &dtx, tx)) || (rc = upload(h, &dex, ex)) || (rc = upload(h, &dsx, sx)) ||
+            (rc = upload(h, &dty, ty)) || (rc = upload(h, &dey, ey)) || (rc = upload(h, &dsy, sy)))
           return bail(rc);
-        lv.fxx = FxDir{dtx, dex};
-        lv.fxy = FxDir{dty, dey};
+        lv.fxx = FxDir{dtx, dex, dsx};
+        lv.fxy = FxDir{dty, dey, dsy};
         h->fx_ok = true;
       }
     }

@@ -633,11 +633,11 @@ std::string coarse_var_inverse(const Mesh1D& mx, const Mesh1D& my, int kind, dou
   return "";
 }
 
-bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t) {
+bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t, std::vector<int>& slot) {
   const int p = d.p, np1 = p + 1, H = p / 2;
   const int NE = (H + 1) * (H + 1), NO = H * H;
-  tab.assign((size_t)(d.n + 1) * (NE + NO) * 4, 0);  // element n: zeros (missing neighbours)
-  t.assign(d.n + 1, 0);
+  const size_t B = (size_t)(NE + NO) * 4;  // ints per table
+  std::vector<int> all((size_t)d.n * B, 0), te_of(d.n, 0);
   std::vector<__int128> li(np1 * np1);
   for (int e = 0; e < d.n; ++e) {
     const double* L = d.Le.data() + (size_t)e * np1 * np1;
@@ -647,7 +647,7 @@ bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t) {
     int ex_max = 0;
     std::frexp(amax, &ex_max);  // amax in [2^(ex_max-1), 2^ex_max)
     const int te = 73 - ex_max;  // |L| 2^te < 2^73
-    t[e] = te;
+    te_of[e] = te;
     for (int i = 0; i < np1 * np1; ++i) {
       int ex = 0;
       const double fr = std::frexp(L[i], &ex);        // L = fr 2^ex, |fr| in [0.5, 1)
@@ -664,7 +664,7 @@ bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t) {
     for (int a = 0; a <= p; ++a)
       for (int k = 0; k <= p; ++k)
         if (li[(p - a) * np1 + (p - k)] != li[a * np1 + k]) return false;
-    int* out = tab.data() + (size_t)e * (NE + NO) * 4;
+    int* out = all.data() + (size_t)e * B;
     auto put = [&](int idx, __int128 v) {  // v = l2 2^50 + l1 2^25 + l0, l0, l1 in [0, 2^25)
       const __int128 q1 = v >> 25, q2 = v >> 50;  // arithmetic shifts (floor)
       out[4 * idx] = (int)(v - (q1 << 25));
@@ -677,6 +677,25 @@ bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t) {
     for (int a = 0; a < H; ++a)
       for (int k = 0; k < H; ++k) put(NE + a * H + k, li[a * np1 + k] - li[a * np1 + p - k]);
   }
+  // one copy per distinct (table, t), in order of first use; then the zero table
+  tab.clear();
+  t.clear();
+  slot.assign(d.n + 1, 0);
+  std::map<std::pair<int, std::vector<int>>, int> seen;
+  for (int e = 0; e < d.n; ++e) {
+    auto key = std::make_pair(te_of[e], std::vector<int>(all.begin() + (size_t)e * B, all.begin() + (size_t)(e + 1) * B));
+    auto it = seen.find(key);
+    if (it == seen.end()) {
+      const int k = (int)t.size();
+      tab.insert(tab.end(), key.second.begin(), key.second.end());
+      t.push_back(te_of[e]);
+      it = seen.emplace(std::move(key), k).first;
+    }
+    slot[e] = it->second;
+  }
+  slot[d.n] = (int)t.size();
+  tab.insert(tab.end(), B, 0);
+  t.push_back(0);
   return true;
 }
 

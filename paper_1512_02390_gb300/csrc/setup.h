@@ -121,11 +121,13 @@ void interp_matrix(int pf, int pc, std::vector<double>& J);
 // exponents; then rounded to nearest), E[a][k] = L_int[a][k] + L_int[a][p-k]
 // (k < p/2), E[a][p/2] = 2 L_int[a][p/2], O[a][k] = L_int[a][k] -
 // L_int[a][p-k], each stored as four ints (l0, l1, l2, 0) with value
-// l2 2^50 + l1 2^25 + l0, l0 and l1 in [0, 2^25).  tab: (n + 1) x
-// ((p/2+1)^2 + (p/2)^2) entries, element n all zero (t[n] = 0) for missing
-// neighbours.  Returns false (tables unusable) when an element matrix is not
-// centro-symmetric in these integers, L_int[p-a][p-k] == L_int[a][k], which
-// the even-odd form needs.
-bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t);
+// l2 2^50 + l1 2^25 + l0, l0 and l1 in [0, 2^25).  Elements whose tables
+// and t are equal share one copy: tab holds k + 1 tables of ((p/2+1)^2 +
+// (p/2)^2) entries, the last all zero (t = 0) for missing neighbours; t has
+// k + 1 entries; slot (n + 1 entries) gives element e's table, slot[n] the
+// zero table (a uniform mesh needs k = 1).  Returns false (tables unusable)
+// when an element matrix is not centro-symmetric in these integers,
+// L_int[p-a][p-k] == L_int[a][k], which the even-odd form needs.
+bool fx_tables(const Dir1D& d, std::vector<int>& tab, std::vector<int>& t, std::vector<int>& slot);
 
 }  // namespace sem

@@ -43,6 +43,8 @@ CASES = [
     dict(nx=3, ny=3, p=32),
     dict(nx=3, ny=4, p=32, periodic=True),
     dict(nx=4, ny=3, p=8, edges=[0.0, 0.1, 0.5, 0.55, 1.0]),  # stretched x
+    dict(nx=5, ny=4, p=8, edges=[0.0, 0.25, 0.5, 0.625, 0.75, 1.0]),  # two element widths, interleaved (shared tables)
+    dict(nx=5, ny=3, p=32, edges=[0.0, 0.25, 0.375, 0.5, 0.75, 1.0], periodic=True),
     dict(nx=6, ny=4, p=16, edges=list(SI.geometric_edges(6, 1.0 / 48))),
 ]
 
