@@ -51,7 +51,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 INT_MAD_PEAK_TOPS = 56.24 * 152 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_apply_fx<16> launch on the 64 x 64,
 # p = 16 workload (profiles/k_apply_fx_p16_64x64.md): p and z read, q stays in L2
-APPLY_FX_DRAM_BYTES = 17.20e6
+APPLY_FX_DRAM_BYTES = 16.90e6
 
 
 def _peaks():
