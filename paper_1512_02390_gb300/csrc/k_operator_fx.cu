@@ -45,36 +45,53 @@ template <int P>
 struct FxTile {
   static constexpr int H = P / 2;
   static constexpr int TE = Tile<P>::TE, TN = Tile<P>::TN, LN = Tile<P>::LN, NP = P + 1;
-  static constexpr int LP = LN | 1;
   static constexpr int NE = (H + 1) * (H + 1), NO = H * H, EO = NE + NO;
   static constexpr int NV = 2 * H + 1;  // e_0..e_H, o_0..o_{H-1}
   static constexpr int NT = 256;  // threads per CTA
   static constexpr int NW = NT / 32;
   static constexpr int SB = P >= 32 ? 1 : 5;  // staging loads issued together per thread
+  // The staged tile without its P x P corner below and left of the tile
+  // (read by neither direction): the low-side halo rows 0 .. P-1 hold only
+  // the columns P .. LN-1 (pitch TW), rows P .. LN-1 all LN columns.
+  static constexpr int TW = LN - P;
+  static constexpr int kTop = P * TW;
+  static constexpr int kTile = kTop + (LN - P) * LN;
+  // The products of one direction: per row (x) or column (y) the low-side
+  // neighbour's y_P, then NP values for each of the TE elements.
+  static constexpr int PS = 1 + TE * NP;
+  static constexpr int kProd = TN * PS;
+  // staged value at tile row ly, column w + P (ly in [0, LN), w in [0, TN))
+  __device__ static __forceinline__ int col_at(int ly, int w) {
+    return ly < P ? ly * TW + w : kTop + (ly - P) * LN + w + P;
+  }
+  // slot sl's value at element node b (slot 0: only b = P)
+  __device__ static __forceinline__ int prod_off(int sl, int b) { return sl == 0 ? 0 : 1 + (sl - 1) * NP + b; }
 };
 
 // Shared memory.  Two phase schedules, chosen per order by measurement:
-//  - merged (p != 16): the e/o pairs of both directions are formed from the
+//  - merged (p <= 8): the e/o pairs of both directions are formed from the
 //    staged tile, then all products run in one pass (one barrier less, and
 //    the items of both directions balance over the warps).  Region A holds
 //    the staged tile, later the x and y products; region B the e/o pairs of
-//    both directions, later the block-sum scratch.
-//  - separate (p = 16, where the larger footprint of the merged form lost at
-//    256 x 256 elements): e/o and products of x, then of y.  Region A holds
-//    the staged tile, later the y products; region B the e/o pairs of one
-//    direction, the x products and the block-sum scratch.
-// Then the mass diagonals, the per-warp exponent maxima and the per-slot
-// table indices and scales.
+//    both directions.
+//  - separate (p = 16, 32; the smaller footprint gives p = 32 four CTAs per
+//    SM instead of three, and the merged form lost at p = 16 on 256 x 256
+//    elements): e/o and products of x, then of y.  Region A holds the staged
+//    tile, later the y products; region B the e/o pairs of one direction and
+//    the x products.
+// The block-sum scratch takes the e/o pairs' place at the end.  Then the mass
+// diagonals, the per-warp exponent maxima and the per-slot table indices and
+// scales.
 template <int P>
 struct FxSmem {
   using Q = FxTile<P>;
-  static constexpr bool kMerged = P != 16;
-  static constexpr int kTile = Q::LN * Q::LP;                // staged tile (double)
-  static constexpr int kProd = Q::TN * (Q::TE + 1) * Q::NP;  // products of one direction (double)
-  static constexpr int kEv = (Q::TE + 1) * Q::NV * Q::TN;    // e/o pairs of one direction (int2)
+  static constexpr bool kMerged = P <= 8;
+  static constexpr int kTile = Q::kTile;                  // staged tile (double)
+  static constexpr int kProd = Q::kProd;                  // products of one direction (double)
+  static constexpr int kEv = (Q::TE + 1) * Q::NV * Q::TN;  // e/o pairs of one direction (int2)
   static constexpr int kA = kMerged ? (kTile > 2 * kProd ? kTile : 2 * kProd) : kTile;
-  static constexpr int kB = kMerged ? 2 * kEv : kEv + kProd + Q::NT;  // 8-byte words
-  static_assert(kMerged ? 2 * kEv >= Q::NT : kProd <= kTile, "shared-memory regions overlap");
+  static constexpr int kB = kMerged ? 2 * kEv : kEv + kProd;  // 8-byte words
+  static_assert(kEv >= Q::NT && (kMerged || kProd <= kTile), "shared-memory regions overlap");
   static constexpr size_t kBytes =
       8 * ((size_t)kA + kB + 2 * (Q::TN + 1)) + sizeof(int) * (Q::NW + 4 * (Q::TE + 1));
 };
@@ -96,20 +113,19 @@ __device__ __forceinline__ int2 fx_pair(long long v) {
 template <int P, bool XDIR>
 __device__ __forceinline__ void fx_form_eo(const double* su, int emax, int2* ev) {
   using Q = FxTile<P>;
-  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LP = Q::LP, NV = Q::NV;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, LN = Q::LN, NV = Q::NV, kTop = Q::kTop;
   for (int idx = threadIdx.x; idx < (TE + 1) * H * TN; idx += blockDim.x) {
     const int w = idx % TN;
     const int q = idx / TN;
     const int sl = q / H, k = q - sl * H;
     long long xk, xm;
-    if (XDIR) {
-      const double* x = su + (w + P) * LP + sl * P;
+    if (XDIR) {  // row w + P (full width)
+      const double* x = su + kTop + w * LN + sl * P;
       xk = fx_of(x[k], emax);
       xm = fx_of(x[P - k], emax);
-    } else {
-      const double* x = su + (sl * P) * LP + w + P;
-      xk = fx_of(x[k * LP], emax);
-      xm = fx_of(x[(P - k) * LP], emax);
+    } else {  // column w + P
+      xk = fx_of(su[Q::col_at(sl * P + k, w)], emax);
+      xm = fx_of(su[Q::col_at(sl * P + P - k, w)], emax);
     }
     ev[(sl * NV + k) * TN + w] = fx_pair(xk + xm);
     ev[(sl * NV + H + 1 + k) * TN + w] = fx_pair(xk - xm);
@@ -117,7 +133,7 @@ __device__ __forceinline__ void fx_form_eo(const double* su, int emax, int2* ev)
   for (int idx = threadIdx.x; idx < (TE + 1) * TN; idx += blockDim.x) {
     const int w = idx % TN, sl = idx / TN;
     ev[(sl * NV + H) * TN + w] =
-        fx_pair(fx_of(XDIR ? su[(w + P) * LP + sl * P + H] : su[(sl * P + H) * LP + w + P], emax));
+        fx_pair(fx_of(XDIR ? su[kTop + w * LN + sl * P + H] : su[Q::col_at(sl * P + H, w)], emax));
   }
 }
 
@@ -129,7 +145,7 @@ template <int P, bool XDIR>
 __device__ __forceinline__ void fx_item(const int4* __restrict__ tab, const int* sts, int emax, const int2* ev,
                                         double* dst_base, int idx) {
   using Q = FxTile<P>;
-  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, NP = Q::NP, EO = Q::EO, NE = Q::NE, NV = Q::NV;
+  constexpr int H = Q::H, TE = Q::TE, TN = Q::TN, EO = Q::EO, NE = Q::NE, NV = Q::NV;
   {
     const int w = idx % TN;
     const int q = idx / TN;
@@ -195,10 +211,11 @@ __device__ __forceinline__ void fx_item(const int4* __restrict__ tab, const int*
     }
     // y = (YE +- YO) 2^-(s + t + 1), s = 1075 - emax
     const int K = 1076 - emax + sts[TE + 1 + sl];
-    double* dst = XDIR ? dst_base + (w * (TE + 1) + sl) * NP : dst_base + (sl * NP) * TN + w;
+    // x: [row w][Q::prod_off], y: [Q::prod_off][column w]; slot 0 stores only y_P (a = 0)
+    double* dst = XDIR ? dst_base + w * Q::PS : dst_base + w;
     constexpr int step = XDIR ? 1 : TN;
-    if (a < H) dst[(P - a) * step] = fx_to_f64(e0 - o0, e1 - o1, e2 - o2, e3 - o3, K);
-    if (sl > 0) dst[a * step] = fx_to_f64(e0 + o0, e1 + o1, e2 + o2, e3 + o3, K);
+    if (a < H) dst[Q::prod_off(sl, P - a) * step] = fx_to_f64(e0 - o0, e1 - o1, e2 - o2, e3 - o3, K);
+    if (sl > 0) dst[Q::prod_off(sl, a) * step] = fx_to_f64(e0 + o0, e1 + o1, e2 + o2, e3 + o3, K);
   }
 }
 
@@ -209,15 +226,16 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
                                                   PcgFuse pf) {
   pdl_enter();
   using Q = FxTile<P>;
-  constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, LP = Q::LP, NP = Q::NP, NW = Q::NW;
+  constexpr int TE = Q::TE, TN = Q::TN, LN = Q::LN, NP = Q::NP, NW = Q::NW;
+  constexpr int TW = Q::TW, kTop = Q::kTop, PS = Q::PS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using S = FxSmem<P>;
-  double* su = reinterpret_cast<double*>(smem_raw);  // region A: the staged tile (LN x LP)
+  double* su = reinterpret_cast<double*>(smem_raw);  // region A: the staged tile (Q::kTile)
   int2* evx = reinterpret_cast<int2*>(su + S::kA);    // region B: e/o pairs, (TE+1) x NV x TN
   int2* evy = S::kMerged ? evx + S::kEv : evx;
-  double* xb = S::kMerged ? su : reinterpret_cast<double*>(evx + S::kEv);  // [row][slot][a]
-  double* yb = S::kMerged ? su + S::kProd : su;                            // [slot][b][col]
-  double* sred = S::kMerged ? reinterpret_cast<double*>(evx) : xb + S::kProd;  // NT doubles
+  double* xb = S::kMerged ? su : reinterpret_cast<double*>(evx + S::kEv);  // [row][Q::prod_off]
+  double* yb = S::kMerged ? su + S::kProd : su;                            // [Q::prod_off][col]
+  double* sred = reinterpret_cast<double*>(evx);  // NT doubles, once the products are formed
   double* sMx = su + S::kA + S::kB;
   double* sMy = sMx + (TN + 1);
   int* semax = reinterpret_cast<int*>(sMy + (TN + 1));
@@ -228,40 +246,44 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
   const int gx0 = ex0 * P - P, gy0 = ey0 * P - P;
   const double beta = fused_beta(pf, blockIdx.y, gridDim.y);
   // staging: the operand (z + beta p with the fused direction update, else
-  // u) on the tile and its low-side halo; the P x P corner below and left of
-  // the tile is read by neither direction and is zeroed.  The loads of kSB
-  // nodes are issued before their stores (one memory latency per batch).
+  // u) on the tile and its low-side halo, without the P x P corner (shared
+  // offset idx: Q::col_at's layout).  The loads of kSB nodes are issued
+  // before their stores (one memory latency per batch).
   int emax = 0;  // largest exponent field of the staged values
-  constexpr int NT = Q::NT, kNS = (LN * LN + NT - 1) / NT, kSB = Q::SB;
+  constexpr int NT = Q::NT, kNS = (Q::kTile + NT - 1) / NT, kSB = Q::SB;
 #pragma unroll
   for (int b0 = 0; b0 < kNS; b0 += kSB) {
     double va[kSB], vb[kSB];
-    int off[kSB];
 #pragma unroll
     for (int j = 0; j < kSB; ++j) {
       const int idx = threadIdx.x + (b0 + j) * NT;
-      off[j] = -1;
       va[j] = 0.0;
       vb[j] = 0.0;
-      if (b0 + j < kNS && idx < LN * LN) {
-        const int ly = idx / LN, lx = idx - ly * LN;
-        off[j] = ly * LP + lx;
-        if (ly >= P || lx >= P) {
-          const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
-          const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
-          if (gx >= 0 && gy >= 0) {
-            const long o = (long)gy * Nx + gx;
-            va[j] = u[o];
-            if (pf.z) vb[j] = pf.z[o];
-          }
+      if (b0 + j < kNS && idx < Q::kTile) {
+        int ly, lx;
+        if (idx < kTop) {
+          ly = idx / TW;
+          lx = P + idx - ly * TW;
+        } else {
+          ly = (idx - kTop) / LN;
+          lx = idx - kTop - ly * LN;
+          ly += P;
+        }
+        const int gx = node_or_wall(gx0 + lx, Nx, dx.periodic, dx.segN);
+        const int gy = node_or_wall(gy0 + ly, Ny, dy.periodic, dy.segN);
+        if (gx >= 0 && gy >= 0) {
+          const long o = (long)gy * Nx + gx;
+          va[j] = u[o];
+          if (pf.z) vb[j] = pf.z[o];
         }
       }
     }
 #pragma unroll
     for (int j = 0; j < kSB; ++j) {
-      if (off[j] < 0) continue;
+      const int idx = threadIdx.x + (b0 + j) * NT;
+      if (b0 + j >= kNS || idx >= Q::kTile) continue;
       const double v = pf.z ? fma(beta, va[j], vb[j]) : va[j];  // as stage_value
-      su[off[j]] = v;
+      su[idx] = v;
       emax = max(emax, (__double2hiint(v) >> 20) & 0x7ff);
     }
   }
@@ -303,7 +325,7 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
     own[q] = 0.0;
     if (idx < ownx * owny) {
       const int jy = idx / ownx, ix = idx - jy * ownx;
-      own[q] = su[(jy + P) * LP + ix + P];
+      own[q] = su[kTop + jy * LN + ix + P];
     }
   }
   const int4* tabx = reinterpret_cast<const int4*>(fx.tab);
@@ -342,10 +364,12 @@ __global__ void __launch_bounds__(FxTile<P>::NT) k_apply_fx(DirView<double> dx, 
     if (!wall) {
       const int lex = ix / P, a = ix - lex * P;
       const int ley = jy / P, b = jy - ley * P;
-      const double* xr = xb + (jy * (TE + 1) + lex + 1) * NP;
+      // slot lex + 1's values; a = 0 adds the left slot's y_P (Q::prod_off:
+      // 1 + (lex - 1) NP + P, or 0 for slot 0)
+      const double* xr = xb + jy * PS + 1 + lex * NP;
       double xs = xr[a];
-      if (a == 0) xs += xr[P - NP];  // y_P of the left slot
-      const double* yc = yb + ((ley + 1) * NP) * TN + ix;
+      if (a == 0) xs += xr[P - NP];
+      const double* yc = yb + (1 + ley * NP) * TN + ix;
       double ys = yc[b * TN];
       if (b == 0) ys += yc[(P - NP) * TN];
       val = sMy[jy] * xs + sMx[ix] * ys;
