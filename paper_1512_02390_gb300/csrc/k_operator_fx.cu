@@ -157,56 +157,24 @@ __device__ __forceinline__ void fx_item(const int4* __restrict__ tab, const int*
     const int2* e = ev + (sl * NV) * TN + w;
     const int2* o = ev + (sl * NV + H + 1) * TN + w;
     long long e0 = 0, e1 = 0, e2 = 0, e3 = 0, o0 = 0, o1 = 0, o2 = 0, o3 = 0;
-    if constexpr (P >= 32) {
-      // the even and odd sums in one loop: their 17- and 16-term chains
-      // interleave; the middle row a = H has no odd part, so its odd sums run
-      // on row H - 1 and are masked off
 #pragma unroll
-      for (int k = 0; k < H; ++k) {
-        const int4 l = __ldg(E + k);
-        const int4 m = __ldg(O + k);
-        const int2 x = e[k * TN];
-        const int2 y = o[k * TN];
-        e0 += (long long)x.x * l.x;
-        o0 += (long long)y.x * m.x;
-        e1 += (long long)x.x * l.y + (long long)x.y * l.x;
-        o1 += (long long)y.x * m.y + (long long)y.y * m.x;
-        e2 += (long long)x.x * l.z + (long long)x.y * l.y;
-        o2 += (long long)y.x * m.z + (long long)y.y * m.y;
-        e3 += (long long)x.y * l.z;
-        o3 += (long long)y.y * m.z;
-      }
-      const int4 l = __ldg(E + H);
-      const int2 x = e[H * TN];
+    for (int k = 0; k <= H; ++k) {
+      const int4 l = __ldg(E + k);
+      const int2 x = e[k * TN];
       e0 += (long long)x.x * l.x;
       e1 += (long long)x.x * l.y + (long long)x.y * l.x;
       e2 += (long long)x.x * l.z + (long long)x.y * l.y;
       e3 += (long long)x.y * l.z;
-      const long long om = a < H ? -1LL : 0LL;
-      o0 &= om;
-      o1 &= om;
-      o2 &= om;
-      o3 &= om;
-    } else {
+    }
+    if (a < H) {  // the middle row has no odd part; uniform across a warp (w = lane)
 #pragma unroll
-      for (int k = 0; k <= H; ++k) {
-        const int4 l = __ldg(E + k);
-        const int2 x = e[k * TN];
-        e0 += (long long)x.x * l.x;
-        e1 += (long long)x.x * l.y + (long long)x.y * l.x;
-        e2 += (long long)x.x * l.z + (long long)x.y * l.y;
-        e3 += (long long)x.y * l.z;
-      }
-      if (a < H) {  // uniform across a warp (w = lane)
-#pragma unroll
-        for (int k = 0; k < H; ++k) {
-          const int4 l = __ldg(O + k);
-          const int2 x = o[k * TN];
-          o0 += (long long)x.x * l.x;
-          o1 += (long long)x.x * l.y + (long long)x.y * l.x;
-          o2 += (long long)x.x * l.z + (long long)x.y * l.y;
-          o3 += (long long)x.y * l.z;
-        }
+      for (int k = 0; k < H; ++k) {
+        const int4 l = __ldg(O + k);
+        const int2 x = o[k * TN];
+        o0 += (long long)x.x * l.x;
+        o1 += (long long)x.x * l.y + (long long)x.y * l.x;
+        o2 += (long long)x.x * l.z + (long long)x.y * l.y;
+        o3 += (long long)x.y * l.z;
       }
     }
     // y = (YE +- YO) 2^-(s + t + 1), s = 1075 - emax
