@@ -23,9 +23,8 @@
 //     the even and odd sums together have p + 1 <= 33 terms, two products per
 //     weight and term, so each accumulator stays below 2^60: no sum rounds or
 //     overflows;
-//   - 2 y_a = YE + YO and 2 y_{p-a} = YE - YO are carry-normalised to
-//     C3 2^75 + R (R in [0, 2^75)) and rounded to FP64 once (nearest, ties to
-//     even).
+//   - 2 y_a = YE + YO and 2 y_{p-a} = YE - YO, four accumulators each, are
+//     rounded to FP64 once (nearest, ties to even; fx_exact.h fx_to_f64).
 // A node's value is then My[j] y_x + Mx[i] y_y in FP64, as in the other forms.
 // The only roundings are the fixed-point step of x (2^-53 of the tile's
 // largest |x|) and the final ones; the even-odd folding itself is exact,
