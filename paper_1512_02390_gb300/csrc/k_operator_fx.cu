@@ -48,7 +48,7 @@ struct FxTile {
   static constexpr int NV = 2 * H + 1;  // e_0..e_H, o_0..o_{H-1}
   static constexpr int NT = 256;  // threads per CTA
   static constexpr int NW = NT / 32;
-  static constexpr int SB = P >= 32 ? 1 : 5;  // staging loads issued together per thread
+  static constexpr int SB = 5;  // staging loads issued together per thread
   // The staged tile without its P x P corner below and left of the tile
   // (read by neither direction): the low-side halo rows 0 .. P-1 hold only
   // the columns P .. LN-1 (pitch TW), rows P .. LN-1 all LN columns.
