@@ -332,3 +332,105 @@ def test_fixed_point_operand_and_limbs_are_exact(tmp_path):
               ctypes.c_long(v.size))
     assert np.all((lo >= 0) & (lo < 2**25))
     assert np.array_equal(lo.astype(np.int64) + hi.astype(np.int64) * 2**25, v)
+
+
+# ---- the fixed-point element tables of the integer FP64 operator ----------
+
+_FXTAB_SRC = r'''
+#include <cstring>
+#include "setup.h"
+extern "C" int fx_tab(int n, const double* edges, int periodic, int p, int n_o, int* tab, int tab_cap, int* t,
+                      int* slot, int* ntab, double* Le) {
+  sem::Mesh1D m;
+  m.n = n;
+  m.periodic = periodic != 0;
+  m.edges.assign(edges, edges + n + 1);
+  sem::Dir1D d;
+  if (!sem::build_dir(m, p, n_o, 5, d).empty()) return -1;
+  std::vector<int> tb, tt, sl;
+  if (!sem::fx_tables(d, tb, tt, sl)) return -2;
+  if ((int)tb.size() > tab_cap) return -3;
+  std::memcpy(tab, tb.data(), tb.size() * sizeof(int));
+  std::memcpy(t, tt.data(), tt.size() * sizeof(int));
+  std::memcpy(slot, sl.data(), sl.size() * sizeof(int));
+  *ntab = (int)tt.size();
+  std::memcpy(Le, d.Le.data(), d.Le.size() * sizeof(double));
+  return 0;
+}
+'''
+
+
+@pytest.mark.parametrize("edges,p,periodic", [
+    ([0.0, 0.25, 0.5, 0.625, 0.75, 1.0], 8, False),      # two element widths, interleaved
+    ([i / 6 for i in range(7)], 16, False),                # uniform (computed edges: widths may differ in the last bit)
+    ([0.0, 0.5, 0.75, 0.875, 0.9375, 1.0], 32, False),     # five widths
+    ([0.0, 0.25, 0.375, 0.5, 0.75, 1.0], 4, True),         # periodic
+])
+def test_fixed_point_tables_are_exact_and_shared(tmp_path, edges, p, periodic):
+    """The operator's element tables (setup.cpp fx_tables): every element
+    matrix L becomes L_int = L 2^t, which must be an exact integer with
+    2^72 <= max |L_int| < 2^73; the even-odd entries E[a][k] = L_int[a][k] +
+    L_int[a][p-k] (E[a][p/2] = 2 L_int[a][p/2]) and O[a][k] = L_int[a][k] -
+    L_int[a][p-k] are stored as three 25-bit limbs l2 2^50 + l1 2^25 + l0.
+    Elements with bitwise equal matrices share one table, others do not, and
+    the last table (that of the missing neighbour) is zero.  Checked against
+    Python's exact rational arithmetic on the library's own element matrices."""
+    import ctypes
+    import shutil
+    import subprocess
+    from fractions import Fraction
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_1512_02390_gb300", "csrc")
+    src = tmp_path / "fxtab.cpp"
+    src.write_text(_FXTAB_SRC)
+    so = tmp_path / "fxtab.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-I", csrc, "-I",
+                    os.path.join(root, "include"), os.path.join(csrc, "setup.cpp"), str(src), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    n, H, np1 = len(edges) - 1, p // 2, p + 1
+    NE, NO = (H + 1) ** 2, H * H
+    EO = NE + NO
+    cap = (n + 1) * EO * 4
+    tab = np.zeros(cap, dtype=np.int32)
+    t = np.zeros(n + 1, dtype=np.int32)
+    slot = np.zeros(n + 1, dtype=np.int32)
+    ntab = ctypes.c_int(0)
+    Le = np.zeros(n * np1 * np1)
+    e = np.ascontiguousarray(np.array(edges, dtype=np.float64))
+    vp = ctypes.c_void_p
+    rc = lib.fx_tab(ctypes.c_int(n), e.ctypes.data_as(vp), ctypes.c_int(int(periodic)), ctypes.c_int(p),
+                    ctypes.c_int(1), tab.ctypes.data_as(vp), ctypes.c_int(cap), t.ctypes.data_as(vp),
+                    slot.ctypes.data_as(vp), ctypes.byref(ntab), Le.ctypes.data_as(vp))
+    assert rc == 0
+    k = ntab.value
+    tab = tab[:k * EO * 4].reshape(k, EO, 4).astype(np.int64)
+    # sharing: equal matrices <=> equal table; the zero table last
+    rows = [Le[i * np1 * np1:(i + 1) * np1 * np1].tobytes() for i in range(n)]
+    assert len(set(rows)) == k - 1
+    for i in range(n):
+        for j in range(n):
+            assert (slot[i] == slot[j]) == (rows[i] == rows[j])
+    assert slot[n] == k - 1 and t[k - 1] == 0 and not tab[k - 1].any()
+    assert sorted(set(slot[:n].tolist())) == list(range(k - 1))
+    # exact fixed point, even-odd folding and limbs
+    assert np.all((tab[..., 0] >= 0) & (tab[..., 0] < 2**25) & (tab[..., 1] >= 0) & (tab[..., 1] < 2**25))
+    assert not tab[..., 3].any()
+    val = [[int(x[2]) * 2**50 + int(x[1]) * 2**25 + int(x[0]) for x in tab[s]] for s in range(k)]
+    for i in range(n):
+        s, te = slot[i], int(t[slot[i]])
+        L = Le[i * np1 * np1:(i + 1) * np1 * np1].reshape(np1, np1)
+        Li = [[Fraction(float(L[a, b])) * Fraction(2) ** te for b in range(np1)] for a in range(np1)]
+        assert all(x.denominator == 1 for row in Li for x in row)
+        Li = [[int(x) for x in row] for row in Li]
+        big = max(abs(x) for row in Li for x in row)
+        assert 2**72 <= big < 2**73
+        for a in range(H + 1):
+            for kk in range(H + 1):
+                want = 2 * Li[a][H] if kk == H else Li[a][kk] + Li[a][p - kk]
+                assert val[s][a * (H + 1) + kk] == want
+        for a in range(H):
+            for kk in range(H):
+                assert val[s][NE + a * H + kk] == Li[a][kk] - Li[a][p - kk]
