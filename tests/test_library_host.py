@@ -434,3 +434,23 @@ def test_fixed_point_tables_are_exact_and_shared(tmp_path, edges, p, periodic):
         for a in range(H):
             for kk in range(H):
                 assert val[s][NE + a * H + kk] == Li[a][kk] - Li[a][p - kk]
+
+
+def test_noalloc_wrapper_rejects_vectors_of_the_wrong_size():
+    """The Python wrapper of the allocation-free correction checks r and u
+    against the node grid the tables describe (n p + 1 nodes per Dirichlet
+    direction, n p periodic) before any call into the library, which cannot
+    check pointer extents itself."""
+    torch = pytest.importorskip("torch")
+    P = pytest.importorskip("paper_1512_02390_gb300")
+    tx = P.sem_sweep_tables(n=4, p=8, n_o=1, periodic=0)
+    ty = P.sem_sweep_tables(n=3, p=8, n_o=1, periodic=0)
+    ok = torch.zeros((3 * 8 + 1) * (4 * 8 + 1), dtype=torch.float64)
+    short = torch.zeros(ok.numel() - 1, dtype=torch.float64)
+    for r, u in ((short, ok), (ok, short), (ok[: (4 * 8 + 1) ** 2 - 8], ok)):
+        with pytest.raises(ValueError):
+            P.sem_schwarz_correction_noalloc(tx, ty, r, u)
+    px = P.sem_sweep_tables(n=4, p=8, n_o=1, periodic=1)
+    py = P.sem_sweep_tables(n=3, p=8, n_o=1, periodic=1)
+    with pytest.raises(ValueError):  # a periodic grid has 24 x 32 nodes
+        P.sem_schwarz_correction_noalloc(px, py, ok, ok)
